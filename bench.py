@@ -1,0 +1,382 @@
+"""Benchmark of the PRTGS hot path on GB300.
+
+One step = one pass of the whole path over the 100k-Gaussian surface workload (SH order 3,
+S = 256 directions, shadow + one-bounce transfer, one 16-coefficient RGB light, 1920x1080):
+BVH build -> transfer precompute (trace + bounce) -> relight -> splat render -> L2 loss ->
+render backward -> relight backward. Inputs are seeded synthetic stand-ins for the paper's
+datasets. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (brute force, all host cores) on bounded samples
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "surface-100k"
+METRIC = "transfer rays/s and relit 1080p frames/s (fwd+bwd) vs plain FP32 at <=1e-4 rel err"
+UNIT = "rays/s"
+L2_BYTES = 256 << 20  # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_inputs():
+    from paper_2408_03538_gb300 import scenes as S
+
+    w = S.WORKLOADS[WORKLOAD]
+    sc = S.make_scene(WORKLOAD)
+    dirs = S.direction_set(w["n_dirs"], S.config_seed(w["config"]))
+    Lsh = S.env_lights(w["lights"], w["order"], S.config_seed(w["config"]) + 1)
+    Ltarget = S.env_lights(w["lights"], w["order"], S.config_seed(w["config"]) + 2)
+    cam = S.make_camera(WORKLOAD)
+    return w, sc, dirs, Lsh, Ltarget, cam
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (also the --impl reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(sc, dirs, order, n_recv, seed):
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    recv = np.sort(rng.choice(sc.n, size=n_recv, replace=False))
+    t0 = time.perf_counter()
+    tr = oracle.trace(sc, dirs, order, recv, shadow=True, bounce=True)
+    dt = time.perf_counter() - t0
+    return dt, n_recv * dirs.shape[0], tr
+
+
+def calibrate_oracle(sc, dirs, order, budget_s):
+    dt, _, _ = oracle_sample(sc, dirs, order, 16, 1)
+    per = dt / 16
+    return max(16, min(sc.n, int(budget_s / max(per, 1e-6))))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w, sc, dirs, *_ = workload_inputs()
+    order = w["order"]
+    import oracle
+
+    oracle.build()
+    n_recv = calibrate_oracle(sc, dirs, order, 4.0)
+    for i in range(args.warmup):
+        oracle_sample(sc, dirs, order, max(16, n_recv // 4), 100 + i)
+    times, rays, hits, traced = [], 0, 0.0, 0
+    for i in range(args.steps):
+        dt, r, tr = oracle_sample(sc, dirs, order, n_recv, 1000 + i)
+        times.append(dt)
+        rays += r
+        hits += float(tr["hits"].sum())
+        traced += int(((tr["flags"] & 1) != 0).sum())
+    total = sum(times)
+    value = rays / total
+    sample = (f"{n_recv} seeded receivers x {dirs.shape[0]} directions of the {WORKLOAD} workload per step "
+              f"(brute force over all {sc.n} Gaussians, shadow + index matrix), FP64 C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_order": order, "n_dirs": int(dirs.shape[0]),
+                       "sampled_receivers_per_step": n_recv},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "hits_per_traced_ray": hits / max(traced, 1)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w, sc, dirs, Lsh_np, Lt_np, cam = workload_inputs()
+    order, S_ = w["order"], int(dirs.shape[0])
+    C = (order + 1) ** 2
+    # host (pinned) inputs for the end-to-end leg
+    host = {f: torch.from_numpy(np.ascontiguousarray(getattr(sc, f))).pin_memory()
+            for f in ("means", "scales", "quats", "opacity", "normals", "albedo")}
+    host["dirs"] = torch.from_numpy(dirs).pin_memory()
+    host["L"] = torch.from_numpy(Lsh_np).pin_memory()
+    g = api.GaussianTensors(*(host[f].to(dev) for f in ("means", "scales", "quats", "opacity", "normals", "albedo")))
+    d_dirs = host["dirs"].to(dev)
+    d_L = host["L"].to(dev)
+    bg = torch.zeros(3, dtype=torch.float32, device=dev)
+    status = api.Status(dev)
+    # target image: the same scene under a second light, plus seeded noise (outside the timed region)
+    bvh0 = api.build_bvh(g, status=status)
+    tr0 = api.precompute_transfer(g, bvh0, d_dirs, order, bounce=True, status=status)
+    col_t = api.relight(tr0["T"], g.albedo, torch.from_numpy(Lt_np).to(dev), order)
+    img_t, st0 = api.render(g, col_t, cam, bg, max_pairs=12_000_000, status=status)
+    torch.cuda.synchronize()
+    n_pairs = st0.n_pairs()
+    max_pairs = int(n_pairs * 1.25) + 4096
+    rng = torch.Generator(device=dev).manual_seed(7)
+    target = (img_t + 0.01 * torch.randn(img_t.shape, generator=rng, device=dev)).contiguous()
+    host_target = target.cpu().pin_memory()
+    del tr0, col_t, img_t, st0, bvh0
+    # persistent buffers
+    P = torch.empty((g.n, C), dtype=torch.float32, device=dev)
+    T = torch.empty((g.n, 3, C), dtype=torch.float32, device=dev)
+    idx = torch.empty((g.n, S_), dtype=torch.int32, device=dev)
+    state = api.RenderState(g.n, cam.width, cam.height, max_pairs, dev)
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    stage_names = ["bvh", "transfer", "relight", "render", "loss", "render_bwd", "relight_bwd"]
+
+    def step(gt, dirs_t, L_t, target_t, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+
+        mark(0)
+        bvh = api.build_bvh(gt, status=status)
+        mark(1)
+        out = api.precompute_transfer(gt, bvh, dirs_t, order, bounce=True, status=status,
+                                      out={"P": P, "T": T, "idx": idx})
+        mark(2)
+        colors = api.relight(out["T"], gt.albedo, L_t, order)
+        mark(3)
+        img, _ = api.render(gt, colors, cam, bg, state=state, status=status)
+        mark(4)
+        loss, dimg = api.l2_loss(img, target_t)
+        mark(5)
+        dm, ds, dq, do, dcol = api.render_backward(gt, colors, cam, bg, state, dimg)
+        mark(6)
+        da, _, dL = api.relight_backward(out["T"], gt.albedo, L_t, order, dcol)
+        mark(7)
+        return loss, dL, (bvh, out, colors, img, dimg, dm, ds, dq, do, dcol, da)
+
+    for _ in range(args.warmup):
+        step(g, d_dirs, d_L, target)
+    torch.cuda.synchronize()
+    assert status.read() == 0, "device status reported an error"
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev_all = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        keep = step(g, d_dirs, d_L, target, ev)
+        ev_all.append((ev, keep))
+    torch.cuda.synchronize()
+    stage_ms = np.zeros(7)
+    total_ms = 0.0
+    for ev, _ in ev_all:
+        for i in range(7):
+            stage_ms[i] += ev[i].elapsed_time(ev[i + 1])
+        total_ms += ev[0].elapsed_time(ev[7])
+    # end-to-end: host inputs copied in, loss and light gradient copied out, every step
+    e2e_ms = 0.0
+    h2d = sum(host[f].numel() * host[f].element_size() for f in host) + host_target.numel() * 4
+    d2h = 4 + Lsh_np.size * 4
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    dL_h = torch.empty(Lsh_np.shape, dtype=torch.float32).pin_memory()
+    gbuf = api.GaussianTensors(*(torch.empty_like(x) for x in (g.means, g.scales, g.quats, g.opacity, g.normals,
+                                                                 g.albedo)))
+    dirs_b, L_b, tgt_b = torch.empty_like(d_dirs), torch.empty_like(d_L), torch.empty_like(target)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f in ("means", "scales", "quats", "opacity", "normals", "albedo"):
+            getattr(gbuf, f).copy_(host[f], non_blocking=True)
+        dirs_b.copy_(host["dirs"], non_blocking=True)
+        L_b.copy_(host["L"], non_blocking=True)
+        tgt_b.copy_(host_target, non_blocking=True)
+        loss, dL, _ = step(gbuf, dirs_b, L_b, tgt_b)
+        loss_h.copy_(loss, non_blocking=True)
+        dL_h.copy_(dL, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    assert status.read() == 0
+    t_local = np.array([total_ms, e2e_ms, stage_ms[1]])
+    if world > 1:
+        tt = torch.tensor(t_local, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_local = tt.cpu().numpy()
+    total_ms, e2e_ms, transfer_ms = (float(x) for x in t_local)
+    rays_per_step = g.n * S_
+    value = world * rays_per_step * args.steps / (total_ms / 1e3)
+    e2e_value = world * rays_per_step * args.steps / (e2e_ms / 1e3)
+    traced = int((sc.normals.astype(np.float64) @ dirs.astype(np.float64).T > 0).sum())
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+    # cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    hits_per_ray = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        n_recv = calibrate_oracle(sc, dirs, order, 12.0)
+        dt, rays, tr = oracle_sample(sc, dirs, order, n_recv, 999)
+        hits_per_ray = float(tr["hits"].sum() / max(1, ((tr["flags"] & 1) != 0).sum()))
+        cpu = {"value": rays / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{n_recv} seeded receivers x {S_} directions of {WORKLOAD} (shadow + index matrix, "
+                         f"brute force over all {sc.n} Gaussians), {dt:.1f} s"}
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA lanes x 2 flop x max clock
+    roof = None
+    if hits_per_ray is not None:
+        flops = traced * (hits_per_ray * 40.0 + 2.0 * C)
+        achieved = flops / (transfer_ms / args.steps / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_trace (+k_bounce), per transfer call", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz ({pk_kind} max clock)",
+                "algorithmic_flops_per_launch": flops}
+    launches = launches_per_step(g.n, n_pairs, cam)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": g.n, "sh_order": order, "n_dirs": S_,
+                       "transfer": "shadow+bounce", "lights": int(Lsh_np.shape[0]),
+                       "image": f"{cam.width}x{cam.height}", "l2": "flushed between steps (256 MB write)",
+                       "traced_rays_per_step": traced, "pairs_per_frame": n_pairs},
+            "frames_per_s": world * args.steps / (total_ms / 1e3),
+            "transfer_rays_per_s_stage": rays_per_step / (transfer_ms / args.steps / 1e3),
+            "relit_frames_per_s_fwd_bwd_stage": 1e3 / (stage_ms[2:].sum() / args.steps),
+            "stages_ms": {k: float(v / args.steps) for k, v in zip(stage_names, stage_ms)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+
+
+def launches_per_step(n, n_pairs, cam):
+    """Kernel launches of one step, following the launch sequence of the library."""
+    scan = 3
+    sort_pass = 1 + scan + 1
+    bvh = 3 + 4 * sort_pass + 2 + 1  # bounds init/bounds/morton, 4 passes, karras + roots, pack/refit
+    transfer = 2  # trace, bounce
+    relight = 1
+    tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    tile_bits = max(1, math.ceil(math.log2(tiles)))
+    render = 1 + scan + 1 + 1 + math.ceil((32 + tile_bits) / 8) * sort_pass + 1 + 1
+    loss = 2
+    render_bwd = 2
+    relight_bwd = 3
+    return bvh + transfer + relight + render + loss + render_bwd + relight_bwd
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

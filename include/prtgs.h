@@ -1,0 +1,289 @@
+/*
+ * libprtgs -- C ABI of a GB300 (sm_103a) implementation of the data-parallel hot path of
+ * "PRTGS: Precomputed Radiance Transfer of Gaussian Splats for Real-Time High-Quality
+ * Relighting" (arxiv 2408.03538).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Every array argument is a caller-owned, contiguous DEVICE pointer unless a comment
+ *    says "host". Floating point arrays are FP32, structure-of-arrays, row-major.
+ *  * The library never allocates device memory. Calls that need scratch space take
+ *    (void* workspace, size_t workspace_bytes) sized by the matching *_workspace_size()
+ *    query; the workspace must be 256-byte aligned and is clobbered by the call.
+ *  * All work is enqueued on the caller's stream (cudaStream_t passed as prtgs_stream_t)
+ *    and the call returns without synchronising. Calls keep no state between invocations,
+ *    so concurrent calls on different streams with distinct buffers are safe.
+ *  * Return value: PRTGS_OK or a negative PRTGS_ERR_* code for errors detected on the host
+ *    (arguments, shapes, workspace size, CUDA launch errors). Errors detected on the device
+ *    (non-finite inputs, traversal stack overflow, buffer capacity) are OR-ed as bit flags
+ *    into a caller-provided int32 device status word, read after synchronisation with
+ *    prtgs_read_status(). No kernel traps, asserts or waits without a bound.
+ *
+ * Notation follows the paper: N Gaussians, S sphere directions, C = (order+1)^2 real SH
+ * coefficients (order <= 3, so C <= 16), k lights, H x W image.
+ */
+#ifndef PRTGS_H
+#define PRTGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* prtgs_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+/* ---- status codes (host return values) ---------------------------------------------- */
+#define PRTGS_OK 0
+#define PRTGS_ERR_INVALID_ARG (-1)  /* null pointer, negative size, value out of range */
+#define PRTGS_ERR_SHAPE (-2)        /* inconsistent sizes */
+#define PRTGS_ERR_UNSUPPORTED (-3)  /* SH order outside 1..3, too many scenes, ... */
+#define PRTGS_ERR_WORKSPACE (-4)    /* workspace too small or misaligned */
+#define PRTGS_ERR_CUDA (-5)         /* a CUDA launch or copy failed */
+
+/* ---- device status bits (OR-ed into the caller's int32 status word) ------------------ */
+#define PRTGS_STATUS_NONFINITE 1       /* a non-finite or out-of-range Gaussian parameter */
+#define PRTGS_STATUS_STACK_OVERFLOW 2  /* BVH traversal stack exceeded (cannot happen for <= 2^27 leaves) */
+#define PRTGS_STATUS_CAPACITY 4        /* render: more (Gaussian, tile) pairs than max_pairs */
+#define PRTGS_STATUS_BAD_INDEX 8       /* an index outside its array was met and skipped */
+
+/* ---- flags of prtgs_transfer_params.flags ------------------------------------------- */
+#define PRTGS_SHADOW 1u  /* visibility V from the other Gaussians (else V = 1) */
+#define PRTGS_BOUNCE 2u  /* index matrix + one-bounce self-transfer, T becomes [N,3,C] */
+#define PRTGS_GLOSSY 4u  /* C x C transfer matrices for Gaussians with glossy_mask != 0 */
+
+/* ---- relight precision ---------------------------------------------------------------- */
+#define PRTGS_PREC_FP32 0   /* FP32 FMA on the CUDA cores */
+#define PRTGS_PREC_BF16X3 1 /* tensor cores (tcgen05), operands split into 3 BF16 terms, FP32 accumulate */
+#define PRTGS_PREC_BF16 2   /* tensor cores, plain BF16 operands, FP32 accumulate */
+
+/*
+ * Gaussian set (Sec. 3.1, Eq. 1-2; PBR attributes of Sec. 4.2-4.3).
+ *   means[n,3], scales[n,3] (standard deviations along the local axes, > 0),
+ *   quats[n,4] as (w,x,y,z) (normalised by the library), opacity[n] in [0,1),
+ *   normals[n,3] (unit), albedo[n,3], roughness[n] and metallic[n] (glossy only, may be
+ *   NULL otherwise), glossy_mask[n] uint8 (NULL = no glossy splats).
+ */
+typedef struct prtgs_gaussians {
+  int64_t n;
+  const float* means;
+  const float* scales;
+  const float* quats;
+  const float* opacity;
+  const float* normals;
+  const float* albedo;
+  const float* roughness;
+  const float* metallic;
+  const uint8_t* glossy_mask;
+} prtgs_gaussians;
+
+/*
+ * Linear BVH over the Gaussians' 3-sigma boxes (Sec. 4.4 "constructed upon the BVH"):
+ * one binary radix tree (Karras 2012) over 64-bit Morton keys, one subtree per scene.
+ * All pointers lie inside one caller buffer laid out by prtgs_bvh_init().
+ *   keys[n]        sorted keys: scene << 57 | morton30 << 27 | index within scene
+ *   order[n]       Gaussian index at each sorted position
+ *   nodes[n-1,16]  internal nodes: floats 0-5 box of child 0 (lo xyz, hi xyz), 6-11 box of
+ *                  child 1, then int32 child0, child1, parent, 0. A child >= 0 is an
+ *                  internal node, a child < 0 is the leaf at sorted position ~child.
+ *   records[n,16]  per sorted position: mean xyz, opacity, A = diag(1/s) R^T (9, row-major),
+ *                  normal xyz -- the traversal record
+ *   leaf_parent[n] parent node of each leaf (sorted position); -1 for a single-leaf scene
+ *   roots[n_scenes] root of each scene's subtree (same encoding as a child)
+ *   scene_offsets  device int64 [n_scenes+1], offsets of the scenes in the Gaussian arrays
+ */
+typedef struct prtgs_bvh {
+  int64_t n;
+  int32_t n_scenes;
+  int32_t reserved;
+  uint64_t* keys;
+  int32_t* order;
+  float* nodes;
+  float* records;
+  int32_t* leaf_parent;
+  int32_t* roots;
+  const int64_t* scene_offsets;
+} prtgs_bvh;
+
+/* Bytes needed for a BVH over n Gaussians in n_scenes scenes (host query). */
+size_t prtgs_bvh_bytes(int64_t n, int32_t n_scenes);
+
+/*
+ * Lay out a BVH in `buffer` (device, >= prtgs_bvh_bytes, 256-byte aligned). Host only;
+ * no GPU work. `scene_offsets` is a device int64 array [n_scenes+1] starting at 0 and
+ * ending at n; it must stay alive as long as the BVH is used. Scenes may hold at most
+ * 2^27 Gaussians each and n_scenes <= 128.
+ */
+int prtgs_bvh_init(void* buffer, size_t bytes, int64_t n, int32_t n_scenes, const int64_t* scene_offsets,
+                   prtgs_bvh* out);
+
+size_t prtgs_build_bvh_workspace_size(int64_t n, int32_t n_scenes);
+
+/*
+ * Build the BVH (Sec. 4.4): per-scene centre bounds, 30-bit Morton codes quantised in
+ * FP32 as q = min(floor((c - lo) * (1024 / (hi - lo))), 1023), an LSD radix sort, the
+ * Karras split search, traversal records and a bottom-up box refit. Keys, order and
+ * topology are deterministic and integer-exact. Boxes are conservative (padded 3-sigma
+ * boxes: half-extent_a = 3 sqrt(Sigma_aa) from Eq. 2). `status` (device int32, may be
+ * NULL) receives PRTGS_STATUS_NONFINITE for invalid Gaussians.
+ */
+int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* workspace,
+                    size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Transfer precompute parameters (Sec. 4.4-4.5).
+ *   sh_order        1..3 (C = (order+1)^2 coefficients)
+ *   n_dirs, dirs    S shared world-space directions [S,3] (device); weight 4 pi / S each
+ *   t_min           a ray stops once its transmittance falls below t_min (bounded error
+ *                   t_min per ray); 0 disables early exit. Suggested 2^-30.
+ *   same_surface_t  the Sec. 4.4 filter: a hit is eligible for the index matrix only if the
+ *                   transmittance in front of it is <= t; 1 disables the filter.
+ *   flags           PRTGS_SHADOW | PRTGS_BOUNCE | PRTGS_GLOSSY
+ */
+typedef struct prtgs_transfer_params {
+  int32_t sh_order;
+  int32_t n_dirs;
+  const float* dirs;
+  float t_min;
+  float same_surface_t;
+  uint32_t flags;
+  int32_t reserved;
+} prtgs_transfer_params;
+
+size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);
+
+/*
+ * Per-Gaussian radiance transfer (Eq. 29, Eq. 33, Eq. 40).
+ *  P[n,C]        out: P_i = sum_s (4 pi/S) V_is max(0, n_i.w_s) Y(w_s), with
+ *                V_is = prod over the other Gaussians j hit by the ray from mu_i along w_s
+ *                of (1 - opacity_j exp(-D_ij^2/2)); a hit is t* > 0 and D^2 <= 9, with t*
+ *                and D the closest approach of the ray to j in j's Mahalanobis metric
+ *                (Eq. 27 read as the Gaussian's maximum along the ray). Albedo and 1/pi are
+ *                applied at relight time.
+ *  T[n,3,C]      out (PRTGS_BOUNCE, else unused): T_i = P_i + sum_s (4 pi/S) max(0, n_i.w_s)
+ *                (albedo_j/pi) P_j, j = idx[i,s] (Eq. 33, one bounce).
+ *  idx[n,S]      out (required with PRTGS_BOUNCE, else unused): index matrix of Sec. 4.4:
+ *                the hit with the largest W_j = alpha_j prod_{before j}(1-alpha) max(0,-w.n_j)
+ *                (Eq. 26), -1 when no eligible hit has W > 0 or n_i.w_s <= 0.
+ *  M[n_glossy,C,C] out (PRTGS_GLOSSY): glossy transfer matrices (Eq. 40), in increasing
+ *                Gaussian order of the glossy splats:
+ *                M[a,b] = sum_s sum_o (4 pi/S)^2 Y_a(w_s) k(w_s,w_o) max(0,n.w_s) V_s Y_b(w_o),
+ *                k = (1-metallic) + pi D F G / (4 (n.w_s)(n.w_o)), zero for n.w_o <= 0.
+ *  status        device int32 word for PRTGS_STATUS_* bits (may be NULL).
+ * A BVH built from the same Gaussian arrays must be passed.
+ */
+int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                              float* P, float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status,
+                              void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Relight (Eq. 14; glossy Eq. 41):
+ *   colors[k,n,3] = (albedo_i/pi) * (T_i[c] . L[k,c,:]) per channel c,
+ * with T [n,C] (t_channels = 1) or [n,3,C] (t_channels = 3). Glossy splats (n_glossy > 0,
+ * glossy_ids[n_glossy] their Gaussian indices, M[n_glossy,C,C]) use
+ *   t_eff[a] = sum_b M[a,b] Y_b(v_i), v_i = normalize(cam_pos - mean_i).
+ * L[k,3,C] light SH per light and channel. precision: PRTGS_PREC_*. The tensor-core paths
+ * need t_channels = 1 and n_glossy = 0, otherwise PRTGS_ERR_UNSUPPORTED.
+ * cam_pos and means may be NULL when n_glossy == 0.
+ */
+size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision);
+int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                  int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* means,
+                  const float* cam_pos, const float* L, int32_t k, int32_t precision, float* colors,
+                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Relight backward (diffuse splats; glossy rows of dcolors must be zero or are ignored).
+ *   dcolors[k,n,3] in; d_albedo[n,3] out (overwritten); dT[n,t_channels,C] out (may be NULL);
+ *   dL[k,3,C] out (overwritten; deterministic two-pass reduction over n).
+ */
+size_t prtgs_relight_backward_workspace_size(int64_t n, int32_t sh_order, int32_t k);
+int prtgs_relight_backward(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                           const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                           void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Pinhole camera. world -> camera: x_c = rot * x_w + trans (rot row-major, camera x right,
+ * y down, z forward). Pixel (px,py) has its centre at (fx x_c/z_c + cx, fy y_c/z_c + cy).
+ */
+typedef struct prtgs_camera {
+  float rot[9];
+  float trans[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_plane;
+  float pos[3];
+} prtgs_camera;
+
+/*
+ * Render state: per-Gaussian projection results, the sorted (tile, depth) pairs and the
+ * per-pixel bookkeeping that the backward pass reuses. Lives in one caller buffer laid out
+ * by prtgs_render_state_init(); max_pairs bounds the number of (Gaussian, tile) pairs.
+ */
+typedef struct prtgs_render_state {
+  int64_t n;
+  int64_t max_pairs;
+  int32_t width, height, tiles_x, tiles_y;
+  float* mean2d;       /* [n,2] */
+  float* conic_op;     /* [n,4] conic a,b,c and opacity */
+  float* depth;        /* [n] */
+  int32_t* radius;     /* [n] (0 = culled) */
+  uint32_t* tiles_touched; /* [n] then inclusive prefix sums */
+  uint64_t* pair_keys; /* [max_pairs] tile << 32 | depth bits, sorted */
+  int32_t* pair_ids;   /* [max_pairs] Gaussian index per sorted pair */
+  uint32_t* ranges;    /* [tiles, 2] start, end of each tile's run of pairs */
+  float* final_T;      /* [H,W] */
+  int32_t* n_contrib;  /* [H,W] one past the last contributing pair of each pixel's tile list */
+  uint32_t* n_pairs;   /* [1] number of pairs produced */
+} prtgs_render_state;
+
+size_t prtgs_render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+int prtgs_render_state_init(void* buffer, size_t bytes, int64_t n, int32_t width, int32_t height,
+                            int64_t max_pairs, prtgs_render_state* out);
+size_t prtgs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+
+/*
+ * Splat render of k relit colour sets (Eq. 3 projection, Eq. 4 front-to-back blending;
+ * 3DGS rasteriser rules: near 0.2, 0.3 px^2 dilation, 3-sigma radius, 16x16 tiles,
+ * alpha = min(0.99, opacity e^power), skip alpha < 1/255, stop before T < 1e-4).
+ *   colors[k,n,3], bg[3] (device), image[k,3,H,W] out. The geometry is shared by the k
+ *   images; each pixel's blend is evaluated once for all k colour sets.
+ * status: PRTGS_STATUS_CAPACITY when max_pairs is exceeded (the image is then incomplete).
+ */
+int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                 const float* bg, float* image, prtgs_render_state* st, int32_t* status, void* workspace,
+                 size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Render backward: dimage[k,3,H,W] in; gradients out (overwritten): d_means[n,3],
+ * d_scales[n,3], d_quats[n,4], d_opacity[n], d_colors[k,n,3]. Uses the state written by the
+ * matching prtgs_render call. Gradients of the discrete decisions (culling, tile binning,
+ * skips, early stop) are zero; the alpha clamp at 0.99 has zero derivative.
+ */
+size_t prtgs_render_backward_workspace_size(int64_t n, int32_t k);
+int prtgs_render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                          const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,
+                          float* d_scales, float* d_quats, float* d_opacity, float* d_colors, void* workspace,
+                          size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * L2 image loss used by the differentiable relight: loss = mean((image - target)^2) and
+ * dimage = 2 (image - target) / count. loss[1], dimage[count] device outputs.
+ */
+size_t prtgs_l2_loss_workspace_size(int64_t count);
+int prtgs_l2_loss(const float* image, const float* target, int64_t count, float* loss, float* dimage,
+                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/* Read and clear a device status word (synchronises `stream`). Returns the bits or a
+ * negative PRTGS_ERR_* code. */
+int prtgs_read_status(int32_t* status, prtgs_stream_t stream);
+
+const char* prtgs_strerror(int code);
+int prtgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRTGS_H */

@@ -144,8 +144,8 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
     c = _cos_weights(scene, dirs, recv)
     traced = (tr["flags"] & RF_TRACED) != 0
     allow_P = (w * c * ynorm[None, :] * (tr["dV"] + np.where(traced, t_min, 0.0))).sum(axis=1)
-    res = dict(P=tr["P"], allow_P=allow_P, V=tr["V"], idx=tr["idx"], flags=tr["flags"], hits=tr["hits"],
-               traced=traced.sum(axis=1))
+    res = dict(P=tr["P"], allow_P=allow_P, V=tr["V"], dV=tr["dV"], idx=tr["idx"], flags=tr["flags"],
+               hits=tr["hits"], traced=traced.sum(axis=1))
     if not bounce:
         return res
     # receivers whose P is needed: every index-matrix entry, plus the alternatives of flagged rays

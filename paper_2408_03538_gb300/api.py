@@ -1,0 +1,323 @@
+"""PyTorch-facing wrappers of libprtgs (argument marshalling only).
+
+PyTorch supplies device memory (outputs and workspaces via the caching allocator) and the
+current CUDA stream; every step of the computation runs in the library's own kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+DEFAULT_T_MIN = 2.0 ** -30
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors passed to libprtgs must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ws(nbytes: int, device):
+    if nbytes == 0:
+        return None, 0
+    t = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+    return t, int(nbytes)
+
+
+def sh_count(order: int) -> int:
+    return (order + 1) ** 2
+
+
+@dataclass
+class GaussianTensors:
+    """Device SoA Gaussian set (FP32; glossy_mask uint8)."""
+
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opacity: torch.Tensor
+    normals: torch.Tensor
+    albedo: torch.Tensor
+    roughness: torch.Tensor = None
+    metallic: torch.Tensor = None
+    glossy_mask: torch.Tensor = None
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+    def struct(self) -> L.Gaussians:
+        return L.Gaussians(self.n, _ptr(self.means), _ptr(self.scales), _ptr(self.quats), _ptr(self.opacity),
+                           _ptr(self.normals), _ptr(self.albedo), _ptr(self.roughness), _ptr(self.metallic),
+                           _ptr(self.glossy_mask))
+
+    @staticmethod
+    def from_scene(scene, device="cuda"):
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return GaussianTensors(f(scene.means), f(scene.scales), f(scene.quats), f(scene.opacity), f(scene.normals),
+                               f(scene.albedo), f(scene.roughness), f(scene.metallic), f(scene.glossy_mask))
+
+    def with_(self, **kw):
+        d = dict(self.__dict__)
+        d.update(kw)
+        return GaussianTensors(**d)
+
+
+class Status:
+    """A device int32 status word (PRTGS_STATUS_* bits)."""
+
+    def __init__(self, device="cuda"):
+        self.t = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def ptr(self):
+        return _ptr(self.t)
+
+    def read(self) -> int:
+        rc = L.load().prtgs_read_status(self.ptr(), _stream())
+        if rc < 0:
+            L.check(rc, "prtgs_read_status")
+        return rc
+
+
+# ------------------------------------------------------------------------------------------
+# BVH
+# ------------------------------------------------------------------------------------------
+class Bvh:
+    def __init__(self, n: int, scene_offsets: torch.Tensor):
+        lib = L.load()
+        self.n = n
+        self.offsets = scene_offsets.to(dtype=torch.int64).contiguous()
+        self.n_scenes = int(self.offsets.numel() - 1)
+        nbytes = lib.prtgs_bvh_bytes(n, self.n_scenes)
+        self.buffer = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.offsets.device)
+        self.s = L.BVH()
+        L.check(lib.prtgs_bvh_init(_ptr(self.buffer), nbytes, n, self.n_scenes, _ptr(self.offsets),
+                                   ctypes.byref(self.s)), "prtgs_bvh_init")
+
+    def view(self, field, dtype, shape):
+        """Tensor view of one BVH array (for tests)."""
+        lib_ptr = getattr(self.s, field)
+        off = lib_ptr - self.buffer.data_ptr()
+        count = int(np.prod(shape))
+        nbytes = count * torch.empty(0, dtype=dtype).element_size()
+        return self.buffer[off:off + nbytes].view(dtype).view(*shape)
+
+
+def build_bvh(g: GaussianTensors, scene_offsets: torch.Tensor | None = None, status: Status | None = None) -> Bvh:
+    lib = L.load()
+    if scene_offsets is None:
+        scene_offsets = torch.tensor([0, g.n], dtype=torch.int64, device=g.means.device)
+    bvh = Bvh(g.n, scene_offsets)
+    ws, nb = _ws(lib.prtgs_build_bvh_workspace_size(g.n, bvh.n_scenes), g.means.device)
+    gs = g.struct()
+    L.check(lib.prtgs_build_bvh(ctypes.byref(gs), ctypes.byref(bvh.s), status.ptr() if status else None, _ptr(ws), nb,
+                                _stream()), "prtgs_build_bvh")
+    bvh._ws = ws  # keep alive until the stream has consumed it
+    return bvh
+
+
+# ------------------------------------------------------------------------------------------
+# Transfer
+# ------------------------------------------------------------------------------------------
+def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int, shadow: bool = True,
+                        bounce: bool = False, glossy: bool = False, t_min: float = DEFAULT_T_MIN,
+                        same_surface_t: float = 1.0, status: Status | None = None, out: dict | None = None):
+    """Transfer vectors P [n,C], and with ``bounce`` T [n,3,C] and idx [n,S]; with ``glossy``
+    the C x C matrices M [n_glossy,C,C] of the glossy splats (in increasing index order)."""
+    lib = L.load()
+    dev = g.means.device
+    S = int(dirs.shape[0])
+    C = sh_count(order)
+    flags = (L.SHADOW if shadow else 0) | (L.BOUNCE if bounce else 0) | (L.GLOSSY if glossy else 0)
+    n_glossy = int(g.glossy_mask.sum().item()) if glossy else 0
+    out = out or {}
+    P = out.get("P") if out.get("P") is not None else torch.empty((g.n, C), dtype=torch.float32, device=dev)
+    T = idx = M = None
+    if bounce:
+        T = out.get("T") if out.get("T") is not None else torch.empty((g.n, 3, C), dtype=torch.float32, device=dev)
+        idx = out.get("idx") if out.get("idx") is not None else torch.empty((g.n, S), dtype=torch.int32, device=dev)
+    if glossy:
+        M = torch.empty((max(n_glossy, 1), C, C), dtype=torch.float32, device=dev)
+    p = L.TransferParams(order, S, _ptr(dirs), float(t_min), float(same_surface_t), flags, 0)
+    ws, nb = _ws(lib.prtgs_transfer_workspace_size(g.n, n_glossy, ctypes.byref(p)), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_precompute_transfer(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(P), _ptr(T),
+                                          _ptr(idx), _ptr(M), n_glossy, status.ptr() if status else None, _ptr(ws),
+                                          nb, _stream()), "prtgs_precompute_transfer")
+    res = {"P": P, "_ws": ws}
+    if bounce:
+        res.update(T=T, idx=idx)
+    if glossy:
+        res.update(M=M[:n_glossy], n_glossy=n_glossy)
+    return res
+
+
+# ------------------------------------------------------------------------------------------
+# Relight
+# ------------------------------------------------------------------------------------------
+def relight(T: torch.Tensor, albedo: torch.Tensor, Lsh: torch.Tensor, order: int, precision: int = L.PREC_FP32,
+            glossy_ids=None, M=None, means=None, cam_pos=None, out=None):
+    """colors [k,n,3] = (albedo/pi) * (T . L_k) (Eq. 14; glossy Eq. 41)."""
+    lib = L.load()
+    n = int(T.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    k = int(Lsh.shape[0])
+    colors = out if out is not None else torch.empty((k, n, 3), dtype=torch.float32, device=T.device)
+    ng = int(glossy_ids.numel()) if glossy_ids is not None else 0
+    ws, nb = _ws(lib.prtgs_relight_workspace_size(n, order, k, precision), T.device)
+    L.check(lib.prtgs_relight(n, order, _ptr(T), tch, _ptr(albedo), ng, _ptr(glossy_ids), _ptr(M), _ptr(means),
+                              _ptr(cam_pos), _ptr(Lsh), k, precision, _ptr(colors), _ptr(ws), nb, _stream()),
+            "prtgs_relight")
+    return colors
+
+
+def relight_backward(T, albedo, Lsh, order, dcolors, need_dT=False):
+    lib = L.load()
+    n = int(T.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    k = int(Lsh.shape[0])
+    d_albedo = torch.empty_like(albedo)
+    dT = torch.empty_like(T) if need_dT else None
+    dL = torch.empty_like(Lsh)
+    ws, nb = _ws(lib.prtgs_relight_backward_workspace_size(n, order, k), T.device)
+    L.check(lib.prtgs_relight_backward(n, order, _ptr(T), tch, _ptr(albedo), _ptr(Lsh), k, _ptr(dcolors.contiguous()),
+                                       _ptr(d_albedo), _ptr(dT), _ptr(dL), _ptr(ws), nb, _stream()),
+            "prtgs_relight_backward")
+    return d_albedo, dT, dL
+
+
+# ------------------------------------------------------------------------------------------
+# Render
+# ------------------------------------------------------------------------------------------
+def camera_struct(cam) -> L.Camera:
+    c = L.Camera()
+    rot = np.asarray(cam.rot, dtype=np.float32).reshape(-1)
+    tr = np.asarray(cam.trans, dtype=np.float32).reshape(-1)
+    for i in range(9):
+        c.rot[i] = float(rot[i])
+    for i in range(3):
+        c.trans[i] = float(tr[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_plane = float(getattr(cam, "near", 0.2))
+    pos = cam.position if cam.position is not None else np.zeros(3)
+    for i in range(3):
+        c.pos[i] = float(pos[i])
+    return c
+
+
+class RenderState:
+    def __init__(self, n, width, height, max_pairs, device="cuda"):
+        lib = L.load()
+        self.n, self.width, self.height, self.max_pairs = n, width, height, int(max_pairs)
+        nbytes = lib.prtgs_render_state_bytes(n, width, height, self.max_pairs)
+        self.buffer = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        self.s = L.RenderState()
+        L.check(lib.prtgs_render_state_init(_ptr(self.buffer), nbytes, n, width, height, self.max_pairs,
+                                            ctypes.byref(self.s)), "prtgs_render_state_init")
+
+    def view(self, field, dtype, shape):
+        off = getattr(self.s, field) - self.buffer.data_ptr()
+        count = int(np.prod(shape))
+        nbytes = count * torch.empty(0, dtype=dtype).element_size()
+        return self.buffer[off:off + nbytes].view(dtype).view(*shape)
+
+    def n_pairs(self) -> int:
+        return int(self.view("n_pairs", torch.int32, (1,)).item())
+
+
+def render(g: GaussianTensors, colors: torch.Tensor, cam, bg: torch.Tensor, state: RenderState | None = None,
+           max_pairs: int | None = None, status: Status | None = None, out=None):
+    """image [k,3,H,W] (Eq. 3-4)."""
+    lib = L.load()
+    k = int(colors.shape[0])
+    if state is None:
+        state = RenderState(g.n, cam.width, cam.height, max_pairs or max(16 * g.n, 1 << 16), g.means.device)
+    image = out if out is not None else torch.empty((k, 3, cam.height, cam.width), dtype=torch.float32,
+                                                    device=g.means.device)
+    ws, nb = _ws(lib.prtgs_render_workspace_size(g.n, cam.width, cam.height, state.max_pairs), g.means.device)
+    gs = g.struct()
+    cs = camera_struct(cam)
+    L.check(lib.prtgs_render(ctypes.byref(gs), _ptr(colors), k, ctypes.byref(cs), _ptr(bg), _ptr(image),
+                             ctypes.byref(state.s), status.ptr() if status else None, _ptr(ws), nb, _stream()),
+            "prtgs_render")
+    state._ws = ws
+    return image, state
+
+
+def render_backward(g: GaussianTensors, colors, cam, bg, state: RenderState, dimage):
+    lib = L.load()
+    k = int(colors.shape[0])
+    dev = g.means.device
+    d_means = torch.empty_like(g.means)
+    d_scales = torch.empty_like(g.scales)
+    d_quats = torch.empty_like(g.quats)
+    d_opacity = torch.empty_like(g.opacity)
+    d_colors = torch.empty_like(colors)
+    ws, nb = _ws(lib.prtgs_render_backward_workspace_size(g.n, k), dev)
+    gs = g.struct()
+    cs = camera_struct(cam)
+    L.check(lib.prtgs_render_backward(ctypes.byref(gs), _ptr(colors), k, ctypes.byref(cs), _ptr(bg),
+                                      ctypes.byref(state.s), _ptr(dimage.contiguous()), _ptr(d_means), _ptr(d_scales),
+                                      _ptr(d_quats), _ptr(d_opacity), _ptr(d_colors), _ptr(ws), nb, _stream()),
+            "prtgs_render_backward")
+    return d_means, d_scales, d_quats, d_opacity, d_colors
+
+
+def l2_loss(image, target):
+    lib = L.load()
+    count = image.numel()
+    loss = torch.empty(1, dtype=torch.float32, device=image.device)
+    dimage = torch.empty_like(image)
+    ws, nb = _ws(lib.prtgs_l2_loss_workspace_size(count), image.device)
+    L.check(lib.prtgs_l2_loss(_ptr(image), _ptr(target), count, _ptr(loss), _ptr(dimage), _ptr(ws), nb, _stream()),
+            "prtgs_l2_loss")
+    return loss, dimage
+
+
+# ------------------------------------------------------------------------------------------
+# autograd: relit splat image as a function of the Gaussians and the light
+# ------------------------------------------------------------------------------------------
+class RelitRender(torch.autograd.Function):
+    """image = render(relight(T, albedo, L)) with the hand-written backward kernels.
+
+    Differentiable in means, scales, quats, opacity, albedo and the light SH; the
+    precomputed transfer T is a constant (the paper freezes geometry after ray tracing,
+    Sec. 4.4).
+    """
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, albedo, Lsh, T, normals, cam, order, bg, max_pairs):
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                            normals.contiguous(), albedo.contiguous())
+        colors = relight(T.contiguous(), g.albedo, Lsh.contiguous(), order)
+        image, state = render(g, colors, cam, bg, max_pairs=max_pairs)
+        ctx.save_for_backward(means, scales, quats, opacity, albedo, Lsh, T, normals, colors)
+        ctx.state, ctx.cam, ctx.order, ctx.bg = state, cam, order, bg
+        return image
+
+    @staticmethod
+    def backward(ctx, dimage):
+        means, scales, quats, opacity, albedo, Lsh, T, normals, colors = ctx.saved_tensors
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                            normals.contiguous(), albedo.contiguous())
+        dm, ds, dq, do, dcol = render_backward(g, colors, ctx.cam, ctx.bg, ctx.state, dimage.contiguous())
+        da, _, dL = relight_backward(T.contiguous(), g.albedo, Lsh.contiguous(), ctx.order, dcol)
+        return dm, ds, dq, do, da, dL, None, None, None, None, None, None
+
+
+def relit_render(means, scales, quats, opacity, albedo, Lsh, T, normals, cam, order, bg=None, max_pairs=None):
+    if bg is None:
+        bg = torch.zeros(3, dtype=torch.float32, device=means.device)
+    return RelitRender.apply(means, scales, quats, opacity, albedo, Lsh, T, normals, cam, order, bg, max_pairs)

@@ -1,0 +1,252 @@
+// extern "C" entry points of libprtgs: argument checks, workspace checks, dispatch.
+#include <stdint.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace prtgs;
+
+namespace {
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+int check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return PRTGS_OK;
+  if (!ws || have < need || !aligned256(ws)) return PRTGS_ERR_WORKSPACE;
+  return PRTGS_OK;
+}
+
+int check_gaussians(const prtgs_gaussians* g) {
+  if (!g || g->n < 0) return PRTGS_ERR_INVALID_ARG;
+  if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity)) return PRTGS_ERR_INVALID_ARG;
+  if (g->n >= (int64_t(1) << 31)) return PRTGS_ERR_UNSUPPORTED;
+  return PRTGS_OK;
+}
+
+int check_order(int32_t order) { return (order >= 1 && order <= 3) ? PRTGS_OK : PRTGS_ERR_UNSUPPORTED; }
+
+int finish(int rc) {
+  if (rc != PRTGS_OK) return rc;
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return PRTGS_ERR_CUDA;
+  }
+  return PRTGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prtgs_version(void) { return 10000; }
+
+const char* prtgs_strerror(int code) {
+  switch (code) {
+    case PRTGS_OK: return "ok";
+    case PRTGS_ERR_INVALID_ARG: return "invalid argument";
+    case PRTGS_ERR_SHAPE: return "inconsistent shapes";
+    case PRTGS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PRTGS_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case PRTGS_ERR_CUDA: return "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+int prtgs_read_status(int32_t* status, prtgs_stream_t stream) {
+  if (!status) return PRTGS_ERR_INVALID_ARG;
+  int32_t h = 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PRTGS_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return PRTGS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PRTGS_ERR_CUDA;
+  return h;
+}
+
+// ---- BVH ----
+size_t prtgs_bvh_bytes(int64_t n, int32_t n_scenes) {
+  if (n < 0 || n_scenes < 1) return 0;
+  return bvh_bytes(n, n_scenes);
+}
+
+int prtgs_bvh_init(void* buffer, size_t bytes, int64_t n, int32_t n_scenes, const int64_t* scene_offsets,
+                   prtgs_bvh* out) {
+  if (!out || n < 0 || n_scenes < 1 || !scene_offsets) return PRTGS_ERR_INVALID_ARG;
+  if (n_scenes > kMaxScenes) return PRTGS_ERR_UNSUPPORTED;
+  if (n > 0 && (!buffer || !aligned256(buffer) || bytes < bvh_bytes(n, n_scenes))) return PRTGS_ERR_WORKSPACE;
+  return bvh_layout(buffer, n, n_scenes, scene_offsets, out);
+}
+
+size_t prtgs_build_bvh_workspace_size(int64_t n, int32_t n_scenes) {
+  if (n < 0 || n_scenes < 1) return 0;
+  return build_bvh_workspace(n, n_scenes);
+}
+
+int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* workspace,
+                    size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!bvh || bvh->n != g->n || bvh->n_scenes < 1 || !bvh->scene_offsets) return PRTGS_ERR_SHAPE;
+  if (g->n > 0 && !g->normals) return PRTGS_ERR_INVALID_ARG;
+  if (g->n == 0) return PRTGS_OK;
+  rc = check_ws(workspace, workspace_bytes, build_bvh_workspace(g->n, bvh->n_scenes));
+  if (rc) return rc;
+  return finish(build_bvh(g, bvh, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"
+
+namespace prtgs {
+int transfer_check_dirs(int S);
+}
+
+extern "C" {
+
+// ---- transfer ----
+
+size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p) {
+  if (!p || n < 0 || n_glossy < 0) return 0;
+  return transfer_workspace(n, n_glossy, p);
+}
+
+int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                              float* P, float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status,
+                              void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
+  if ((rc = check_order(p->sh_order))) return rc;
+  if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
+  if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
+  if (g->n == 0) return PRTGS_OK;
+  if (!P || !g->normals) return PRTGS_ERR_INVALID_ARG;
+  if ((p->flags & PRTGS_BOUNCE) && (!T || !idx || !g->albedo)) return PRTGS_ERR_INVALID_ARG;
+  if (p->flags & PRTGS_GLOSSY) {
+    if (n_glossy < 0 || n_glossy > g->n) return PRTGS_ERR_SHAPE;
+    if (n_glossy > 0 && (!M || !g->glossy_mask || !g->roughness || !g->metallic)) return PRTGS_ERR_INVALID_ARG;
+  }
+  rc = check_ws(workspace, workspace_bytes, transfer_workspace(g->n, n_glossy, p));
+  if (rc) return rc;
+  return finish(precompute_transfer(g, bvh, p, P, T, idx, M, n_glossy, status, workspace,
+                                    reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---- relight ----
+size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision) {
+  if (n < 0 || k < 0) return 0;
+  return relight_workspace(n, sh_order, k, precision);
+}
+
+int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                  int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* means,
+                  const float* cam_pos, const float* L, int32_t k, int32_t precision, float* colors,
+                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc;
+  if (n < 0 || k < 0 || n_glossy < 0 || n_glossy > n) return PRTGS_ERR_SHAPE;
+  if ((rc = check_order(sh_order))) return rc;
+  if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
+  if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
+  if (n == 0 || k == 0) return PRTGS_OK;
+  if (!T || !albedo || !L || !colors) return PRTGS_ERR_INVALID_ARG;
+  if (n_glossy > 0 && (!glossy_ids || !M || !means || !cam_pos)) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, relight_workspace(n, sh_order, k, precision));
+  if (rc) return rc;
+  return finish(relight(n, sh_order, T, t_channels, albedo, n_glossy, glossy_ids, M, means, cam_pos, L, k, precision,
+                        colors, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_relight_backward_workspace_size(int64_t n, int32_t sh_order, int32_t k) {
+  if (n < 0 || k < 0 || check_order(sh_order)) return 0;
+  return relight_backward_workspace(n, sh_order, k);
+}
+
+int prtgs_relight_backward(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                           const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                           void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc;
+  if (n < 0 || k < 0) return PRTGS_ERR_SHAPE;
+  if ((rc = check_order(sh_order))) return rc;
+  if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
+  if (k == 0) return PRTGS_OK;
+  if (!dL || (n > 0 && (!T || !albedo || !L || !dcolors || !d_albedo))) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, relight_backward_workspace(n, sh_order, k));
+  if (rc) return rc;
+  return finish(relight_backward(n, sh_order, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, workspace,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---- render ----
+size_t prtgs_render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {
+  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0) return 0;
+  return render_state_bytes(n, width, height, max_pairs);
+}
+
+int prtgs_render_state_init(void* buffer, size_t bytes, int64_t n, int32_t width, int32_t height,
+                            int64_t max_pairs, prtgs_render_state* out) {
+  if (!out || n < 0 || width <= 0 || height <= 0 || max_pairs < 0) return PRTGS_ERR_INVALID_ARG;
+  if (max_pairs >= (int64_t(1) << 32)) return PRTGS_ERR_UNSUPPORTED;
+  if (!buffer || !aligned256(buffer) || bytes < render_state_bytes(n, width, height, max_pairs))
+    return PRTGS_ERR_WORKSPACE;
+  return render_state_layout(buffer, n, width, height, max_pairs, out);
+}
+
+size_t prtgs_render_workspace_size(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {
+  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0) return 0;
+  return render_workspace(n, width, height, max_pairs);
+}
+
+static int check_camera(const prtgs_camera* cam) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f))
+    return PRTGS_ERR_INVALID_ARG;
+  if ((int64_t)((cam->width + 15) / 16) * ((cam->height + 15) / 16) >= (int64_t(1) << 31))
+    return PRTGS_ERR_UNSUPPORTED;
+  return PRTGS_OK;
+}
+
+int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                 const float* bg, float* image, prtgs_render_state* st, int32_t* status, void* workspace,
+                 size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if ((rc = check_camera(cam))) return rc;
+  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (k < 1 || !bg || !image || (g->n > 0 && !colors)) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, render_workspace(g->n, cam->width, cam->height, st->max_pairs));
+  if (rc) return rc;
+  return finish(render(g, colors, k, cam, bg, image, st, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_render_backward_workspace_size(int64_t n, int32_t k) {
+  if (n < 0 || k < 1) return 0;
+  return render_backward_workspace(n, k);
+}
+
+int prtgs_render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                          const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,
+                          float* d_scales, float* d_quats, float* d_opacity, float* d_colors, void* workspace,
+                          size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if ((rc = check_camera(cam))) return rc;
+  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (k < 1 || !bg || !dimage) return PRTGS_ERR_INVALID_ARG;
+  if (g->n == 0) return PRTGS_OK;
+  if (!colors || !d_means || !d_scales || !d_quats || !d_opacity || !d_colors) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, render_backward_workspace(g->n, k));
+  if (rc) return rc;
+  return finish(render_backward(g, colors, k, cam, bg, st, dimage, d_means, d_scales, d_quats, d_opacity, d_colors,
+                                workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_l2_loss_workspace_size(int64_t count) { return count > 0 ? l2_loss_workspace(count) : 0; }
+
+int prtgs_l2_loss(const float* image, const float* target, int64_t count, float* loss, float* dimage,
+                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  if (count <= 0 || !image || !target || !loss || !dimage) return PRTGS_ERR_INVALID_ARG;
+  int rc = check_ws(workspace, workspace_bytes, l2_loss_workspace(count));
+  if (rc) return rc;
+  return finish(l2_loss(image, target, count, loss, dimage, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Shared device helpers of libprtgs (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/prtgs.h"
+
+#define PRTGS_CHECK_LAUNCH()                               \
+  do {                                                     \
+    if (cudaPeekAtLastError() != cudaSuccess) {            \
+      (void)cudaGetLastError();                            \
+      return PRTGS_ERR_CUDA;                               \
+    }                                                      \
+  } while (0)
+
+namespace prtgs {
+
+constexpr int kMaxC = 16;           // SH coefficients for order <= 3
+constexpr int kStackDepth = 64;     // binary radix tree over 64-bit keys: depth <= 64
+constexpr int kSceneShift = 57;     // key: scene << 57 | code << 27 | local index
+constexpr int kCodeShift = 27;
+constexpr int kMaxScenes = 128;
+constexpr int64_t kMaxScenePoints = int64_t(1) << 27;
+constexpr float kPi = 3.14159265358979323846f;
+
+__host__ __device__ inline int sh_count(int order) { return (order + 1) * (order + 1); }
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Carve aligned sub-buffers out of a workspace.
+struct Carver {
+  char* base;
+  size_t off;
+  explicit Carver(void* b) : base(static_cast<char*>(b)), off(0) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+__device__ inline void set_status(int32_t* status, int bits) {
+  if (status) atomicOr(status, bits);
+}
+
+// ---- real spherical harmonics, Cartesian form (l <= 3, Condon-Shortley phase, k = l*l+l+m)
+// The constants are sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the polynomial factors of
+// the associated Legendre functions, evaluated once in double precision.
+template <int ORDER>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
+  Y[0] = 0.28209479177387814f;
+  if (ORDER >= 1) {
+    Y[1] = -0.48860251190291992f * y;
+    Y[2] = 0.48860251190291992f * z;
+    Y[3] = -0.48860251190291992f * x;
+  }
+  if (ORDER >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);
+    if (ORDER >= 3) {
+      Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+      Y[10] = 2.8906114426405538f * x * y * z;
+      Y[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);
+      Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);
+      Y[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
+      Y[14] = 1.4453057213202769f * z * (xx - yy);
+      Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+    }
+  }
+}
+
+__device__ __forceinline__ void sh_eval_dyn(int order, float x, float y, float z, float* Y) {
+  switch (order) {
+    case 1: sh_eval<1>(x, y, z, Y); break;
+    case 2: sh_eval<2>(x, y, z, Y); break;
+    default: sh_eval<3>(x, y, z, Y); break;
+  }
+}
+
+// ---- error-free transformations (Knuth TwoSum) for compensated sums
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Neumaier-style compensated accumulator.
+struct CompSum {
+  float s, c;
+  __device__ __forceinline__ CompSum() : s(0.f), c(0.f) {}
+  __device__ __forceinline__ void add(float v) {
+    float t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// Warp sum of a compensated pair: the error terms are carried along.
+__device__ __forceinline__ float warp_comp_sum(float s, float c) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float so = __shfl_xor_sync(0xffffffffu, s, off);
+    float co = __shfl_xor_sync(0xffffffffu, c, off);
+    float t, e;
+    two_sum(s, so, t, e);
+    s = t;
+    c = c + co + e;
+  }
+  return s + c;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Order-preserving float <-> uint32 map for atomic min/max.
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Index of the scene that contains Gaussian `i` (offsets[0] = 0 <= i < offsets[B]).
+__device__ __forceinline__ int find_scene(const int64_t* offsets, int n_scenes, int64_t i) {
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace prtgs

@@ -1,0 +1,59 @@
+// Host-side launchers shared between the translation units of libprtgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/prtgs.h"
+
+namespace prtgs {
+
+// sort.cu
+size_t scan_workspace(int64_t n);
+int scan_u32(const uint32_t* in, uint32_t* out, int64_t n, bool exclusive, uint32_t* total, void* ws,
+             cudaStream_t stream);
+size_t radix_sort_workspace(int64_t capacity);
+int radix_sort_pairs(const uint64_t* keys_x, const int32_t* vals_x, uint64_t* keys_f, int32_t* vals_f,
+                     uint64_t* keys_y, int32_t* vals_y, int64_t capacity, const uint32_t* d_count, int begin_bit,
+                     int end_bit, void* ws, cudaStream_t stream);
+
+// bvh.cu
+size_t bvh_bytes(int64_t n, int32_t n_scenes);
+int bvh_layout(void* buffer, int64_t n, int32_t n_scenes, const int64_t* scene_offsets, prtgs_bvh* out);
+size_t build_bvh_workspace(int64_t n, int32_t n_scenes);
+int build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* ws, cudaStream_t stream);
+
+// transfer.cu
+size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);
+int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p, float* P,
+                        float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
+                        cudaStream_t stream);
+
+// relight.cu
+size_t relight_workspace(int64_t n, int32_t order, int32_t k, int32_t precision);
+int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
+            const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
+            int32_t k, int32_t precision, float* colors, void* ws, cudaStream_t stream);
+size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k);
+int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                     const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                     void* ws, cudaStream_t stream);
+
+// render.cu
+size_t render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+int render_state_layout(void* buffer, int64_t n, int32_t width, int32_t height, int64_t max_pairs,
+                        prtgs_render_state* out);
+size_t render_workspace(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+int render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam, const float* bg,
+           float* image, prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream);
+size_t render_backward_workspace(int64_t n, int32_t k);
+int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                    const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,
+                    float* d_scales, float* d_quats, float* d_opacity, float* d_colors, void* ws,
+                    cudaStream_t stream);
+size_t l2_loss_workspace(int64_t count);
+int l2_loss(const float* image, const float* target, int64_t count, float* loss, float* dimage, void* ws,
+            cudaStream_t stream);
+
+}  // namespace prtgs

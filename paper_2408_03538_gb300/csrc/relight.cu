@@ -1,0 +1,304 @@
+// Relight contraction (Eq. 14; glossy splats Eq. 41) and its backward pass.
+//
+// colors[k,i,c] = (rho_i[c] / pi) * sum_m T_i[c or 0][m] L[k,c,m]
+#include "common.cuh"
+#include "internal.h"
+
+namespace prtgs {
+
+constexpr int kRelightThreads = 256;
+constexpr int kMaxLightsSmem = 256;
+
+// One thread per Gaussian; the lights sit in shared memory.
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight(int64_t n, const float* __restrict__ T,
+                                                             const float* __restrict__ albedo,
+                                                             const float* __restrict__ L, int k,
+                                                             float* __restrict__ colors) {
+  extern __shared__ float sL[];  // [k][3][C]
+  for (int e = threadIdx.x; e < k * 3 * C; e += blockDim.x) sL[e] = L[e];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float t[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) t[c][m] = __ldg(T + (i * TCH + c) * C + m);
+  const float r0 = __ldg(albedo + 3 * i) * (1.0f / kPi);
+  const float r1 = __ldg(albedo + 3 * i + 1) * (1.0f / kPi);
+  const float r2 = __ldg(albedo + 3 * i + 2) * (1.0f / kPi);
+  for (int l = 0; l < k; ++l) {
+    const float* Ll = sL + l * 3 * C;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+      d0 = fmaf(t[0][m], Ll[m], d0);
+      d1 = fmaf(t[TCH > 1 ? 1 : 0][m], Ll[C + m], d1);
+      d2 = fmaf(t[TCH > 1 ? 2 : 0][m], Ll[2 * C + m], d2);
+    }
+    float* out = colors + ((int64_t)l * n + i) * 3;
+    out[0] = r0 * d0;
+    out[1] = r1 * d1;
+    out[2] = r2 * d2;
+  }
+}
+
+// Glossy splats: t_eff[a] = sum_b M[a,b] Y_b(v), v = normalize(cam - mu) (Eq. 41).
+template <int ORDER>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_glossy(int64_t n, int64_t n_glossy,
+                                                                    const int32_t* __restrict__ ids,
+                                                                    const float* __restrict__ M,
+                                                                    const float* __restrict__ means,
+                                                                    const float* __restrict__ cam,
+                                                                    const float* __restrict__ albedo,
+                                                                    const float* __restrict__ L, int k,
+                                                                    float* __restrict__ colors) {
+  constexpr int C = (ORDER + 1) * (ORDER + 1);
+  extern __shared__ float sL[];
+  for (int e = threadIdx.x; e < k * 3 * C; e += blockDim.x) sL[e] = L[e];
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_glossy) return;
+  const int64_t i = ids[g];
+  float vx = cam[0] - means[3 * i], vy = cam[1] - means[3 * i + 1], vz = cam[2] - means[3 * i + 2];
+  float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+  float Y[kMaxC];
+  sh_eval<ORDER>(vx * rn, vy * rn, vz * rn, Y);
+  float te[C];
+#pragma unroll
+  for (int a = 0; a < C; ++a) {
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b < C; ++b) acc = fmaf(__ldg(M + (g * C + a) * C + b), Y[b], acc);
+    te[a] = acc;
+  }
+  const float r0 = albedo[3 * i] * (1.0f / kPi), r1 = albedo[3 * i + 1] * (1.0f / kPi),
+              r2 = albedo[3 * i + 2] * (1.0f / kPi);
+  for (int l = 0; l < k; ++l) {
+    const float* Ll = sL + l * 3 * C;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+      d0 = fmaf(te[m], Ll[m], d0);
+      d1 = fmaf(te[m], Ll[C + m], d1);
+      d2 = fmaf(te[m], Ll[2 * C + m], d2);
+    }
+    float* out = colors + ((int64_t)l * n + i) * 3;
+    out[0] = r0 * d0;
+    out[1] = r1 * d1;
+    out[2] = r2 * d2;
+  }
+}
+
+size_t relight_workspace(int64_t, int32_t, int32_t, int32_t) { return 0; }
+
+template <int C>
+static void launch_relight_c(int64_t n, const float* T, int tch, const float* albedo, const float* L, int k,
+                             float* colors, cudaStream_t stream) {
+  size_t smem = sizeof(float) * k * 3 * C;
+  unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
+  if (tch == 3)
+    k_relight<C, 3><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
+  else
+    k_relight<C, 1><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
+}
+
+int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
+               int32_t precision, float* colors, void* ws, cudaStream_t stream);
+
+int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
+            const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
+            int32_t k, int32_t precision, float* colors, void* ws, cudaStream_t stream) {
+  if (n == 0 || k == 0) return PRTGS_OK;
+  if (k > kMaxLightsSmem) return PRTGS_ERR_UNSUPPORTED;
+  if (precision != PRTGS_PREC_FP32) {
+    if (t_channels != 1 || n_glossy > 0) return PRTGS_ERR_UNSUPPORTED;
+    return relight_tc(n, order, T, albedo, L, k, precision, colors, ws, stream);
+  }
+  switch (order) {
+    case 1: launch_relight_c<4>(n, T, t_channels, albedo, L, k, colors, stream); break;
+    case 2: launch_relight_c<9>(n, T, t_channels, albedo, L, k, colors, stream); break;
+    case 3: launch_relight_c<16>(n, T, t_channels, albedo, L, k, colors, stream); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
+  }
+  PRTGS_CHECK_LAUNCH();
+  if (n_glossy > 0) {
+    const int C = sh_count(order);
+    size_t smem = sizeof(float) * k * 3 * C;
+    unsigned grid = (unsigned)((n_glossy + kRelightThreads - 1) / kRelightThreads);
+    switch (order) {
+      case 1: k_relight_glossy<1><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
+                                                                          albedo, L, k, colors); break;
+      case 2: k_relight_glossy<2><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
+                                                                          albedo, L, k, colors); break;
+      default: k_relight_glossy<3><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means,
+                                                                           cam_pos, albedo, L, k, colors); break;
+    }
+    PRTGS_CHECK_LAUNCH();
+  }
+  return PRTGS_OK;
+}
+
+// ---- backward ------------------------------------------------------------------------------
+// Per Gaussian: d_albedo[c] = sum_k dc[k,i,c] (T_i[c].L_k[c]) / pi and
+// dT[c][m] = sum_k dc[k,i,c] (rho[c]/pi) L_k[c][m] (summed over c when T has one channel).
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_bwd_local(int64_t n, const float* __restrict__ T,
+                                                                       const float* __restrict__ albedo,
+                                                                       const float* __restrict__ L, int k,
+                                                                       const float* __restrict__ dcol,
+                                                                       float* __restrict__ d_albedo,
+                                                                       float* __restrict__ dT) {
+  extern __shared__ float sL[];
+  for (int e = threadIdx.x; e < k * 3 * C; e += blockDim.x) sL[e] = L[e];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float t[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) t[c][m] = __ldg(T + (i * TCH + c) * C + m);
+  float rho[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+  float da[3] = {0.f, 0.f, 0.f};
+  float gT[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) gT[c][m] = 0.f;
+  for (int l = 0; l < k; ++l) {
+    const float* Ll = sL + l * 3 * C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float g = __ldg(dcol + ((int64_t)l * n + i) * 3 + c);
+      float dot = 0.f;
+#pragma unroll
+      for (int m = 0; m < C; ++m) {
+        dot = fmaf(t[TCH > 1 ? c : 0][m], Ll[c * C + m], dot);
+        gT[TCH > 1 ? c : 0][m] = fmaf(g * rho[c], Ll[c * C + m], gT[TCH > 1 ? c : 0][m]);
+      }
+      da[c] = fmaf(g, dot, da[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d_albedo[3 * i + c] = da[c] * (1.0f / kPi);
+  if (dT) {
+#pragma unroll
+    for (int c = 0; c < TCH; ++c)
+#pragma unroll
+      for (int m = 0; m < C; ++m) dT[(i * TCH + c) * C + m] = gT[c][m];
+  }
+}
+
+// dL[k,c,m] = sum_i dc[k,i,c] (rho_i[c]/pi) T_i[c][m]: per-chunk partial sums (each block walks
+// its chunk of Gaussians in order), then a fixed-order sum of the partials: deterministic.
+constexpr int kDLChunk = 2048;
+constexpr int kDLBatch = 32;
+
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_dL_partial(int64_t n, const float* __restrict__ T,
+                                                                        const float* __restrict__ albedo, int k,
+                                                                        const float* __restrict__ dcol,
+                                                                        float* __restrict__ partial) {
+  __shared__ float sT[kDLBatch][TCH * C];
+  __shared__ float sW[kDLBatch][3 * 8];  // dc * rho / pi for up to 8 lights per pass
+  const int outs_per_light = 3 * C;
+  const int64_t i0 = (int64_t)blockIdx.x * kDLChunk;
+  for (int l0 = 0; l0 < k; l0 += 8) {
+    const int nl = min(8, k - l0);
+    const int nout = nl * outs_per_light;
+    float acc[2] = {0.f, 0.f};  // outputs tid and tid + 256 (nout <= 8*48 = 384)
+    for (int64_t b = i0; b < i0 + kDLChunk && b < n; b += kDLBatch) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kDLBatch * TCH * C; e += blockDim.x) {
+        int j = e / (TCH * C), r = e % (TCH * C);
+        int64_t i = b + j;
+        sT[j][r] = i < n ? T[i * TCH * C + r] : 0.f;
+      }
+      for (int e = threadIdx.x; e < kDLBatch * 3 * nl; e += blockDim.x) {
+        int j = e / (3 * nl), r = e % (3 * nl);
+        int l = r / 3, c = r % 3;
+        int64_t i = b + j;
+        sW[j][r] = i < n ? dcol[((int64_t)(l0 + l) * n + i) * 3 + c] * albedo[3 * i + c] * (1.0f / kPi) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        int o = threadIdx.x + q * kRelightThreads;
+        if (o < nout) {
+          int l = o / outs_per_light, r = o % outs_per_light;
+          int c = r / C, m = r % C;
+          float a = acc[q];
+          for (int j = 0; j < kDLBatch; ++j) a = fmaf(sW[j][3 * l + c], sT[j][(TCH > 1 ? c : 0) * C + m], a);
+          acc[q] = a;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int o = threadIdx.x + q * kRelightThreads;
+      if (o < nout) partial[(int64_t)blockIdx.x * k * outs_per_light + (int64_t)l0 * outs_per_light + o] = acc[q];
+    }
+  }
+}
+
+__global__ void k_sum_partials(const float* __restrict__ partial, int64_t nblocks, int nout, float* __restrict__ out) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  float s = 0.f, c = 0.f;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    float t, e;
+    two_sum(s, partial[b * nout + o], t, e);
+    s = t;
+    c += e;
+  }
+  out[o] = s + c;
+}
+
+size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k) {
+  int64_t nb = (n + kDLChunk - 1) / kDLChunk;
+  return align_up(sizeof(float) * (size_t)(nb > 0 ? nb : 1) * k * 3 * sh_count(order));
+}
+
+template <int C>
+static void launch_relight_bwd(int64_t n, const float* T, int tch, const float* albedo, const float* L, int k,
+                               const float* dcol, float* d_albedo, float* dT, float* dL, float* partial,
+                               cudaStream_t stream) {
+  size_t smem = sizeof(float) * k * 3 * C;
+  unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
+  int64_t nb = (n + kDLChunk - 1) / kDLChunk;
+  if (tch == 3) {
+    k_relight_bwd_local<C, 3><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
+    k_relight_dL_partial<C, 3><<<(unsigned)nb, kRelightThreads, 0, stream>>>(n, T, albedo, k, dcol, partial);
+  } else {
+    k_relight_bwd_local<C, 1><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
+    k_relight_dL_partial<C, 1><<<(unsigned)nb, kRelightThreads, 0, stream>>>(n, T, albedo, k, dcol, partial);
+  }
+  int nout = k * 3 * C;
+  k_sum_partials<<<(nout + 255) / 256, 256, 0, stream>>>(partial, nb, nout, dL);
+}
+
+int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                     const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                     void* ws, cudaStream_t stream) {
+  if (k == 0) return PRTGS_OK;
+  if (k > kMaxLightsSmem) return PRTGS_ERR_UNSUPPORTED;
+  if (n == 0) {
+    cudaMemsetAsync(dL, 0, sizeof(float) * k * 3 * sh_count(order), stream);
+    return PRTGS_OK;
+  }
+  float* partial = static_cast<float*>(ws);
+  switch (order) {
+    case 1: launch_relight_bwd<4>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 2: launch_relight_bwd<9>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 3: launch_relight_bwd<16>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
+  }
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
+}  // namespace prtgs

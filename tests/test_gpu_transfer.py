@@ -1,0 +1,204 @@
+"""GPU parity of the BVH build and the transfer precompute against the FP64 oracle.
+
+Tolerances (norm-wise per receiver, see oracle.transfer for the allowance):
+  ||P_gpu - P_ref|| <= 1e-4 * max(||P_ref||, 1e-3 * ||P_unoccluded||) + allow_P
+Integer outputs (Morton keys, sorted order, tree topology, index matrix on unflagged rays)
+are compared bit-exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_03538_gb300 import api, scenes as S
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def _gt(scene):
+    return api.GaussianTensors.from_scene(scene)
+
+
+def _offsets(sizes):
+    o = np.zeros(len(sizes) + 1, np.int64)
+    o[1:] = np.cumsum(sizes)
+    return torch.from_numpy(o).cuda()
+
+
+def _children_as_ids(children, order):
+    ch = children.copy()
+    leaf = ch < 0
+    ch[leaf] = -1 - order[~ch[leaf]]
+    return ch
+
+
+@pytest.mark.parametrize("sizes", [[1024], [1000], [2], [1], [5, 1, 40, 17], [300, 0, 299]])
+def test_bvh_bit_exact(sizes):
+    parts = [S.isotropic_scene(n, 100 + i + n) for i, n in enumerate(sizes)]
+    sc, offs = S.concat_scenes(parts)
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, torch.from_numpy(offs).cuda(), st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    ref = oracle.morton_lbvh(sc.means, offs)
+    n = sc.n
+    keys = bvh.view("keys", torch.int64, (n,)).cpu().numpy().view(np.uint64)
+    order = bvh.view("order", torch.int32, (n,)).cpu().numpy()
+    np.testing.assert_array_equal(keys, ref["keys"])
+    np.testing.assert_array_equal(order, ref["order"])
+    roots = bvh.view("roots", torch.int32, (len(sizes),)).cpu().numpy()
+    if n > 1:
+        nodes = bvh.view("nodes", torch.float32, (n - 1, 16)).cpu().numpy()
+        ch = nodes[:, 12:14].copy().view(np.int32)
+        np.testing.assert_array_equal(_children_as_ids(ch, order), ref["children"])
+        # every child box contains the exact FP64 3-sigma box of its subtree
+        box = oracle.aabb_3sigma(sc)
+        sub = np.zeros((2 * n - 1, 6))
+        lo_hi = {}
+
+        def subtree_box(c):
+            if c < 0:
+                return box[order[~c]]
+            if c in lo_hi:
+                return lo_hi[c]
+            a, b = subtree_box(int(ch[c, 0])), subtree_box(int(ch[c, 1]))
+            lo_hi[c] = np.concatenate([np.minimum(a[:3], b[:3]), np.maximum(a[3:], b[3:])])
+            return lo_hi[c]
+
+        import sys
+        sys.setrecursionlimit(10000)
+        for node in range(n - 1):
+            for slot in range(2):
+                bx = nodes[node, 6 * slot:6 * slot + 6].astype(np.float64)
+                ex = subtree_box(int(ch[node, slot]))
+                assert np.all(bx[:3] <= ex[:3]) and np.all(bx[3:] >= ex[3:])
+    for b, r in enumerate(ref["roots"]):
+        if sizes[b] == 0:
+            continue
+        rr = roots[b]
+        if rr < 0:
+            assert -1 - order[~rr] == r
+        else:
+            assert rr == r
+
+
+def _transfer_gpu(scene, dirs, order, bounce=False, glossy=False, t_min=api.DEFAULT_T_MIN):
+    g = _gt(scene)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    d = torch.from_numpy(dirs).cuda()
+    out = api.precompute_transfer(g, bvh, d, order, bounce=bounce, glossy=glossy, t_min=t_min, status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+
+
+def _check_norm(gpu, ref, allow, floor, tol=TOL):
+    err = np.linalg.norm((gpu - ref).reshape(len(ref), -1), axis=1)
+    lim = tol * np.maximum(np.linalg.norm(ref.reshape(len(ref), -1), axis=1), floor) + allow
+    bad = np.nonzero(err > lim)[0]
+    assert bad.size == 0, f"{bad.size} receivers over tolerance, worst {np.max(err / lim):.3g}x at {bad[:5]}"
+    return float(np.max(err / np.maximum(np.linalg.norm(ref.reshape(len(ref), -1), axis=1), floor)))
+
+
+def test_transfer_shadow_tiny_config_all_receivers():
+    """1,024 isotropic Gaussians, order 2, S = 64 (the plain-method tiny workload)."""
+    sc = S.make_scene("tiny-1k")
+    dirs = S.direction_set(64, S.config_seed(0))
+    out = _transfer_gpu(sc, dirs, 2)
+    ref = oracle.transfer(sc, dirs, 2, np.arange(sc.n))
+    floor = 1e-3 * oracle.unoccluded_norm(2)
+    _check_norm(out["P"], ref["P"], ref["allow_P"], floor)
+    assert np.mean(ref["hits"] / np.maximum(ref["traced"], 1)) > 5  # the workload really occludes
+
+
+def test_transfer_exact_without_early_exit_and_unshadowed():
+    sc = S.isotropic_scene(700, 5)
+    dirs = S.direction_set(96, 3)
+    out = _transfer_gpu(sc, dirs, 3, t_min=0.0)
+    ref = oracle.transfer(sc, dirs, 3, np.arange(sc.n), t_min=0.0)
+    _check_norm(out["P"], ref["P"], ref["allow_P"], 1e-3 * oracle.unoccluded_norm(3))
+    # without shadowing every receiver gets the discrete clamped-cosine projection
+    g = _gt(sc)
+    bvh = api.build_bvh(g)
+    P = api.precompute_transfer(g, bvh, torch.from_numpy(dirs).cuda(), 3, shadow=False)["P"].cpu().numpy()
+    refu = oracle.transfer(sc, dirs, 3, np.arange(sc.n), shadow=False)["P"]
+    np.testing.assert_allclose(P, refu, atol=2e-6, rtol=0)
+
+
+@pytest.mark.parametrize("n,order,nd", [(1, 2, 64), (2, 1, 32), (3, 3, 1), (33, 3, 100)])
+def test_transfer_edge_sizes(n, order, nd):
+    sc = S_mod_scene(n)
+    dirs = S_dirs(nd)
+    out = _transfer_gpu(sc, dirs, order, bounce=True)
+    ref = oracle.transfer(sc, dirs, order, np.arange(sc.n), bounce=True)
+    _check_norm(out["P"], ref["P"], ref["allow_P"], 1e-3 * oracle.unoccluded_norm(order))
+    _check_norm(out["T"], ref["T"], ref["allow_T"].max(axis=1), 1e-3 * oracle.unoccluded_norm(order))
+
+
+def S_mod_scene(n):
+    sc = S.isotropic_scene(n, 900 + n)
+    sc.means *= 0.2  # crowd them so that they occlude each other
+    return sc
+
+
+def S_dirs(k):
+    return S.direction_set(k, 17)
+
+
+def test_transfer_bounce_surface_scene():
+    """Anisotropic surface splats, order 3, S = 128, shadow + one bounce, every receiver."""
+    sc = S.surface_scene(3000, S.config_seed(1))
+    dirs = S.direction_set(128, S.config_seed(1))
+    out = _transfer_gpu(sc, dirs, 3, bounce=True)
+    ref = oracle.transfer(sc, dirs, 3, np.arange(sc.n), bounce=True)
+    floor = 1e-3 * oracle.unoccluded_norm(3)
+    _check_norm(out["P"], ref["P"], ref["allow_P"], floor)
+    _check_norm(out["T"], ref["T"], ref["allow_T"].max(axis=1), floor)
+    # index matrix: exact on every ray without a flagged decision
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    np.testing.assert_array_equal(out["idx"][clean], ref["idx"][clean])
+    assert clean.mean() > 0.99
+    assert np.mean(ref["idx"] >= 0) > 0.05  # the bounce term is exercised
+
+
+def test_transfer_full_size_sampled_receivers():
+    """The 100k-Gaussian surface workload (order 3, S = 256, shadow + bounce) on the GPU,
+    checked on seeded sampled receivers that the oracle computes one by one."""
+    sc = S.make_scene("surface-100k")
+    dirs = S.direction_set(256, S.config_seed(1))
+    out = _transfer_gpu(sc, dirs, 3, bounce=True)
+    rng = np.random.default_rng(4)
+    recv = np.sort(rng.choice(sc.n, size=12, replace=False))
+    ref = oracle.transfer(sc, dirs, 3, recv, bounce=True)
+    floor = 1e-3 * oracle.unoccluded_norm(3)
+    _check_norm(out["P"][recv], ref["P"], ref["allow_P"], floor)
+    _check_norm(out["T"][recv], ref["T"], ref["allow_T"].max(axis=1), floor)
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    np.testing.assert_array_equal(out["idx"][recv][clean], ref["idx"][clean])
+    # properties that hold everywhere: finite, idx in range, untraced rays have no index
+    assert np.all(np.isfinite(out["T"]))
+    assert out["idx"].min() >= -1 and out["idx"].max() < sc.n
+    c = sc.normals.astype(np.float64) @ dirs.astype(np.float64).T
+    assert np.all(out["idx"][c <= 0] == -1)
+
+
+def test_glossy_matrices():
+    sc = S.surface_scene(1500, 77)
+    rng = np.random.default_rng(5)
+    sc.glossy_mask = (rng.random(sc.n) < 0.3).astype(np.uint8)
+    sc.roughness = rng.uniform(0.1, 0.6, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    dirs = S.direction_set(64, 8)
+    out = _transfer_gpu(sc, dirs, 3, glossy=True)
+    gids = np.nonzero(sc.glossy_mask)[0]
+    assert out["n_glossy"] == gids.size
+    tr = oracle.transfer(sc, dirs, 3, gids)
+    Vallow = tr["dV"] + np.where((tr["flags"] & oracle.RF_TRACED) != 0, api.DEFAULT_T_MIN, 0.0)
+    M, allow = oracle.glossy(sc, dirs, 3, gids, tr["V"], Vallow)
+    floor = 1e-3 * np.median(np.linalg.norm(M.reshape(len(M), -1), axis=1))
+    _check_norm(out["M"], M, allow, floor)
