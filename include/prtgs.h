@@ -140,6 +140,11 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *   same_surface_t  the Sec. 4.4 filter: a hit is eligible for the index matrix only if the
  *                   transmittance in front of it is <= t; 1 disables the filter.
  *   flags           PRTGS_SHADOW | PRTGS_BOUNCE | PRTGS_GLOSSY
+ *   index_buffer    tuning: candidates per index-matrix search round (1, 2, 4 or 8; 0 = default)
+ *   stats           optional device uint64[6] that the call ADDS its work counters to:
+ *                   BVH node visits of the visibility walks, node visits of the index-matrix
+ *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays
+ *                   (NULL = not gathered)
  */
 typedef struct prtgs_transfer_params {
   int32_t sh_order;
@@ -148,7 +153,8 @@ typedef struct prtgs_transfer_params {
   float t_min;
   float same_surface_t;
   uint32_t flags;
-  int32_t reserved;
+  int32_t index_buffer;
+  unsigned long long* stats;
 } prtgs_transfer_params;
 
 size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);

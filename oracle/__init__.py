@@ -62,7 +62,7 @@ def _load():
         P = ctypes.c_void_p
         lib.oracle_sh.argtypes = [ctypes.c_int, ctypes.c_int64, P, P]
         lib.oracle_trace.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P, P]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P, P]
         lib.oracle_morton_lbvh.argtypes = [ctypes.c_int64, P, ctypes.c_int, P, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -96,8 +96,12 @@ def sh(order: int, dirs) -> np.ndarray:
 # ------------------------------------------------------------------------------------------
 # Transfer (Sec. 4.4-4.5)
 # ------------------------------------------------------------------------------------------
-def trace(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = False, filter_t: float = 1.0):
-    """Brute-force tracing for receivers ``recv``; see prtgs_oracle.c for the outputs."""
+def trace(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = False, filter_t: float = 1.0,
+          t_min: float = DEFAULT_T_MIN):
+    """Brute-force tracing for receivers ``recv``; see prtgs_oracle.c for the outputs.
+
+    Index-matrix candidates must have prefix transmittance >= t_min (the visibility cut-off);
+    t_min = 0 gives the unrestricted argmax of Sec. 4.4."""
     lib = _load()
     recv = np.ascontiguousarray(np.asarray(recv, dtype=np.int64).reshape(-1))
     dirs = _f32(dirs)
@@ -110,7 +114,7 @@ def trace(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = Fal
                cand=np.full((R, S, 4), -1, np.int32), flags=np.zeros((R, S), np.int32), dV=np.zeros((R, S)),
                hits=np.zeros(R))
     rc = lib.oracle_trace(m.shape[0], _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(nrm), S, _ptr(dirs), order,
-                          (1 if shadow else 0) | (2 if bounce else 0), float(filter_t), R, _ptr(recv),
+                          (1 if shadow else 0) | (2 if bounce else 0), float(filter_t), float(t_min), R, _ptr(recv),
                           _ptr(out["P"]), _ptr(out["V"]), _ptr(out["idx"]), _ptr(out["cand"]), _ptr(out["flags"]),
                           _ptr(out["dV"]), _ptr(out["hits"]))
     if rc != 0:
@@ -138,7 +142,7 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
     recv = np.asarray(recv, dtype=np.int64).reshape(-1)
     S = np.asarray(dirs).shape[0]
     w = 4.0 * math.pi / S
-    tr = trace(scene, dirs, order, recv, shadow, bounce, filter_t)
+    tr = trace(scene, dirs, order, recv, shadow, bounce, filter_t, t_min)
     Ys = sh(order, dirs)
     ynorm = np.linalg.norm(Ys, axis=1)
     c = _cos_weights(scene, dirs, recv)

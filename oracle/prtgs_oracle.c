@@ -177,6 +177,9 @@ static int hit_cmp(const void* pa, const void* pb) {
  * oracle_trace: brute-force tracing for a list of receivers.
  *
  * flags: bit0 = shadow (visibility), bit1 = bounce bookkeeping (weights, index matrix).
+ * Index-matrix candidates are the eligible hits whose prefix transmittance (the product in
+ * front of them) is at least t_min: hits behind a prefix below the visibility cut-off are
+ * not candidates (t_min = 0 gives the unrestricted argmax).
  * Outputs (n_recv rows):
  *   P[n_recv, C]         diffuse transfer vector, raw (no rho, no 1/pi)
  *   V[n_recv, S]         visibility per ray (0 for untraced rays, n.w <= 0)
@@ -188,7 +191,7 @@ static int hit_cmp(const void* pa, const void* pb) {
  */
 int oracle_trace(int64_t n, const float* means, const float* scales, const float* quats, const float* opacity,
                  const float* normals, int S, const float* dirs, int order, int flags, double filter_t,
-                 int64_t n_recv, const int64_t* recv, double* P, double* V, int32_t* idx, int32_t* cand,
+                 double t_min, int64_t n_recv, const int64_t* recv, double* P, double* V, int32_t* idx, int32_t* cand,
                  int32_t* ray_flags, double* dV, double* hits) {
   if (order < 0 || order > ORACLE_MAX_ORDER) return -3;
   const int C = (order + 1) * (order + 1);
@@ -265,38 +268,42 @@ int oracle_trace(int64_t n, const float* means, const float* scales, const float
 
       if ((flags & 2) && nh > 0) {
         qsort(hl, (size_t)nh, sizeof(Hit), hit_cmp);
-        double T = 1.0, wbest = 0.0;
+        /* W_j = alpha_j * prod_{earlier}(1 - alpha) * max(-d.n_j, 0) (Eq. 26), compared in the
+         * log domain so that deep prefix products cannot underflow; the argmax is the same. */
+        const double lfilter = log(filter_t);
+        const double lhorizon = t_min > 0 ? log(t_min) : -INFINITY;
+        double lT = 0.0, lwbest = -INFINITY;
         int64_t best = -1;
         int best_pos = -1;
-        double top[4] = {0, 0, 0, 0};
+        double top[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
         int64_t topj[4] = {-1, -1, -1, -1};
         int amb_arg = 0;
         for (int q = 0; q < nh; ++q) {
-          if (hl[q].ambiguous == 2) { amb_arg = amb_arg || (T > wbest); continue; }
+          if (hl[q].ambiguous == 2) { amb_arg = amb_arg || (lT > lwbest); continue; }
           const OG* gj = &g[hl[q].j];
           double m = -(d[0] * gj->n[0] + d[1] * gj->n[1] + d[2] * gj->n[2]);
-          if (m < 0) m = 0;
-          double W = hl[q].alpha * T * m;
-          int eligible = T <= filter_t;
-          if (filter_t < 1.0 && fabs(T - filter_t) <= 1e-5) amb_arg = 1;
-          if (eligible) {
-            if (W > wbest) { wbest = W; best = hl[q].j; best_pos = q; }
+          double lW = (m > 0 && hl[q].alpha > 0) ? log(hl[q].alpha) + lT + log(m) : -INFINITY;
+          int eligible = lT <= lfilter && lT >= lhorizon;
+          if (filter_t < 1.0 && fabs(lT - lfilter) <= 1e-5) amb_arg = 1;
+          if (t_min > 0 && fabs(lT - lhorizon) <= 1e-4 * fabs(lhorizon) + 1e-5) amb_arg = 1;
+          if (eligible && lW > -INFINITY) {
+            if (lW > lwbest) { lwbest = lW; best = hl[q].j; best_pos = q; }
             /* keep the 4 largest weights as alternative candidates */
             for (int a2 = 0; a2 < 4; ++a2) {
-              if (W > top[a2]) {
+              if (lW > top[a2]) {
                 for (int b2 = 3; b2 > a2; --b2) { top[b2] = top[b2 - 1]; topj[b2] = topj[b2 - 1]; }
-                top[a2] = W; topj[a2] = hl[q].j;
+                top[a2] = lW; topj[a2] = hl[q].j;
                 break;
               }
             }
           }
-          if (hl[q].ambiguous) amb_arg = amb_arg || (T > wbest * (1.0 - BAND_W_REL));
-          T *= (1.0 - hl[q].alpha);
+          if (hl[q].ambiguous) amb_arg = amb_arg || (lT > lwbest - BAND_W_REL);
+          lT += log1p(-hl[q].alpha);
         }
         idx[rs] = (int32_t)best;
         if (best >= 0) {
           /* near-tied runner-up */
-          if (top[1] > 0 && top[1] >= wbest * (1.0 - BAND_W_REL)) amb_arg = 1;
+          if (top[1] > -INFINITY && top[1] >= lwbest - BAND_W_REL) amb_arg = 1;
           /* near-equal hit distances up to just past the winner can reorder the prefix products */
           for (int q = 0; q + 1 < nh && q <= best_pos + 1; ++q) {
             double dt = fabs(hl[q + 1].t - hl[q].t);

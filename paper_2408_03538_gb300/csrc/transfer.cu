@@ -22,7 +22,7 @@ namespace prtgs {
 
 constexpr int kTraceWarps = 4;
 constexpr int kTraceThreads = 32 * kTraceWarps;
-constexpr int kKBuf = 8;
+constexpr int kDefaultIndexBuffer = 8;
 constexpr int kMaxDirs = 1024;
 
 struct TraceArgs {
@@ -45,7 +45,19 @@ struct TraceArgs {
   const int32_t* glossy_slot; // [n] slot of each Gaussian in Vg, -1 if none (nullable)
   int32_t* status;
   unsigned int* work;
+  unsigned long long* stats;  // nodes, leaves, hits, index rounds, traced rays (nullable)
+  int64_t r0, r1;             // receivers [r0, r1) of this batch, in sorted (Morton) positions
+  void* queue;                // rays with index-matrix candidates, resolved by k_resolve
+  unsigned int* queue_count;
 };
+
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned v) {
+  unsigned long long x = v;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
 
 struct Ray {
   float ox, oy, oz, dx, dy, dz;
@@ -144,98 +156,28 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, int 
   c1 = __float_as_int(n3.y);
 }
 
-// Unordered traversal: multiplies (1 - alpha) of every hit with key > (t_last, p_last) into
-// T, stopping early once T < t_min. Returns T.
-__device__ float trace_unordered(const TraceArgs& a, const Ray& r, int root, int self, float T, float t_last,
-                                 int p_last) {
-  float t, al, m;
-  const float t_prune = t_last * (1.0f - 1e-5f) - 1e-6f;
-  if (root < 0) {
-    int pos = ~root;
-    if (root != INT32_MIN && pos != self && gauss_hit(a.recs, pos, r, t, al, m) &&
-        (t > t_last || (t == t_last && pos > p_last)))
-      T *= 1.0f - al;
-    return T;
-  }
-  int stack[kStackDepth];
-  int sp = 0;
-  int node = root;
-  const int64_t max_visits = 2 * a.n + 64;
-  for (int64_t visits = 0;; ++visits) {
-    if (visits > max_visits) {
-      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
-      break;
-    }
-    float4 n0, n1, n2;
-    int c0, c1;
-    load_node(a.nodes, node, n0, n1, n2, c0, c1);
-    float tn0, tf0, tn1, tf1;
-    bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tn0, tf0) && tf0 >= t_prune && child_ok(c0, a.n, a.status);
-    bool h1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tn1, tf1) && tf1 >= t_prune && child_ok(c1, a.n, a.status);
-    if (h0 && c0 < 0) {
-      int pos = ~c0;
-      if (pos != self && gauss_hit(a.recs, pos, r, t, al, m) && (t > t_last || (t == t_last && pos > p_last)))
-        T *= 1.0f - al;
-      h0 = false;
-    }
-    if (h1 && c1 < 0) {
-      int pos = ~c1;
-      if (pos != self && gauss_hit(a.recs, pos, r, t, al, m) && (t > t_last || (t == t_last && pos > p_last)))
-        T *= 1.0f - al;
-      h1 = false;
-    }
-    if (T < a.t_min) break;
-    if (h0 && h1) {
-      bool first0 = tn0 <= tn1;
-      if (sp < kStackDepth) stack[sp++] = first0 ? c1 : c0;
-      else set_status(a.status, PRTGS_STATUS_STACK_OVERFLOW);
-      node = first0 ? c0 : c1;
-    } else if (h0) {
-      node = c0;
-    } else if (h1) {
-      node = c1;
-    } else {
-      if (sp == 0) break;
-      node = stack[--sp];
-    }
-  }
-  return T;
+// Per-ray work counters (only gathered when the caller asks for them).
+struct RayStats {
+  unsigned nodes, search_nodes, leaves, hits, rounds;
+};
+
+__device__ __forceinline__ bool key_less(float t0, int p0, float t1, int p1) {
+  return t0 < t1 || (t0 == t1 && p0 < p1);
 }
 
-// Sorted insertion of (t, pos, alpha, m) into the K-buffer; the largest entry drops out.
-__device__ __forceinline__ void kbuf_insert(float (&bt)[kKBuf], int (&bp)[kKBuf], float (&ba)[kKBuf],
-                                            float (&bm)[kKBuf], float t, int p, float al, float m) {
-#pragma unroll
-  for (int k = 0; k < kKBuf; ++k) {
-    bool less = (t < bt[k]) || (t == bt[k] && p < bp[k]);
-    if (less) {
-      float tt = bt[k]; bt[k] = t; t = tt;
-      int pp = bp[k]; bp[k] = p; p = pp;
-      float aa = ba[k]; ba[k] = al; al = aa;
-      float mm = bm[k]; bm[k] = m; m = mm;
-    }
-  }
-}
-
-// One ordered pass: the K nearest hits with key > (t_last, p_last).
-__device__ void trace_kbuf(const TraceArgs& a, const Ray& r, int root, int self, float t_last, int p_last,
-                           float (&bt)[kKBuf], int (&bp)[kKBuf], float (&ba)[kKBuf], float (&bm)[kKBuf]) {
-#pragma unroll
-  for (int k = 0; k < kKBuf; ++k) {
-    bt[k] = FLT_MAX;
-    bp[k] = INT32_MAX;
-    ba[k] = 0.f;
-    bm[k] = 0.f;
-  }
-  float t, al, m;
-  const float t_lo = t_last * (1.0f - 1e-5f) - 1e-6f;
+// Depth-first traversal of one scene's subtree. Children are visited when the ray's slab
+// interval overlaps [t_lo, vis.t_hi()]; leaves are handed to vis.leaf(pos); the walk ends
+// when vis.stop() turns true. Leaf children are handled at their parent, so only internal
+// nodes go on the stack.
+template <class Vis>
+__device__ __forceinline__ void traverse(const TraceArgs& a, const Ray& r, int root, float t_lo, Vis& vis,
+                                         RayStats& st, unsigned& node_count) {
+  if (root == INT32_MIN) return;
   if (root < 0) {
-    int pos = ~root;
-    if (root != INT32_MIN && pos != self && gauss_hit(a.recs, pos, r, t, al, m) &&
-        (t > t_last || (t == t_last && pos > p_last)))
-      kbuf_insert(bt, bp, ba, bm, t, pos, al, m);
+    vis.leaf(~root);
     return;
   }
+  const float prune_lo = t_lo > 0.f ? t_lo * (1.0f - 1e-5f) - 1e-6f : -FLT_MAX;
   int stack[kStackDepth];
   int sp = 0;
   int node = root;
@@ -248,24 +190,22 @@ __device__ void trace_kbuf(const TraceArgs& a, const Ray& r, int root, int self,
     float4 n0, n1, n2;
     int c0, c1;
     load_node(a.nodes, node, n0, n1, n2, c0, c1);
-    const float t_hi = bt[kKBuf - 1] == FLT_MAX ? FLT_MAX : bt[kKBuf - 1] * (1.0f + 1e-5f) + 1e-6f;
+    ++node_count;
+    const float th = vis.t_hi();
     float tn0, tf0, tn1, tf1;
-    bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tn0, tf0) && tf0 >= t_lo && tn0 <= t_hi &&
+    bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tn0, tf0) && tf0 >= prune_lo && tn0 <= th &&
               child_ok(c0, a.n, a.status);
-    bool h1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tn1, tf1) && tf1 >= t_lo && tn1 <= t_hi &&
+    bool h1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tn1, tf1) && tf1 >= prune_lo && tn1 <= th &&
               child_ok(c1, a.n, a.status);
     if (h0 && c0 < 0) {
-      int pos = ~c0;
-      if (pos != self && gauss_hit(a.recs, pos, r, t, al, m) && (t > t_last || (t == t_last && pos > p_last)))
-        kbuf_insert(bt, bp, ba, bm, t, pos, al, m);
+      vis.leaf(~c0);
       h0 = false;
     }
     if (h1 && c1 < 0) {
-      int pos = ~c1;
-      if (pos != self && gauss_hit(a.recs, pos, r, t, al, m) && (t > t_last || (t == t_last && pos > p_last)))
-        kbuf_insert(bt, bp, ba, bm, t, pos, al, m);
+      vis.leaf(~c1);
       h1 = false;
     }
+    if (vis.stop()) break;
     if (h0 && h1) {
       bool first0 = tn0 <= tn1;
       if (sp < kStackDepth) stack[sp++] = first0 ? c1 : c0;
@@ -282,46 +222,219 @@ __device__ void trace_kbuf(const TraceArgs& a, const Ray& r, int root, int self,
   }
 }
 
-// Visibility and (optionally) the index-matrix entry of one ray.
-template <bool BOUNCE>
-__device__ float trace_ray(const TraceArgs& a, const Ray& r, int root, int self, int& best) {
-  best = -1;
-  if (!BOUNCE) return trace_unordered(a, r, root, self, 1.0f, -FLT_MAX, INT32_MIN);
-  float T = 1.0f, wbest = 0.0f;
-  float t_last = -FLT_MAX;
-  int p_last = INT32_MIN;
-  float bt[kKBuf], ba[kKBuf], bm[kKBuf];
-  int bp[kKBuf];
-  for (int64_t pass = 0;; ++pass) {
-    if (pass > a.n / kKBuf + 1) {  // every pass consumes kKBuf hits
-      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
-      return T;
+// Visibility: product of (1 - alpha) over every hit, in any order; stops below t_min.
+struct ShadowVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float T;
+  __device__ float t_hi() const { return FLT_MAX; }
+  __device__ bool stop() const { return T < a.t_min; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (gauss_hit(a.recs, pos, r, t, al, m)) {
+      ++st.hits;
+      T *= 1.0f - al;
     }
-    trace_kbuf(a, r, root, self, t_last, p_last, bt, bp, ba, bm);
-#pragma unroll
-    for (int k = 0; k < kKBuf; ++k) {
-      if (bt[k] == FLT_MAX) break;
-      float W = ba[k] * T * bm[k];
-      if (T <= a.filter_t && W > wbest) {
-        wbest = W;
-        best = bp[k];
-      }
-      T *= 1.0f - ba[k];
-    }
-    if (bt[kKBuf - 1] == FLT_MAX) return T;  // every hit seen
-    t_last = bt[kKBuf - 1];
-    p_last = bp[kKBuf - 1];
-    if (T < a.t_min) return T;
-    if (T <= wbest) break;  // no later hit can outweigh the current best (W_later <= T)
   }
-  return trace_unordered(a, r, root, self, T, t_last, p_last);
+};
+
+// Sorted K-buffer of front-facing hits (max(-d.n_j, 0) > 0), keyed by (t*, position).
+template <int KB>
+struct FrontBuf {
+  float bt[KB], ba[KB], bm[KB];
+  int bp[KB];
+  __device__ void clear() {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      bt[k] = FLT_MAX;
+      bp[k] = INT32_MAX;
+      ba[k] = 0.f;
+      bm[k] = 0.f;
+    }
+  }
+  __device__ float t_full() const { return bt[KB - 1]; }
+  __device__ void insert(float t, int p, float al, float m) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (key_less(t, p, bt[k], bp[k])) {
+        float tt = bt[k]; bt[k] = t; t = tt;
+        int pp = bp[k]; bp[k] = p; p = pp;
+        float aa = ba[k]; ba[k] = al; al = aa;
+        float mm = bm[k]; bm[k] = m; m = mm;
+      }
+    }
+  }
+  __device__ int count() const {
+    int nc = 0;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) nc += bt[k] != FLT_MAX ? 1 : 0;
+    return nc;
+  }
+};
+
+// A ray whose visibility walk left index-matrix candidates: resolved by k_resolve.
+template <int KB>
+struct QueueRec {
+  int self;
+  int s;
+  float t_hor;
+  int pad;
+  FrontBuf<KB> fb;
+};
+
+__device__ __forceinline__ float slack_hi(float t) { return t == FLT_MAX ? FLT_MAX : t * (1.0f + 1e-5f) + 1e-6f; }
+
+// Visibility walk of the bounce mode. Until T < t_min it multiplies every hit into T (in
+// any order, as ShadowVis) and keeps the KB nearest front-facing hits. At the cut-off it
+// records the horizon: the largest t* met so far; every hit past it has a prefix
+// transmittance below t_min, so it is no index-matrix candidate. The same walk then goes on,
+// pruned to the horizon (and to the KB-th candidate), so that the buffer ends up holding the
+// KB nearest front-facing hits of the whole ray within the horizon.
+template <int KB>
+struct ShadowFrontVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float T;
+  float t_seen;
+  float t_hor;
+  FrontBuf<KB> fb;
+  __device__ float t_hi() const {
+    return T < a.t_min ? fminf(slack_hi(t_hor), slack_hi(fb.t_full())) : FLT_MAX;
+  }
+  __device__ bool stop() const { return false; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    if (!(T < a.t_min)) {
+      T *= 1.0f - al;
+      t_seen = fmaxf(t_seen, t);
+      if (T < a.t_min) t_hor = t_seen;
+    } else if (t > t_hor) {
+      return;
+    }
+    if (m > 0.f) fb.insert(t, pos, al, m);
+  }
+};
+
+// Index-matrix round, part A: the KB nearest front-facing hits with key greater than the
+// previous round's last candidate and t* within the horizon.
+template <int KB>
+struct FrontVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float t_last;
+  int p_last;
+  float t_hor;
+  FrontBuf<KB> fb;
+  __device__ float t_hi() const { return fminf(slack_hi(fb.t_full()), slack_hi(t_hor)); }
+  __device__ bool stop() const { return false; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    if (!(m > 0.f) || !key_less(t_last, p_last, t, pos)) return;
+    fb.insert(t, pos, al, m);
+  }
+};
+
+// Index-matrix round, part B: log prefix transmittance in front of each candidate,
+// lt[j] += log(1 - alpha_k) for every hit k with previous-last < key_k < key_j.
+template <int KB>
+struct PrefixVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float t_last;
+  int p_last;
+  const FrontBuf<KB>& fb;
+  int nc;
+  float lt[KB];
+  __device__ float t_hi() const { return slack_hi(fb.bt[nc - 1]); }
+  __device__ bool stop() const { return false; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    if (!key_less(t_last, p_last, t, pos)) return;
+    const float l = log1pf(-al);
+#pragma unroll
+    for (int j = 0; j < KB; ++j)
+      if (j < nc && key_less(t, pos, fb.bt[j], fb.bp[j])) lt[j] += l;
+  }
+};
+
+// Index-matrix entry of one ray (Sec. 4.4): argmax_j W_j, W_j = alpha_j T_j max(-d.n_j, 0)
+// (Eq. 26), over eligible hits (T_j <= the same-surface threshold) whose prefix
+// transmittance T_j is at least t_min, compared as logarithms. Rounds of (A, B) walk the
+// front-facing hits in key order, KB at a time, until the prefix past the last candidate
+// cannot exceed the best weight or falls below t_min. Round 0 reuses the candidates of the
+// visibility walk when that walk saw every hit.
+template <int KB>
+__device__ int index_search(const TraceArgs& a, const Ray& r, int root, int self, RayStats& st, bool complete,
+                            float t_hor, const FrontBuf<KB>* seed, float t_last, int p_last, float lt_base,
+                            int best, float lw_best) {
+  const float lfilter = logf(a.filter_t);
+  const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
+  for (int64_t round = 0;; ++round) {
+    if (round > a.n / KB + 1) {  // every full round consumes KB front-facing hits
+      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+      break;
+    }
+    FrontVis<KB> fa{a, r, self, st, t_last, p_last, t_hor};
+    if (round == 0 && complete && seed) {
+      fa.fb = *seed;
+    } else {
+      ++st.rounds;
+      fa.fb.clear();
+      traverse(a, r, root, t_last, fa, st, st.search_nodes);
+    }
+    const int nc = fa.fb.count();
+    if (nc == 0) break;
+    PrefixVis<KB> pb{a, r, self, st, t_last, p_last, fa.fb, nc};
+#pragma unroll
+    for (int k = 0; k < KB; ++k) pb.lt[k] = lt_base;
+    traverse(a, r, root, t_last, pb, st, st.search_nodes);
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (k < nc && pb.lt[k] <= lfilter && pb.lt[k] >= lmin) {
+        float lw = logf(fa.fb.ba[k]) + pb.lt[k] + logf(fa.fb.bm[k]);
+        if (lw > lw_best) {
+          lw_best = lw;
+          best = fa.fb.bp[k];
+        }
+      }
+    }
+    if (nc < KB) break;  // no front-facing hit left within the horizon
+    const float lt_next = pb.lt[KB - 1] + log1pf(-fa.fb.ba[KB - 1]);
+    if (lt_next <= lw_best || lt_next < lmin) break;  // later W_j <= T_j < T_next
+    t_last = fa.fb.bt[KB - 1];
+    p_last = fa.fb.bp[KB - 1];
+    lt_base = lt_next;
+  }
+  return best;
 }
 
 __device__ __forceinline__ float ray_cos(float nx, float ny, float nz, const float* d) {
   return fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));
 }
 
-template <bool BOUNCE>
+template <bool BOUNCE, int KB>
 __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   extern __shared__ float smem[];
   float* sdir = smem;                                     // [S*3]
@@ -340,8 +453,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     unsigned int w = 0;
     if (lane == 0) w = atomicAdd(a.work, 1u);
     w = __shfl_sync(0xffffffffu, w, 0);
-    if ((int64_t)w >= a.n) break;
-    const int self = (int)w;  // receivers are visited in sorted (Morton) order
+    if ((int64_t)w >= a.r1 - a.r0) break;
+    const int self = (int)(a.r0 + w);  // receivers are visited in sorted (Morton) order
     const float4 q0 = __ldg(a.recs + 4 * self);
     const float4 q3 = __ldg(a.recs + 4 * self + 3);
     const int gid = a.order[self];
@@ -363,17 +476,42 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
     if (lane == 0) s_next[warp] = 0;
     __syncwarp();
     // lanes pull rays until the list is exhausted
+    RayStats rs{0u, 0u, 0u, 0u, 0u};
     for (;;) {
       unsigned int t = atomicAdd(&s_next[warp], 1u);
       if ((int)t >= cnt) break;
       int s = list[t];
       Ray r;
       make_ray(r, q0.x, q0.y, q0.z, sdir[3 * s], sdir[3 * s + 1], sdir[3 * s + 2]);
-      int best = -1;
       float V = 1.0f;
-      if (a.flags & PRTGS_SHADOW) V = trace_ray<BOUNCE>(a, r, root, self, best);
+      if (a.flags & PRTGS_SHADOW) {
+        if (BOUNCE) {
+          ShadowFrontVis<KB> sv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX};
+          sv.fb.clear();
+          traverse(a, r, root, 0.0f, sv, rs, rs.nodes);
+          V = sv.T;
+          // the buffer holds the KB nearest front-facing hits within the horizon; rays with
+          // candidates go to the queue that k_resolve works through
+          if (sv.fb.count() == 0) {
+            a.idx[(int64_t)gid * a.S + s] = -1;
+          } else {
+            unsigned slot = atomicAdd(a.queue_count, 1u);
+            QueueRec<KB>* q = static_cast<QueueRec<KB>*>(a.queue) + slot;
+            q->self = self;
+            q->s = s;
+            q->t_hor = sv.t_hor;
+            q->pad = 0;
+            q->fb = sv.fb;
+          }
+        } else {
+          ShadowVis sv{a, r, self, rs, 1.0f};
+          traverse(a, r, root, 0.0f, sv, rs, rs.nodes);
+          V = sv.T;
+        }
+      } else if (BOUNCE) {
+        a.idx[(int64_t)gid * a.S + s] = -1;
+      }
       vis[s] = V;
-      if (BOUNCE) a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
     }
     __syncwarp();
     // SH projection of V (n.w)^+ with a compensated sum per lane, then across the warp
@@ -406,12 +544,58 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       }
     }
     if (lane < C) a.P[(int64_t)gid * C + lane] = mine;
+    if (a.stats) {
+      unsigned long long c0 = warp_sum_u64(rs.nodes), c1 = warp_sum_u64(rs.search_nodes),
+                         c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits), c4 = warp_sum_u64(rs.rounds);
+      if (lane == 0) {
+        atomicAdd(a.stats + 0, c0);
+        atomicAdd(a.stats + 1, c1);
+        atomicAdd(a.stats + 2, c2);
+        atomicAdd(a.stats + 3, c3);
+        atomicAdd(a.stats + 4, c4);
+        atomicAdd(a.stats + 5, (unsigned long long)cnt);
+      }
+    }
     if (a.Vg) {
       int slot = a.glossy_slot[gid];
       if (slot >= 0)
         for (int s = lane; s < a.S; s += 32) a.Vg[(int64_t)slot * a.S + s] = vis[s];
     }
     __syncwarp();
+  }
+}
+
+// Index-matrix entries of the queued rays: one thread per ray.
+template <int KB>
+__global__ void __launch_bounds__(128) k_resolve(TraceArgs a) {
+  const unsigned count = *a.queue_count;
+  RayStats rs{0u, 0u, 0u, 0u, 0u};
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    const QueueRec<KB> rec = static_cast<const QueueRec<KB>*>(a.queue)[q];
+    const int self = rec.self, s = rec.s;
+    if (self < 0 || (int64_t)self >= a.n || s < 0 || s >= a.S) {
+      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+      continue;
+    }
+    const float4 q0 = __ldg(a.recs + 4 * self);
+    const int gid = a.order[self];
+    int root = a.roots[find_scene(a.offsets, a.n_scenes, gid)];
+    if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
+    Ray r;
+    make_ray(r, q0.x, q0.y, q0.z, __ldg(a.dirs + 3 * s), __ldg(a.dirs + 3 * s + 1), __ldg(a.dirs + 3 * s + 2));
+    const int best = index_search<KB>(a, r, root, self, rs, true, rec.t_hor, &rec.fb, -FLT_MAX, INT32_MIN, 0.0f,
+                                      -1, -FLT_MAX);
+    a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
+  }
+  if (a.stats) {
+    unsigned long long c1 = warp_sum_u64(rs.search_nodes), c2 = warp_sum_u64(rs.leaves),
+                       c3 = warp_sum_u64(rs.hits), c4 = warp_sum_u64(rs.rounds);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(a.stats + 1, c1);
+      atomicAdd(a.stats + 2, c2);
+      atomicAdd(a.stats + 3, c3);
+      atomicAdd(a.stats + 4, c4);
+    }
   }
 }
 
@@ -469,10 +653,15 @@ __device__ __forceinline__ float brdf_kernel(float nx, float ny, float nz, const
                                              float ni, float no, float alpha, float metal) {
   float hx = wi[0] + wo[0], hy = wi[1] + wo[1], hz = wi[2] + wo[2];
   float rh = rsqrtf(fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
-  float nh = fmaf(nx, hx, fmaf(ny, hy, nz * hz)) * rh;
-  float oh = fminf(fmaxf(fmaf(wo[0], hx, fmaf(wo[1], hy, wo[2] * hz)) * rh, 0.f), 1.f);
+  hx *= rh; hy *= rh; hz *= rh;
+  float nh = fmaf(nx, hx, fmaf(ny, hy, nz * hz));
+  float oh = fminf(fmaxf(fmaf(wo[0], hx, fmaf(wo[1], hy, wo[2] * hz)), 0.f), 1.f);
+  // GGX denominator nh^2 (a^2 - 1) + 1 written as a^2 nh^2 + |n x h|^2: no cancellation
+  // near the lobe peak, where 1 - nh^2 is tiny.
+  float cx = ny * hz - nz * hy, cy = nz * hx - nx * hz, cz = nx * hy - ny * hx;
+  float s2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
   float a2 = alpha * alpha;
-  float den = fmaf(nh * nh, a2 - 1.0f, 1.0f);
+  float den = fmaf(a2 * nh, nh, s2);
   float D = a2 / (kPi * den * den);
   float x = 1.0f - oh;
   float x2 = x * x;
@@ -569,14 +758,48 @@ __global__ void k_mask_u32(int64_t n, const uint8_t* __restrict__ mask, uint32_t
 static size_t trace_smem(int S) { return sizeof(float) * 3 * S + kTraceWarps * S * (sizeof(float) + 2); }
 static size_t glossy_smem(int S, int C) { return sizeof(float) * (3 * S + 3 * (size_t)S * C); }
 
+// Receivers per batch: the resolve queue holds at most batch * S rays.
+static int64_t trace_batch(int64_t n, int S) {
+  int64_t b = (int64_t(1) << 24) / (S > 0 ? S : 1);
+  if (b < 1) b = 1;
+  return b < n ? b : n;
+}
+
+static size_t queue_rec_bytes(int kb) { return 16 + 16 * (size_t)kb; }
+
+static int index_buffer_of(const prtgs_transfer_params* p) {
+  const int kb = p->index_buffer > 0 ? p->index_buffer : kDefaultIndexBuffer;
+  return kb <= 1 ? 1 : (kb <= 2 ? 2 : (kb <= 4 ? 4 : 8));
+}
+
 size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p) {
-  size_t b = align_up(sizeof(unsigned int));
+  size_t b = 2 * align_up(sizeof(unsigned int));
+  if (p->flags & PRTGS_BOUNCE)
+    b += align_up(queue_rec_bytes(index_buffer_of(p)) * (size_t)trace_batch(n, p->n_dirs) * p->n_dirs);
   if (p->flags & PRTGS_GLOSSY) {
     b += 2 * align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + scan_workspace(n) +
          align_up(sizeof(uint32_t)) + align_up(sizeof(float) * (size_t)n_glossy * p->n_dirs);
   }
   return b;
 }
+
+template <bool BOUNCE, int KB>
+static void launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, cudaStream_t stream) {
+  int per_sm = 0, per_sm_b = 0;
+  cudaFuncSetAttribute(k_trace<BOUNCE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<BOUNCE, KB>, kTraceThreads, smem);
+  if (BOUNCE) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_resolve<KB>, 128, 0);
+  for (int64_t r0 = 0; r0 < a.n; r0 += batch) {
+    a.r0 = r0;
+    a.r1 = r0 + batch < a.n ? r0 + batch : a.n;
+    cudaMemsetAsync(a.work, 0, sizeof(unsigned int), stream);
+    if (BOUNCE) cudaMemsetAsync(a.queue_count, 0, sizeof(unsigned int), stream);
+    k_trace<BOUNCE, KB><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a);
+    if (BOUNCE) k_resolve<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a);
+  }
+}
+
+
 
 static int device_sms() {
   int dev = 0, sms = 0;
@@ -596,6 +819,9 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   const bool glossy = (p->flags & PRTGS_GLOSSY) != 0 && n_glossy > 0;
   Carver c(ws);
   unsigned int* work = c.take<unsigned int>(1);
+  unsigned int* qcount = c.take<unsigned int>(1);
+  const int kbq = index_buffer_of(p);
+  void* queue = bounce ? c.take<char>(queue_rec_bytes(kbq) * (size_t)trace_batch(n, S) * S) : nullptr;
   int32_t* slot = nullptr;
   int32_t* gids = nullptr;
   float* Vg = nullptr;
@@ -611,7 +837,6 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
     if (rc != PRTGS_OK) return rc;
     k_glossy_slots<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, g->glossy_mask, flags, slot, gids);
   }
-  cudaMemsetAsync(work, 0, sizeof(unsigned int), stream);
   TraceArgs a;
   a.nodes = reinterpret_cast<const float4*>(bvh->nodes);
   a.recs = reinterpret_cast<const float4*>(bvh->records);
@@ -632,17 +857,24 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.glossy_slot = slot;
   a.status = status;
   a.work = work;
+  a.stats = p->stats;
+  a.r0 = 0;
+  a.r1 = n;
+  a.queue = queue;
+  a.queue_count = qcount;
   size_t smem = trace_smem(S);
   int sms = device_sms();
-  int per_sm = 0;
-  if (bounce) {
-    cudaFuncSetAttribute(k_trace<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<true>, kTraceThreads, smem);
-    k_trace<true><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a);
+  const int64_t batch = bounce ? trace_batch(n, S) : n;
+  if (!bounce) {
+    launch_trace<false, 1>(a, smem, sms, batch, stream);
+  } else if (kbq == 1) {
+    launch_trace<true, 1>(a, smem, sms, batch, stream);
+  } else if (kbq == 2) {
+    launch_trace<true, 2>(a, smem, sms, batch, stream);
+  } else if (kbq == 4) {
+    launch_trace<true, 4>(a, smem, sms, batch, stream);
   } else {
-    cudaFuncSetAttribute(k_trace<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<false>, kTraceThreads, smem);
-    k_trace<false><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a);
+    launch_trace<true, 8>(a, smem, sms, batch, stream);
   }
   PRTGS_CHECK_LAUNCH();
   if (bounce) {

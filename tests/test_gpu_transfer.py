@@ -166,6 +166,33 @@ def test_transfer_bounce_surface_scene():
     assert np.mean(ref["idx"] >= 0) > 0.05  # the bounce term is exercised
 
 
+@pytest.mark.parametrize("t_min", [0.0, 1e-3])
+def test_transfer_bounce_cutoff_variants(t_min):
+    """Index matrix and bounce without the early cut-off (t_min = 0, the literal argmax) and
+    with a coarse one (t_min = 1e-3): both sides apply the same candidate rule."""
+    sc = S.surface_scene(1200, 33)
+    dirs = S.direction_set(64, 9)
+    out = _transfer_gpu(sc, dirs, 2, bounce=True, t_min=t_min)
+    ref = oracle.transfer(sc, dirs, 2, np.arange(sc.n), bounce=True, t_min=t_min)
+    floor = 1e-3 * oracle.unoccluded_norm(2)
+    _check_norm(out["P"], ref["P"], ref["allow_P"], floor)
+    _check_norm(out["T"], ref["T"], ref["allow_T"].max(axis=1), floor)
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    np.testing.assert_array_equal(out["idx"][clean], ref["idx"][clean])
+
+
+@pytest.mark.parametrize("kb", [1, 2, 4, 8])
+def test_index_buffer_sizes_agree(kb):
+    sc = S.surface_scene(2000, 34)
+    dirs = torch.from_numpy(S.direction_set(64, 10)).cuda()
+    g = _gt(sc)
+    bvh = api.build_bvh(g)
+    a = api.precompute_transfer(g, bvh, dirs, 2, bounce=True, index_buffer=kb)["idx"].cpu().numpy()
+    ref = oracle.transfer(sc, dirs.cpu().numpy(), 2, np.arange(sc.n), bounce=True)
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    np.testing.assert_array_equal(a[clean], ref["idx"][clean])
+
+
 def test_transfer_full_size_sampled_receivers():
     """The 100k-Gaussian surface workload (order 3, S = 256, shadow + bounce) on the GPU,
     checked on seeded sampled receivers that the oracle computes one by one."""

@@ -267,6 +267,15 @@ def test_index_matrix_weight_closed_form(oracle_mod):
     sc = _sc([[0, 0, 0], [0, 0, 1], [0, 0, 2]], [[0.05] * 3, [0.1] * 3, [0.1] * 3], [0.5, 0.3, 0.9],
              [[0, 0, 1], [0, 0, -1], [0, 0, -1]])
     assert oracle_mod.trace(sc, up, 2, [0], bounce=True, filter_t=0.8)["idx"][0, 0] == 2
+    # a front-facing splat behind a near-opaque stack: it is the argmax, unless its prefix
+    # transmittance is below the cut-off t_min
+    stack = [[0, 0, 0.5 + 0.01 * k] for k in range(6)]
+    sc = _sc([[0, 0, 0]] + stack + [[0, 0, 2]], [[0.05] * 3] + [[0.1] * 3] * 6 + [[0.1] * 3],
+             [0.5] + [0.9] * 6 + [0.9], [[0, 0, 1]] + [[0, 0, 1]] * 6 + [[0, 0, -1]])
+    # prefix in front of the last splat: 0.1^6 = 1e-6
+    assert oracle_mod.trace(sc, up, 2, [0], bounce=True, t_min=0.0)["idx"][0, 0] == 7
+    assert oracle_mod.trace(sc, up, 2, [0], bounce=True, t_min=1e-7)["idx"][0, 0] == 7
+    assert oracle_mod.trace(sc, up, 2, [0], bounce=True, t_min=1e-5)["idx"][0, 0] == -1
     # back-facing hits have zero weight: no index
     sc = _sc([[0, 0, 0], [0, 0, 1]], [[0.05] * 3, [0.1] * 3], [0.5, 0.9], [[0, 0, 1], [0, 0, 1]])
     assert oracle_mod.trace(sc, up, 2, [0], bounce=True)["idx"][0, 0] == -1
