@@ -210,6 +210,27 @@ int prtgs_relight_backward(int64_t n, int32_t sh_order, const float* T, int32_t 
                            void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Relight backward that allocates nothing and takes no workspace. The paper has no
+ * counterpart: this is a convenience for callers that cannot give the library device
+ * memory, e.g. a host application that owns every device allocation through its own fixed
+ * pool, or a latency-critical loop that must not call cudaMalloc. Same arguments and results
+ * as prtgs_relight_backward.
+ *  * Its scratch is a fixed 1 MiB array in the library's device memory
+ *    (prtgs_relight_backward_noalloc_max_bytes()), present on every GPU that loads the
+ *    library until the process exits. Problems needing more scratch than that
+ *    (ceil(n / 2048) * k * 3 * C floats) return PRTGS_ERR_UNSUPPORTED.
+ *  * The first call on a device looks up the array's device address on the current device;
+ *    make that first call before any stream capture.
+ *  * Every call shares the one array and leaves its partial sums in it (the kernels
+ *    overwrite all they read, so nothing needs clearing). Calls that overlap on the GPU
+ *    (different streams, or different host threads) race on it.
+ */
+size_t prtgs_relight_backward_noalloc_max_bytes(void);
+int prtgs_relight_backward_noalloc(int64_t n, int32_t sh_order, const float* T, int32_t t_channels,
+                                   const float* albedo, const float* L, int32_t k, const float* dcolors,
+                                   float* d_albedo, float* dT, float* dL, prtgs_stream_t stream);
+
+/*
  * Pinhole camera. world -> camera: x_c = rot * x_w + trans (rot row-major, camera x right,
  * y down, z forward). Pixel (px,py) has its centre at (fx x_c/z_c + cx, fy y_c/z_c + cy).
  */

@@ -71,6 +71,9 @@ _SIGS = {
     "prtgs_relight_backward_workspace_size": (c_size_t, [c_int64, c_int32, c_int32]),
     "prtgs_relight_backward": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_relight_backward_noalloc_max_bytes": (c_size_t, []),
+    "prtgs_relight_backward_noalloc": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "prtgs_render_state_bytes": (c_size_t, [c_int64, c_int32, c_int32, c_int64]),
     "prtgs_render_state_init": (c_int32, [c_void_p, c_size_t, c_int64, c_int32, c_int32, c_int64, P(RenderState)]),
     "prtgs_render_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int64]),
