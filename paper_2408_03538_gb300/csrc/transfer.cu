@@ -47,7 +47,8 @@ struct TraceArgs {
   unsigned int* work;
   unsigned long long* stats;  // nodes, leaves, hits, index rounds, traced rays (nullable)
   int64_t r0, r1;             // receivers [r0, r1) of this batch, in sorted (Morton) positions
-  void* queue;                // rays with index-matrix candidates, resolved by k_resolve
+  void* queue;                // [batch * S] per-ray candidate records, resolved by k_resolve
+  uint32_t* pending;          // [batch * S] 1 = the ray has index-matrix candidates
   unsigned int* queue_count;
 };
 
@@ -470,7 +471,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
       unsigned m = __ballot_sync(0xffffffffu, up);
       if (up) list[cnt + __popc(m & lt_mask)] = (unsigned short)s;
       if (s < a.S) vis[s] = 0.0f;
-      if (BOUNCE && s < a.S && !up) a.idx[(int64_t)gid * a.S + s] = -1;
+      if (BOUNCE && s < a.S && !up) {
+        a.idx[(int64_t)gid * a.S + s] = -1;
+        a.pending[(int64_t)(self - a.r0) * a.S + s] = 0;
+      }
       cnt += __popc(m);
     }
     if (lane == 0) s_next[warp] = 0;
@@ -492,16 +496,18 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
           V = sv.T;
           // the buffer holds the KB nearest front-facing hits within the horizon; rays with
           // candidates go to the queue that k_resolve works through
+          const int64_t slot = (int64_t)(self - a.r0) * a.S + s;
           if (sv.fb.count() == 0) {
             a.idx[(int64_t)gid * a.S + s] = -1;
+            a.pending[slot] = 0;
           } else {
-            unsigned slot = atomicAdd(a.queue_count, 1u);
             QueueRec<KB>* q = static_cast<QueueRec<KB>*>(a.queue) + slot;
             q->self = self;
             q->s = s;
             q->t_hor = sv.t_hor;
             q->pad = 0;
             q->fb = sv.fb;
+            a.pending[slot] = 1;
           }
         } else {
           ShadowVis sv{a, r, self, rs, 1.0f};
@@ -510,6 +516,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
         }
       } else if (BOUNCE) {
         a.idx[(int64_t)gid * a.S + s] = -1;
+        a.pending[(int64_t)(self - a.r0) * a.S + s] = 0;
       }
       vis[s] = V;
     }
@@ -565,13 +572,22 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
   }
 }
 
-// Index-matrix entries of the queued rays: one thread per ray.
+// Slots of the rays that still have candidates, compacted in (receiver, direction) order.
+__global__ void k_compact_pending(int64_t count, const uint32_t* __restrict__ pending,
+                                  const uint32_t* __restrict__ incl, uint32_t* __restrict__ list) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && pending[i]) list[incl[i] - 1] = (uint32_t)i;
+}
+
+// Index-matrix entries of the listed rays: one thread per ray. Neighbouring threads hold
+// rays of the same receiver, so a warp's walks start from the same origin.
 template <int KB>
-__global__ void __launch_bounds__(128) k_resolve(TraceArgs a) {
+__global__ void __launch_bounds__(128) k_resolve(TraceArgs a, const uint32_t* __restrict__ list) {
   const unsigned count = *a.queue_count;
   RayStats rs{0u, 0u, 0u, 0u, 0u};
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-    const QueueRec<KB> rec = static_cast<const QueueRec<KB>*>(a.queue)[q];
+    const uint32_t slot = list[q];
+    const QueueRec<KB> rec = static_cast<const QueueRec<KB>*>(a.queue)[slot];
     const int self = rec.self, s = rec.s;
     if (self < 0 || (int64_t)self >= a.n || s < 0 || s >= a.S) {
       set_status(a.status, PRTGS_STATUS_BAD_INDEX);
@@ -760,7 +776,7 @@ static size_t glossy_smem(int S, int C) { return sizeof(float) * (3 * S + 3 * (s
 
 // Receivers per batch: the resolve queue holds at most batch * S rays.
 static int64_t trace_batch(int64_t n, int S) {
-  int64_t b = (int64_t(1) << 24) / (S > 0 ? S : 1);
+  int64_t b = (int64_t(1) << 23) / (S > 0 ? S : 1);
   if (b < 1) b = 1;
   return b < n ? b : n;
 }
@@ -774,8 +790,11 @@ static int index_buffer_of(const prtgs_transfer_params* p) {
 
 size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p) {
   size_t b = 2 * align_up(sizeof(unsigned int));
-  if (p->flags & PRTGS_BOUNCE)
-    b += align_up(queue_rec_bytes(index_buffer_of(p)) * (size_t)trace_batch(n, p->n_dirs) * p->n_dirs);
+  if (p->flags & PRTGS_BOUNCE) {
+    const size_t rays = (size_t)trace_batch(n, p->n_dirs) * p->n_dirs;
+    b += align_up(queue_rec_bytes(index_buffer_of(p)) * rays) + 3 * align_up(sizeof(uint32_t) * rays) +
+         scan_workspace((int64_t)rays);
+  }
   if (p->flags & PRTGS_GLOSSY) {
     b += 2 * align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + scan_workspace(n) +
          align_up(sizeof(uint32_t)) + align_up(sizeof(float) * (size_t)n_glossy * p->n_dirs);
@@ -784,7 +803,8 @@ size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_para
 }
 
 template <bool BOUNCE, int KB>
-static void launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, cudaStream_t stream) {
+static int launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, uint32_t* incl, uint32_t* list,
+                        void* scan_ws, cudaStream_t stream) {
   int per_sm = 0, per_sm_b = 0;
   cudaFuncSetAttribute(k_trace<BOUNCE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<BOUNCE, KB>, kTraceThreads, smem);
@@ -793,10 +813,16 @@ static void launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, cudaS
     a.r0 = r0;
     a.r1 = r0 + batch < a.n ? r0 + batch : a.n;
     cudaMemsetAsync(a.work, 0, sizeof(unsigned int), stream);
-    if (BOUNCE) cudaMemsetAsync(a.queue_count, 0, sizeof(unsigned int), stream);
     k_trace<BOUNCE, KB><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a);
-    if (BOUNCE) k_resolve<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a);
+    if (BOUNCE) {
+      const int64_t rays = (a.r1 - a.r0) * a.S;
+      int rc = scan_u32(a.pending, incl, rays, false, a.queue_count, scan_ws, stream);
+      if (rc != PRTGS_OK) return rc;
+      k_compact_pending<<<(unsigned)((rays + 255) / 256), 256, 0, stream>>>(rays, a.pending, incl, list);
+      k_resolve<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a, list);
+    }
   }
+  return PRTGS_OK;
 }
 
 
@@ -822,6 +848,11 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   unsigned int* qcount = c.take<unsigned int>(1);
   const int kbq = index_buffer_of(p);
   void* queue = bounce ? c.take<char>(queue_rec_bytes(kbq) * (size_t)trace_batch(n, S) * S) : nullptr;
+  const size_t batch_rays = bounce ? (size_t)trace_batch(n, S) * S : 0;
+  uint32_t* pending = bounce ? c.take<uint32_t>(batch_rays) : nullptr;
+  uint32_t* incl = bounce ? c.take<uint32_t>(batch_rays) : nullptr;
+  uint32_t* rlist = bounce ? c.take<uint32_t>(batch_rays) : nullptr;
+  void* rscan_ws = bounce ? c.take<char>(scan_workspace((int64_t)batch_rays)) : nullptr;
   int32_t* slot = nullptr;
   int32_t* gids = nullptr;
   float* Vg = nullptr;
@@ -861,21 +892,24 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.r0 = 0;
   a.r1 = n;
   a.queue = queue;
+  a.pending = pending;
   a.queue_count = qcount;
   size_t smem = trace_smem(S);
   int sms = device_sms();
   const int64_t batch = bounce ? trace_batch(n, S) : n;
+  int rct;
   if (!bounce) {
-    launch_trace<false, 1>(a, smem, sms, batch, stream);
+    rct = launch_trace<false, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
   } else if (kbq == 1) {
-    launch_trace<true, 1>(a, smem, sms, batch, stream);
+    rct = launch_trace<true, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
   } else if (kbq == 2) {
-    launch_trace<true, 2>(a, smem, sms, batch, stream);
+    rct = launch_trace<true, 2>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
   } else if (kbq == 4) {
-    launch_trace<true, 4>(a, smem, sms, batch, stream);
+    rct = launch_trace<true, 4>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
   } else {
-    launch_trace<true, 8>(a, smem, sms, batch, stream);
+    rct = launch_trace<true, 8>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
   }
+  if (rct != PRTGS_OK) return rct;
   PRTGS_CHECK_LAUNCH();
   if (bounce) {
     k_bounce<<<(unsigned)((n + 7) / 8), 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, idx, T,
