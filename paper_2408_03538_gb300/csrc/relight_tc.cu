@@ -1,12 +1,229 @@
-// Relight contraction on the tensor cores (placeholder until the tcgen05 path lands).
+// Relight contraction on the 5th-generation tensor cores (tcgen05), Eq. 14:
+//   D[i, (l,c)] = sum_m T[i,m] L[l,c,m],   colors[l,i,c] = (rho_i[c] / pi) D[i, (l,c)]
+// as a [128 x K'] x [K' x N] product per tile of 128 Gaussians, N = 3k padded to a multiple
+// of 16 (<= 256), accumulated in FP32 in tensor memory.
+//
+// Precision. PRTGS_PREC_BF16 feeds bf16(T) and bf16(L) (one K = 16 slab). PRTGS_PREC_BF16X3
+// splits both operands into three BF16 terms, x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1),
+// x3 = bf16(x - x1 - x2)), and accumulates the six products whose order is at most 2^-16
+// relative: T1L1 + T1L2 + T2L1 + T1L3 + T2L2 + T3L1, as six K slabs of one MMA chain (the
+// split-BF16 scheme of Henry, Tang and Heinecke, "Leveraging the bfloat16 AI datatype for
+// higher-precision computations", 2019). The dropped terms are below 2^-24 relative.
+//
+// Data movement. The operands are transformed on the way in (split into BF16 terms), so they
+// are staged with ordinary coalesced loads and stores into shared memory in the canonical
+// no-swizzle K-major layout: 8-row x 16-byte core matrices, core matrices adjacent in K
+// 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride byte offset).
+// One elected thread issues the MMAs; completion is signalled through an mbarrier
+// (tcgen05.commit); each warp then reads its 32 accumulator lanes with tcgen05.ld.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace prtgs {
 
-int relight_tc(int64_t, int32_t, const float*, const float*, const float*, int32_t, int32_t, float*, void*,
-               cudaStream_t) {
-  return PRTGS_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kTcRows = 128;       // MMA M (one Gaussian per TMEM lane)
+constexpr int kTcThreads = 128;    // 4 warps: warp w owns TMEM lanes 32w..32w+31
+constexpr int kSlabBytesA = kTcRows * 16 * 2;  // one K = 16 slab of A: 4 KB
+constexpr int kMaxN = 256;
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Byte offset of element (row, k) of a K = 16 slab in the no-swizzle K-major layout.
+__device__ __forceinline__ int kmajor_offset(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading / stride byte offsets
+// (all >> 4), version bits 46-48 = 0b001, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3fffu);
+  d |= (uint64_t)((lbo >> 4) & 0x3fffu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3fffu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r);
+  r = r - __bfloat162float(b);
+  c = __float2bfloat16_rn(r);
+}
+
+// Which split term of T and of L each K slab multiplies (BF16X3).
+__device__ __forceinline__ int a_term(int slab) { return slab == 2 || slab == 4 ? 1 : (slab == 5 ? 2 : 0); }
+__device__ __forceinline__ int b_term(int slab) { return slab == 1 || slab == 4 ? 1 : (slab == 3 ? 2 : 0); }
+
+template <int C>
+__global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const float* __restrict__ T,
+                                                           const float* __restrict__ albedo,
+                                                           const float* __restrict__ L, int k, int n_pad, int slabs,
+                                                           int tmem_cols, float* __restrict__ colors) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // layout: [A slabs][B slabs], each region 1024-aligned
+  unsigned char* sA = smem_raw;
+  unsigned char* sB = smem_raw + slabs * kSlabBytesA;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nout = 3 * k;
+
+  // B operand: row n = (light l, channel c), K-major; zero for the padding rows and for
+  // SH indices >= C within the 16-wide slab.
+  for (int e = tid; e < slabs * n_pad * 16; e += kTcThreads) {
+    const int slab = e / (n_pad * 16), rem = e % (n_pad * 16);
+    const int row = rem / 16, kk = rem % 16;
+    float v = 0.f;
+    if (row < nout && kk < C) v = L[(int64_t)row * C + kk];  // L[l][c][m] with row = 3l + c
+    __nv_bfloat16 t1, t2, t3;
+    split3(v, t1, t2, t3);
+    const int term = slabs == 1 ? 0 : b_term(slab);
+    const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
+    *reinterpret_cast<__nv_bfloat16*>(sB + slab * n_pad * 32 + kmajor_offset(row, kk)) = sel;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = idesc_bf16(kTcRows, n_pad);
+  uint32_t phase = 0;
+  const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTcRows;
+    // A operand: this thread's row (Gaussian row0 + tid), split into BF16 terms
+    const int64_t gi = row0 + tid;
+    float tv[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) tv[m] = (gi < n && m < C) ? __ldg(T + gi * C + m) : 0.f;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      __nv_bfloat16 t1, t2, t3;
+      split3(tv[m], t1, t2, t3);
+      for (int slab = 0; slab < slabs; ++slab) {
+        const int term = slabs == 1 ? 0 : a_term(slab);
+        const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
+        *reinterpret_cast<__nv_bfloat16*>(sA + slab * kSlabBytesA + kmajor_offset(tid, m)) = sel;
+      }
+    }
+    // make the generic-proxy stores visible to the tensor core's async proxy
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int slab = 0; slab < slabs; ++slab) {
+        const uint64_t da = smem_desc(smem_u32(sA + slab * kSlabBytesA), 128, 256);
+        const uint64_t db = smem_desc(smem_u32(sB + slab * n_pad * 32), 128, 256);
+        const uint32_t acc = slab > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    // bounded wait for the MMA chain
+    bool done = false;
+    for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(smem_u32(&mbar)), "r"(phase));
+      done = ok != 0;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // epilogue: this thread holds accumulator row tid (TMEM lane tid)
+    float rho[3] = {0.f, 0.f, 0.f};
+    if (gi < n) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * gi + c) * (1.0f / kPi);
+    }
+    for (int col = 0; col < n_pad; col += 8) {
+      uint32_t r[8];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (gi < n) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int o = col + j;
+          if (o < nout) {
+            const int l = o / 3, c = o % 3;
+            colors[((int64_t)l * n + gi) * 3 + c] = done ? __uint_as_float(r[j]) * rho[c] : __int_as_float(0x7fc00000);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // the next tile overwrites the A operand and the accumulator
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  (void)lane;
+}
+
+}  // namespace
+
+int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
+               int32_t precision, float* colors, void*, cudaStream_t stream) {
+  if (n == 0 || k == 0) return PRTGS_OK;
+  const int nout = 3 * k;
+  const int n_pad = (nout + 15) / 16 * 16;
+  if (n_pad > kMaxN) return PRTGS_ERR_UNSUPPORTED;
+  int tmem_cols = 32;
+  while (tmem_cols < n_pad) tmem_cols <<= 1;
+  const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
+  const size_t smem = (size_t)slabs * kSlabBytesA + (size_t)slabs * n_pad * 32 + 1024;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+  // one resident CTA per SM: TMEM columns are allocated per CTA
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  switch (order) {
+    case 1:
+      cudaFuncSetAttribute(k_relight_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_relight_tc<4><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      break;
+    case 2:
+      cudaFuncSetAttribute(k_relight_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_relight_tc<9><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      break;
+    default:
+      cudaFuncSetAttribute(k_relight_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_relight_tc<16><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      break;
+  }
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
 }
 
 }  // namespace prtgs

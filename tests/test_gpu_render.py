@@ -185,3 +185,39 @@ def test_relit_render_autograd_end_to_end():
     assert abs(loss.item() - rl.item()) <= 1e-4 * rl.item()
     for got, p, name in zip(leaves, ps, ("means", "scales", "quats", "opacity", "albedo", "light")):
         assert _rel(got.grad.cpu(), p.grad) < 2e-3, name
+
+
+@pytest.mark.parametrize("order,k,n", [(3, 1, 5003), (3, 64, 20000), (2, 4, 129), (1, 2, 128), (3, 85, 777)])
+def test_relight_tensor_core_bf16x3(order, k, n):
+    """tcgen05 relight with the 3-term BF16 split meets the FP32 bar (1e-4 norm-wise)."""
+    rng = np.random.default_rng(order * 100 + k)
+    C = (order + 1) ** 2
+    T = rng.standard_normal((n, C)).astype(np.float32)
+    alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    L = rng.standard_normal((k, 3, C)).astype(np.float32)
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), order, precision=1).cpu().numpy()
+    ref = oracle.relight(T, alb, L)
+    err = oracle.norm_err(col.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
+    assert np.all(np.isfinite(col))
+    assert err.max() < 1e-4, err.max()
+
+
+def test_relight_tensor_core_plain_bf16_error_is_bf16_sized():
+    rng = np.random.default_rng(7)
+    n, C, k = 4096, 16, 8
+    T = rng.standard_normal((n, C)).astype(np.float32)
+    alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    L = rng.standard_normal((k, 3, C)).astype(np.float32)
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), 3, precision=2).cpu().numpy()
+    ref = oracle.relight(T, alb, L)
+    err = oracle.norm_err(col.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
+    assert 1e-5 < np.median(err) < 2e-2  # plain BF16 operands: about 2^-8 relative
+
+
+def test_relight_tensor_core_rejects_unsupported():
+    T = torch.zeros((10, 3, 16), device="cuda")
+    with pytest.raises(Exception):
+        api.relight(T, torch.zeros((10, 3), device="cuda"), torch.zeros((1, 3, 16), device="cuda"), 3, precision=1)
+    with pytest.raises(Exception):  # 3k > 256 output columns
+        api.relight(torch.zeros((10, 16), device="cuda"), torch.zeros((10, 3), device="cuda"),
+                    torch.zeros((90, 3, 16), device="cuda"), 3, precision=1)
