@@ -200,6 +200,17 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
                   void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Relight of many scenes in one launch: scene b holds Gaussians scene_offsets[b] ..
+ * scene_offsets[b+1] (device int64 [n_scenes+1]) and has its own k lights
+ * L[b,k,3,C] (device). colors[3 k n] holds one contiguous [k, n_b, 3] block per scene,
+ * scene b's block starting at float 3 k scene_offsets[b] (the input layout of prtgs_render
+ * for that scene). No workspace. Tensor-core precisions need t_channels = 1 and 3k <= 256.
+ */
+int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                          const int64_t* scene_offsets, int32_t n_scenes, const float* L, int32_t k,
+                          int32_t precision, float* colors, prtgs_stream_t stream);
+
+/*
  * Relight backward (diffuse splats; glossy rows of dcolors must be zero or are ignored).
  *   dcolors[k,n,3] in; d_albedo[n,3] out (overwritten); dT[n,t_channels,C] out (may be NULL);
  *   dL[k,3,C] out (overwritten; deterministic two-pass reduction over n).

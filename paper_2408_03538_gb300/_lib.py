@@ -68,6 +68,8 @@ _SIGS = {
     "prtgs_relight": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
                                 c_void_p]),
+    "prtgs_relight_batched": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
+                                        c_int32, c_int32, c_void_p, c_void_p]),
     "prtgs_relight_backward_workspace_size": (c_size_t, [c_int64, c_int32, c_int32]),
     "prtgs_relight_backward": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -183,6 +183,25 @@ def relight(T: torch.Tensor, albedo: torch.Tensor, Lsh: torch.Tensor, order: int
     return colors
 
 
+def relight_batched(T, albedo, scene_offsets, Lsh, order, precision=L.PREC_FP32, out=None):
+    """Relight many scenes in one launch; Lsh [B,k,3,C] holds each scene's lights. Returns a flat
+    buffer of 3kn floats holding one [k, n_b, 3] block per scene (see scene_colors)."""
+    lib = L.load()
+    n = int(T.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    B, k = int(Lsh.shape[0]), int(Lsh.shape[1])
+    colors = out if out is not None else torch.empty(3 * k * n, dtype=torch.float32, device=T.device)
+    L.check(lib.prtgs_relight_batched(n, order, _ptr(T), tch, _ptr(albedo), _ptr(scene_offsets), B, _ptr(Lsh), k,
+                                      precision, _ptr(colors), _stream()), "prtgs_relight_batched")
+    return colors
+
+
+def scene_colors(colors_flat, k, offsets_host, b):
+    """View of scene b's [k, n_b, 3] block in a prtgs_relight_batched output."""
+    o0, o1 = int(offsets_host[b]), int(offsets_host[b + 1])
+    return colors_flat[3 * k * o0:3 * k * o1].view(k, o1 - o0, 3)
+
+
 def relight_backward(T, albedo, Lsh, order, dcolors, need_dT=False):
     lib = L.load()
     n = int(T.shape[0])

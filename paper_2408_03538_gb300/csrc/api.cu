@@ -156,6 +156,21 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
                         colors, workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
+                          const int64_t* scene_offsets, int32_t n_scenes, const float* L, int32_t k,
+                          int32_t precision, float* colors, prtgs_stream_t stream) {
+  int rc;
+  if (n < 0 || k < 0 || n_scenes < 1) return PRTGS_ERR_SHAPE;
+  if ((rc = check_order(sh_order))) return rc;
+  if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
+  if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
+  if (n == 0 || k == 0) return PRTGS_OK;
+  if (!T || !albedo || !L || !colors || !scene_offsets) return PRTGS_ERR_INVALID_ARG;
+  if (precision != PRTGS_PREC_FP32 && 3 * k > 256) return PRTGS_ERR_UNSUPPORTED;
+  return finish(relight_batched(n, sh_order, T, t_channels, albedo, scene_offsets, n_scenes, L, k, precision,
+                                colors, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 size_t prtgs_relight_backward_workspace_size(int64_t n, int32_t sh_order, int32_t k) {
   if (n < 0 || k < 0 || check_order(sh_order)) return 0;
   return relight_backward_workspace(n, sh_order, k);

@@ -35,6 +35,9 @@ size_t relight_workspace(int64_t n, int32_t order, int32_t k, int32_t precision)
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
             const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
             int32_t k, int32_t precision, float* colors, void* ws, cudaStream_t stream);
+int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                    const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
+                    float* colors, cudaStream_t stream);
 size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k);
 int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                      const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,

@@ -105,7 +105,7 @@ static void launch_relight_c(int64_t n, const float* T, int tch, const float* al
 }
 
 int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
-               int32_t precision, float* colors, void* ws, cudaStream_t stream);
+               int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors, cudaStream_t stream);
 
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
             const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
@@ -114,7 +114,7 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
   if (k > kMaxLightsSmem) return PRTGS_ERR_UNSUPPORTED;
   if (precision != PRTGS_PREC_FP32) {
     if (t_channels != 1 || n_glossy > 0) return PRTGS_ERR_UNSUPPORTED;
-    return relight_tc(n, order, T, albedo, L, k, precision, colors, ws, stream);
+    return relight_tc(n, order, T, albedo, L, k, precision, nullptr, 1, colors, stream);
   }
   switch (order) {
     case 1: launch_relight_c<4>(n, T, t_channels, albedo, L, k, colors, stream); break;
@@ -137,6 +137,73 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
     }
     PRTGS_CHECK_LAUNCH();
   }
+  return PRTGS_OK;
+}
+
+// ---- many scenes in one launch: scene b (Gaussians offsets[b] .. offsets[b+1]) has its own
+// k lights L[b] --------------------------------------------------------------------------------
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_batched(int64_t n, const float* __restrict__ T,
+                                                                     const float* __restrict__ albedo,
+                                                                     const int64_t* __restrict__ offsets,
+                                                                     int n_scenes, const float* __restrict__ L, int k,
+                                                                     float* __restrict__ colors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = find_scene(offsets, n_scenes, i);
+  const float* Lb = L + (int64_t)b * k * 3 * C;
+  const int64_t ob = offsets[b], nb = offsets[b + 1] - ob;
+  float* cb = colors + 3 * (int64_t)k * ob;  // this scene's [k, n_b, 3] block
+  float t[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) t[c][m] = __ldg(T + (i * TCH + c) * C + m);
+  const float r0 = __ldg(albedo + 3 * i) * (1.0f / kPi);
+  const float r1 = __ldg(albedo + 3 * i + 1) * (1.0f / kPi);
+  const float r2 = __ldg(albedo + 3 * i + 2) * (1.0f / kPi);
+  for (int l = 0; l < k; ++l) {
+    const float* Ll = Lb + l * 3 * C;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+      d0 = fmaf(t[0][m], __ldg(Ll + m), d0);
+      d1 = fmaf(t[TCH > 1 ? 1 : 0][m], __ldg(Ll + C + m), d1);
+      d2 = fmaf(t[TCH > 1 ? 2 : 0][m], __ldg(Ll + 2 * C + m), d2);
+    }
+    float* out = cb + ((int64_t)l * nb + (i - ob)) * 3;
+    out[0] = r0 * d0;
+    out[1] = r1 * d1;
+    out[2] = r2 * d2;
+  }
+}
+
+template <int C>
+static void launch_relight_batched_c(int64_t n, const float* T, int tch, const float* albedo,
+                                     const int64_t* offsets, int n_scenes, const float* L, int k, float* colors,
+                                     cudaStream_t stream) {
+  unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
+  if (tch == 3)
+    k_relight_batched<C, 3><<<grid, kRelightThreads, 0, stream>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
+  else
+    k_relight_batched<C, 1><<<grid, kRelightThreads, 0, stream>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
+}
+
+int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                    const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
+                    float* colors, cudaStream_t stream) {
+  if (n == 0 || k == 0) return PRTGS_OK;
+  if (precision != PRTGS_PREC_FP32) {
+    if (t_channels != 1) return PRTGS_ERR_UNSUPPORTED;
+    return relight_tc(n, order, T, albedo, L, k, precision, offsets, n_scenes, colors, stream);
+  }
+  switch (order) {
+    case 1: launch_relight_batched_c<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
+    case 2: launch_relight_batched_c<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
+    case 3: launch_relight_batched_c<16>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
+  }
+  PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }
 

@@ -68,23 +68,11 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
 __device__ __forceinline__ int a_term(int slab) { return slab == 2 || slab == 4 ? 1 : (slab == 5 ? 2 : 0); }
 __device__ __forceinline__ int b_term(int slab) { return slab == 1 || slab == 4 ? 1 : (slab == 3 ? 2 : 0); }
 
+// B operand (the split light SH of one scene) into shared memory.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const float* __restrict__ T,
-                                                           const float* __restrict__ albedo,
-                                                           const float* __restrict__ L, int k, int n_pad, int slabs,
-                                                           int tmem_cols, float* __restrict__ colors) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // layout: [A slabs][B slabs], each region 1024-aligned
-  unsigned char* sA = smem_raw;
-  unsigned char* sB = smem_raw + slabs * kSlabBytesA;
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nout = 3 * k;
-
-  // B operand: row n = (light l, channel c), K-major; zero for the padding rows and for
-  // SH indices >= C within the 16-wide slab.
-  for (int e = tid; e < slabs * n_pad * 16; e += kTcThreads) {
+__device__ __forceinline__ void load_lights(unsigned char* sB, const float* __restrict__ L, int nout, int n_pad,
+                                            int slabs) {
+  for (int e = threadIdx.x; e < slabs * n_pad * 16; e += kTcThreads) {
     const int slab = e / (n_pad * 16), rem = e % (n_pad * 16);
     const int row = rem / 16, kk = rem % 16;
     float v = 0.f;
@@ -95,6 +83,26 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
     *reinterpret_cast<__nv_bfloat16*>(sB + slab * n_pad * 32 + kmajor_offset(row, kk)) = sel;
   }
+}
+
+// offsets == nullptr: one scene with lights L. Otherwise scene b (rows offsets[b] ..
+// offsets[b+1]) uses lights L + b * k * 3 * C; a tile that straddles scenes is run once per
+// scene with the other rows zeroed.
+template <int C>
+__global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const float* __restrict__ T,
+                                                           const float* __restrict__ albedo,
+                                                           const float* __restrict__ L, int k, int n_pad, int slabs,
+                                                           int tmem_cols, const int64_t* __restrict__ offsets,
+                                                           int n_scenes, float* __restrict__ colors) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // layout: [A slabs][B slabs], each region 1024-aligned
+  unsigned char* sA = smem_raw;
+  unsigned char* sB = smem_raw + slabs * kSlabBytesA;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nout = 3 * k;
+
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(tmem_cols));
@@ -111,79 +119,99 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   const uint32_t idesc = idesc_bf16(kTcRows, n_pad);
   uint32_t phase = 0;
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+  int cached = -1;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kTcRows;
-    // A operand: this thread's row (Gaussian row0 + tid), split into BF16 terms
+    const int64_t row_end = row0 + kTcRows < n ? row0 + kTcRows : n;
+    const int b_first = offsets ? find_scene(offsets, n_scenes, row0) : 0;
+    const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
     const int64_t gi = row0 + tid;
     float tv[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) tv[m] = (gi < n && m < C) ? __ldg(T + gi * C + m) : 0.f;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      __nv_bfloat16 t1, t2, t3;
-      split3(tv[m], t1, t2, t3);
-      for (int slab = 0; slab < slabs; ++slab) {
-        const int term = slabs == 1 ? 0 : a_term(slab);
-        const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
-        *reinterpret_cast<__nv_bfloat16*>(sA + slab * kSlabBytesA + kmajor_offset(tid, m)) = sel;
-      }
-    }
-    // make the generic-proxy stores visible to the tensor core's async proxy
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int slab = 0; slab < slabs; ++slab) {
-        const uint64_t da = smem_desc(smem_u32(sA + slab * kSlabBytesA), 128, 256);
-        const uint64_t db = smem_desc(smem_u32(sB + slab * n_pad * 32), 128, 256);
-        const uint32_t acc = slab > 0 ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&mbar)));
-    }
-    // bounded wait for the MMA chain
-    bool done = false;
-    for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
-      uint32_t ok;
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(ok)
-          : "r"(smem_u32(&mbar)), "r"(phase));
-      done = ok != 0;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: this thread holds accumulator row tid (TMEM lane tid)
     float rho[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * gi + c) * (1.0f / kPi);
     }
-    for (int col = 0; col < n_pad; col += 8) {
-      uint32_t r[8];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (gi < n) {
+    for (int b = b_first; b <= b_last; ++b) {
+      const int64_t lo = offsets ? (offsets[b] > row0 ? offsets[b] : row0) : row0;
+      const int64_t hi = offsets ? (offsets[b + 1] < row_end ? offsets[b + 1] : row_end) : row_end;
+      if (hi <= lo) continue;  // empty scene (uniform over the block)
+      if (b != cached) {
+        load_lights<C>(sB, L + (int64_t)b * k * 3 * C, nout, n_pad, slabs);
+        cached = b;
+      }
+      const bool mine = gi >= lo && gi < hi;
+      // output block of this scene: [k, n_b, 3] at 3 k offsets[b] (the whole [k, n, 3] for one scene)
+      const int64_t ob = offsets ? offsets[b] : 0;
+      const int64_t nb = offsets ? offsets[b + 1] - ob : n;
+      float* cb = colors + 3 * (int64_t)k * ob;
+      // A operand: this thread's row, split into BF16 terms (zero outside the scene)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int o = col + j;
-          if (o < nout) {
-            const int l = o / 3, c = o % 3;
-            colors[((int64_t)l * n + gi) * 3 + c] = done ? __uint_as_float(r[j]) * rho[c] : __int_as_float(0x7fc00000);
+      for (int m = 0; m < 16; ++m) {
+        __nv_bfloat16 t1, t2, t3;
+        split3(mine ? tv[m] : 0.f, t1, t2, t3);
+        for (int slab = 0; slab < slabs; ++slab) {
+          const int term = slabs == 1 ? 0 : a_term(slab);
+          const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
+          *reinterpret_cast<__nv_bfloat16*>(sA + slab * kSlabBytesA + kmajor_offset(tid, m)) = sel;
+        }
+      }
+      // make the generic-proxy stores visible to the tensor core's async proxy
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int slab = 0; slab < slabs; ++slab) {
+          const uint64_t da = smem_desc(smem_u32(sA + slab * kSlabBytesA), 128, 256);
+          const uint64_t db = smem_desc(smem_u32(sB + slab * n_pad * 32), 128, 256);
+          const uint32_t acc = slab > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mbar)));
+      }
+      // bounded wait for the MMA chain
+      bool done = false;
+      for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(&mbar)), "r"(phase));
+        done = ok != 0;
+      }
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // epilogue: this thread holds accumulator row tid (TMEM lane tid)
+      for (int col = 0; col < n_pad; col += 8) {
+        uint32_t r[8];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (mine) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int o = col + j;
+            if (o < nout) {
+              const int l = o / 3, c = o % 3;
+              cb[((int64_t)l * nb + (gi - ob)) * 3 + c] =
+                  done ? __uint_as_float(r[j]) * rho[c] : __int_as_float(0x7fc00000);
+            }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();  // the next pass overwrites the operands and the accumulator
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // the next tile overwrites the A operand and the accumulator
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
@@ -193,7 +221,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 }  // namespace
 
 int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
-               int32_t precision, float* colors, void*, cudaStream_t stream) {
+               int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors, cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
   const int nout = 3 * k;
   const int n_pad = (nout + 15) / 16 * 16;
@@ -211,15 +239,18 @@ int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, co
   switch (order) {
     case 1:
       cudaFuncSetAttribute(k_relight_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<4><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      k_relight_tc<4><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
+                                                         n_scenes, colors);
       break;
     case 2:
       cudaFuncSetAttribute(k_relight_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<9><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      k_relight_tc<9><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
+                                                         n_scenes, colors);
       break;
     default:
       cudaFuncSetAttribute(k_relight_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<16><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, colors);
+      k_relight_tc<16><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
+                                                          n_scenes, colors);
       break;
   }
   PRTGS_CHECK_LAUNCH();
