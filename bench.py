@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched-32"],
+                    help="batched-32: 32 isotropic scenes, one graph-captured step (measurement of batching)")
+    ap.add_argument("--case", default=None, choices=["kernels-small"],
+                    help="run the small profiling case used for the ncu captures instead of the bench")
     return ap.parse_args()
 
 
@@ -370,10 +374,109 @@ def launches_per_step(n, n_pairs, cam):
     return bvh + transfer + relight + render + loss + render_bwd + relight_bwd
 
 
+def run_kernels_small():
+    """Small case for `ncu --set full`: transfer with bounce on a 20k-splat surface scene (S = 64),
+    relight of 1M splats x 64 lights on the tensor cores and on the CUDA cores, and a 1280x720
+    render forward + backward of the 100k surface scene."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    sc = S.surface_scene(20000, 11)
+    g = api.GaussianTensors.from_scene(sc)
+    dirs = torch.from_numpy(S.direction_set(64, 2)).cuda()
+    bvh = api.build_bvh(g)
+    out = api.precompute_transfer(g, bvh, dirs, 3, bounce=True)
+    n = 1_000_000
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    T = torch.randn((n, 16), device="cuda", generator=gen)
+    alb = torch.rand((n, 3), device="cuda", generator=gen)
+    L = torch.randn((64, 3, 16), device="cuda", generator=gen)
+    col = api.relight(T, alb, L, 3, precision=1)
+    col32 = api.relight(T, alb, L, 3, precision=0)
+    sc2 = S.make_scene(WORKLOAD)
+    g2 = api.GaussianTensors.from_scene(sc2)
+    cam = S.make_camera(WORKLOAD, 1280, 720)
+    colors = torch.rand((1, g2.n, 3), device="cuda", generator=gen)
+    bg = torch.zeros(3, device="cuda")
+    img, st = api.render(g2, colors, cam, bg, max_pairs=4_000_000)
+    api.render_backward(g2, colors, cam, bg, st, torch.randn(img.shape, device="cuda", generator=gen))
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "kernels-small", "idx_max": int(out["idx"].max()),
+                      "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
+
+
+def run_batched(args):
+    """32 isotropic scenes (Gaussian counts log-uniform in [1e4, 5e5]), order 3, S = 128, shadowed
+    transfer, 8 lights per scene relit, 1280x720 render + L2 loss + backward per scene; the whole
+    step is one CUDA-graph replay. Reports summed transfer rays/s and relit frames/s."""
+    import torch
+
+    from paper_2408_03538_gb300 import batched, scenes as S
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w = S.WORKLOADS["batched-32"]
+    seed = S.config_seed(w["config"])
+    parts = S.batched_scenes(seed)
+    lights = np.stack([S.env_lights(w["lights"], w["order"], seed + 100 + b) for b in range(len(parts))])
+    cams = [S.make_camera("batched-32") for _ in parts]
+    dirs = S.direction_set(w["n_dirs"], seed)
+    pipe = batched.BatchedPipeline(parts, dirs, w["order"], lights, cams)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        pipe.step()
+    pipe.capture()
+    for _ in range(args.warmup):
+        pipe.replay()
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    graph_ms = eager_ms = 0.0
+    for mode in ("graph", "eager"):
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "graph":
+                pipe.replay()
+            else:
+                pipe.step()
+            e1.record(stream)
+            e1.synchronize()
+            if mode == "graph":
+                graph_ms += e0.elapsed_time(e1)
+            else:
+                eager_ms += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    n_total = sum(p.n for p in parts)
+    rays = n_total * int(dirs.shape[0])
+    frames = len(parts) * w["lights"]
+    line = {"metric": METRIC, "value": rays * args.steps / (graph_ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-32", "scenes": len(parts), "n_gaussians": n_total,
+                       "sizes_min_max": [min(p.n for p in parts), max(p.n for p in parts)], "sh_order": w["order"],
+                       "n_dirs": int(dirs.shape[0]), "lights_per_scene": w["lights"],
+                       "image": f"{cams[0].width}x{cams[0].height}", "relight_precision": int(pipe.precision),
+                       "l2": "flushed between steps (256 MB write)"},
+            "frames_per_s": frames * args.steps / (graph_ms / 1e3),
+            "eager_ms_per_step": eager_ms / args.steps, "graph_ms_per_step": graph_ms / args.steps,
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.case == "kernels-small":
+        run_kernels_small()
+    elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched-32":
+        run_batched(args)
     else:
         run_ours(args)
 

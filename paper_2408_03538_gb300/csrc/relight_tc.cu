@@ -234,8 +234,12 @@ int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, co
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-  // one resident CTA per SM: TMEM columns are allocated per CTA
-  const int grid = (int)(tiles < sms ? tiles : sms);
+  // resident CTAs per SM bounded by the 512 TMEM columns (allocations beyond that would wait
+  // for a CTA to finish) and kept at <= 4 so that one CTA's epilogue overlaps another's MMA
+  int per_sm = 512 / tmem_cols;
+  if (per_sm > 4) per_sm = 4;
+  const int64_t want = (int64_t)sms * per_sm;
+  const int grid = (int)(tiles < want ? tiles : want);
   switch (order) {
     case 1:
       cudaFuncSetAttribute(k_relight_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -21,6 +21,11 @@
 namespace prtgs {
 
 constexpr int kTraceWarps = 4;
+// Resident 128-thread blocks per SM the kernels are compiled for (register caps chosen by
+// measurement on the 100k surface workload: the visibility-only walk is fastest at 64
+// registers, the bounce walk and the resolve kernel at 128).
+constexpr int kShadowMinBlocks = 8;
+constexpr int kBounceMinBlocks = 4;
 constexpr int kTraceThreads = 32 * kTraceWarps;
 constexpr int kDefaultIndexBuffer = 8;
 constexpr int kMaxDirs = 1024;
@@ -436,7 +441,7 @@ __device__ __forceinline__ float ray_cos(float nx, float ny, float nz, const flo
 }
 
 template <bool BOUNCE, int KB>
-__global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs a) {
+__global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kShadowMinBlocks) k_trace(TraceArgs a) {
   extern __shared__ float smem[];
   float* sdir = smem;                                     // [S*3]
   float* svis = sdir + 3 * a.S;                           // [warps][S]
@@ -582,7 +587,7 @@ __global__ void k_compact_pending(int64_t count, const uint32_t* __restrict__ pe
 // Index-matrix entries of the listed rays: one thread per ray. Neighbouring threads hold
 // rays of the same receiver, so a warp's walks start from the same origin.
 template <int KB>
-__global__ void __launch_bounds__(128) k_resolve(TraceArgs a, const uint32_t* __restrict__ list) {
+__global__ void __launch_bounds__(128, kBounceMinBlocks) k_resolve(TraceArgs a, const uint32_t* __restrict__ list) {
   const unsigned count = *a.queue_count;
   RayStats rs{0u, 0u, 0u, 0u, 0u};
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
