@@ -52,7 +52,7 @@ struct TraceArgs {
   unsigned int* work;
   unsigned long long* stats;  // nodes, leaves, hits, index rounds, traced rays (nullable)
   int64_t r0, r1;             // receivers [r0, r1) of this batch, in sorted (Morton) positions
-  void* queue;                // [batch * S] per-ray candidate records, resolved by k_resolve
+  void* queue;                // [batch * S] per-ray candidate records, resolved by k_prefix / k_rounds
   uint32_t* pending;          // [batch * S] 1 = the ray has index-matrix candidates
   unsigned int* queue_count;
 };
@@ -282,7 +282,7 @@ struct FrontBuf {
   }
 };
 
-// A ray whose visibility walk left index-matrix candidates: resolved by k_resolve.
+// A ray whose visibility walk left index-matrix candidates: resolved by k_prefix / k_rounds.
 template <int KB>
 struct QueueRec {
   int self;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
           traverse(a, r, root, 0.0f, sv, rs, rs.nodes);
           V = sv.T;
           // the buffer holds the KB nearest front-facing hits within the horizon; rays with
-          // candidates go to the queue that k_resolve works through
+          // candidates are listed for k_prefix (and, when needed, k_rounds)
           const int64_t slot = (int64_t)(self - a.r0) * a.S + s;
           if (sv.fb.count() == 0) {
             a.idx[(int64_t)gid * a.S + s] = -1;
@@ -577,22 +577,31 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
   }
 }
 
-// Slots of the rays that still have candidates, compacted in (receiver, direction) order.
-__global__ void k_compact_pending(int64_t count, const uint32_t* __restrict__ pending,
-                                  const uint32_t* __restrict__ incl, uint32_t* __restrict__ list) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count && pending[i]) list[incl[i] - 1] = (uint32_t)i;
-}
+// State of a ray whose first index-matrix round did not settle the argmax.
+struct RoundRec {
+  int self;
+  int s;
+  float t_hor;
+  float t_last;
+  int p_last;
+  float lt_base;
+  int best;
+  float lw_best;
+};
 
-// Index-matrix entries of the listed rays: one thread per ray. Neighbouring threads hold
-// rays of the same receiver, so a warp's walks start from the same origin.
+// First index-matrix round of the listed rays (one thread per ray): the prefix walk for the
+// candidates found by the visibility walk and the decision. Rays that need more rounds go to
+// a second queue for k_rounds.
 template <int KB>
-__global__ void __launch_bounds__(128, kBounceMinBlocks) k_resolve(TraceArgs a, const uint32_t* __restrict__ list) {
+__global__ void __launch_bounds__(128, kShadowMinBlocks) k_prefix(TraceArgs a, const uint32_t* __restrict__ list,
+                                                                  RoundRec* __restrict__ more,
+                                                                  unsigned int* __restrict__ more_count) {
   const unsigned count = *a.queue_count;
+  const float lfilter = logf(a.filter_t);
+  const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
   RayStats rs{0u, 0u, 0u, 0u, 0u};
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-    const uint32_t slot = list[q];
-    const QueueRec<KB> rec = static_cast<const QueueRec<KB>*>(a.queue)[slot];
+    const QueueRec<KB>& rec = static_cast<const QueueRec<KB>*>(a.queue)[list[q]];
     const int self = rec.self, s = rec.s;
     if (self < 0 || (int64_t)self >= a.n || s < 0 || s >= a.S) {
       set_status(a.status, PRTGS_STATUS_BAD_INDEX);
@@ -604,8 +613,73 @@ __global__ void __launch_bounds__(128, kBounceMinBlocks) k_resolve(TraceArgs a, 
     if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
     Ray r;
     make_ray(r, q0.x, q0.y, q0.z, __ldg(a.dirs + 3 * s), __ldg(a.dirs + 3 * s + 1), __ldg(a.dirs + 3 * s + 2));
-    const int best = index_search<KB>(a, r, root, self, rs, true, rec.t_hor, &rec.fb, -FLT_MAX, INT32_MIN, 0.0f,
-                                      -1, -FLT_MAX);
+    FrontBuf<KB> fb;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      fb.bt[k] = rec.fb.bt[k];
+      fb.bp[k] = rec.fb.bp[k];
+    }
+    const int nc = fb.count();
+    PrefixVis<KB> pb{a, r, self, rs, -FLT_MAX, INT32_MIN, fb, nc};
+#pragma unroll
+    for (int k = 0; k < KB; ++k) pb.lt[k] = 0.f;
+    traverse(a, r, root, 0.0f, pb, rs, rs.search_nodes);
+    float lw_best = -FLT_MAX;
+    int best = -1;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (k < nc && pb.lt[k] <= lfilter && pb.lt[k] >= lmin) {
+        const float lw = logf(rec.fb.ba[k]) + pb.lt[k] + logf(rec.fb.bm[k]);
+        if (lw > lw_best) {
+          lw_best = lw;
+          best = fb.bp[k];
+        }
+      }
+    }
+    bool settled = nc < KB;
+    float lt_next = 0.f;
+    if (!settled) {
+      lt_next = pb.lt[KB - 1] + log1pf(-rec.fb.ba[KB - 1]);
+      settled = lt_next <= lw_best || lt_next < lmin;
+    }
+    if (settled) {
+      a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
+    } else {
+      const unsigned m = atomicAdd(more_count, 1u);
+      more[m] = RoundRec{self, s, rec.t_hor, fb.bt[KB - 1], fb.bp[KB - 1], lt_next, best, lw_best};
+    }
+  }
+  if (a.stats) {
+    unsigned long long c1 = warp_sum_u64(rs.search_nodes), c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(a.stats + 1, c1);
+      atomicAdd(a.stats + 2, c2);
+      atomicAdd(a.stats + 3, c3);
+    }
+  }
+}
+
+// Further rounds for the rays k_prefix could not settle (one thread per ray).
+template <int KB>
+__global__ void __launch_bounds__(128, kBounceMinBlocks) k_rounds(TraceArgs a, const RoundRec* __restrict__ more,
+                                                                  const unsigned int* __restrict__ more_count) {
+  const unsigned count = *more_count;
+  RayStats rs{0u, 0u, 0u, 0u, 0u};
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    const RoundRec rec = more[q];
+    const int self = rec.self, s = rec.s;
+    if (self < 0 || (int64_t)self >= a.n || s < 0 || s >= a.S) {
+      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+      continue;
+    }
+    const float4 q0 = __ldg(a.recs + 4 * self);
+    const int gid = a.order[self];
+    int root = a.roots[find_scene(a.offsets, a.n_scenes, gid)];
+    if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
+    Ray r;
+    make_ray(r, q0.x, q0.y, q0.z, __ldg(a.dirs + 3 * s), __ldg(a.dirs + 3 * s + 1), __ldg(a.dirs + 3 * s + 2));
+    const int best = index_search<KB>(a, r, root, self, rs, false, rec.t_hor, nullptr, rec.t_last, rec.p_last,
+                                      rec.lt_base, rec.best, rec.lw_best);
     a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
   }
   if (a.stats) {
@@ -618,6 +692,13 @@ __global__ void __launch_bounds__(128, kBounceMinBlocks) k_resolve(TraceArgs a, 
       atomicAdd(a.stats + 4, c4);
     }
   }
+}
+
+// Slots of the rays that still have candidates, compacted in (receiver, direction) order.
+__global__ void k_compact_pending(int64_t count, const uint32_t* __restrict__ pending,
+                                  const uint32_t* __restrict__ incl, uint32_t* __restrict__ list) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && pending[i]) list[incl[i] - 1] = (uint32_t)i;
 }
 
 // ---- one-bounce self-transfer (Eq. 33) -------------------------------------------------------
@@ -798,7 +879,7 @@ size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_para
   if (p->flags & PRTGS_BOUNCE) {
     const size_t rays = (size_t)trace_batch(n, p->n_dirs) * p->n_dirs;
     b += align_up(queue_rec_bytes(index_buffer_of(p)) * rays) + 3 * align_up(sizeof(uint32_t) * rays) +
-         scan_workspace((int64_t)rays);
+         scan_workspace((int64_t)rays) + align_up(sizeof(RoundRec) * rays) + align_up(sizeof(unsigned int));
   }
   if (p->flags & PRTGS_GLOSSY) {
     b += 2 * align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + scan_workspace(n) +
@@ -809,11 +890,14 @@ size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_para
 
 template <bool BOUNCE, int KB>
 static int launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, uint32_t* incl, uint32_t* list,
-                        void* scan_ws, cudaStream_t stream) {
-  int per_sm = 0, per_sm_b = 0;
+                        void* scan_ws, RoundRec* more, unsigned int* more_count, cudaStream_t stream) {
+  int per_sm = 0, per_sm_b = 0, per_sm_r = 0;
   cudaFuncSetAttribute(k_trace<BOUNCE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<BOUNCE, KB>, kTraceThreads, smem);
-  if (BOUNCE) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_resolve<KB>, 128, 0);
+  if (BOUNCE) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_prefix<KB>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_rounds<KB>, 128, 0);
+  }
   for (int64_t r0 = 0; r0 < a.n; r0 += batch) {
     a.r0 = r0;
     a.r1 = r0 + batch < a.n ? r0 + batch : a.n;
@@ -824,7 +908,9 @@ static int launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, uint32
       int rc = scan_u32(a.pending, incl, rays, false, a.queue_count, scan_ws, stream);
       if (rc != PRTGS_OK) return rc;
       k_compact_pending<<<(unsigned)((rays + 255) / 256), 256, 0, stream>>>(rays, a.pending, incl, list);
-      k_resolve<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a, list);
+      cudaMemsetAsync(more_count, 0, sizeof(unsigned int), stream);
+      k_prefix<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a, list, more, more_count);
+      k_rounds<KB><<<sms * (per_sm_r > 0 ? per_sm_r : 1), 128, 0, stream>>>(a, more, more_count);
     }
   }
   return PRTGS_OK;
@@ -858,6 +944,8 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   uint32_t* incl = bounce ? c.take<uint32_t>(batch_rays) : nullptr;
   uint32_t* rlist = bounce ? c.take<uint32_t>(batch_rays) : nullptr;
   void* rscan_ws = bounce ? c.take<char>(scan_workspace((int64_t)batch_rays)) : nullptr;
+  RoundRec* more = bounce ? c.take<RoundRec>(batch_rays) : nullptr;
+  unsigned int* more_count = bounce ? c.take<unsigned int>(1) : nullptr;
   int32_t* slot = nullptr;
   int32_t* gids = nullptr;
   float* Vg = nullptr;
@@ -904,15 +992,15 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   const int64_t batch = bounce ? trace_batch(n, S) : n;
   int rct;
   if (!bounce) {
-    rct = launch_trace<false, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
+    rct = launch_trace<false, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, more, more_count, stream);
   } else if (kbq == 1) {
-    rct = launch_trace<true, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
+    rct = launch_trace<true, 1>(a, smem, sms, batch, incl, rlist, rscan_ws, more, more_count, stream);
   } else if (kbq == 2) {
-    rct = launch_trace<true, 2>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
+    rct = launch_trace<true, 2>(a, smem, sms, batch, incl, rlist, rscan_ws, more, more_count, stream);
   } else if (kbq == 4) {
-    rct = launch_trace<true, 4>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
+    rct = launch_trace<true, 4>(a, smem, sms, batch, incl, rlist, rscan_ws, more, more_count, stream);
   } else {
-    rct = launch_trace<true, 8>(a, smem, sms, batch, incl, rlist, rscan_ws, stream);
+    rct = launch_trace<true, 8>(a, smem, sms, batch, incl, rlist, rscan_ws, more, more_count, stream);
   }
   if (rct != PRTGS_OK) return rct;
   PRTGS_CHECK_LAUNCH();
