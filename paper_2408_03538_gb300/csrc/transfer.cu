@@ -26,6 +26,10 @@ constexpr int kTraceWarps = 4;
 // registers, the bounce walk and the resolve kernel at 128).
 constexpr int kShadowMinBlocks = 8;
 constexpr int kBounceMinBlocks = 4;
+#ifndef PRTGS_ROUND_HITS
+#define PRTGS_ROUND_HITS 16
+#endif
+constexpr int kRoundHits = PRTGS_ROUND_HITS;  // hits per round in k_rounds
 constexpr int kTraceThreads = 32 * kTraceWarps;
 constexpr int kDefaultIndexBuffer = 8;
 constexpr int kMaxDirs = 1024;
@@ -659,6 +663,72 @@ __global__ void __launch_bounds__(128, kShadowMinBlocks) k_prefix(TraceArgs a, c
   }
 }
 
+// Rounds over all hits: the KR nearest hits of any kind with key past the last processed one
+// (and t* within the horizon), processed in key order -- one walk per round.
+template <int KR>
+struct AllHitsVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float t_last;
+  int p_last;
+  float t_hor;
+  FrontBuf<KR> fb;  // here: every hit (ba = alpha, bm = max(-d.n, 0))
+  __device__ float t_hi() const { return fminf(slack_hi(fb.t_full()), slack_hi(t_hor)); }
+  __device__ bool stop() const { return false; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    if (!key_less(t_last, p_last, t, pos)) return;
+    fb.insert(t, pos, al, m);
+  }
+};
+
+template <int KR>
+__device__ int index_search_all(const TraceArgs& a, const Ray& r, int root, int self, RayStats& st, float t_hor,
+                                float t_last, int p_last, float lt, int best, float lw_best) {
+  const float lfilter = logf(a.filter_t);
+  const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
+  for (int64_t round = 0;; ++round) {
+    if (round > a.n / KR + 1) {
+      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+      break;
+    }
+    if (lt < lmin || lt <= lw_best) break;  // nothing past this point can be a better candidate
+    ++st.rounds;
+    AllHitsVis<KR> v{a, r, self, st, t_last, p_last, t_hor};
+    v.fb.clear();
+    traverse(a, r, root, t_last, v, st, st.search_nodes);
+    const int nh = v.fb.count();
+    bool decided = false;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (k < nh && !decided) {
+        if (lt < lmin || lt <= lw_best) {
+          decided = true;
+        } else {
+          if (v.fb.bm[k] > 0.f && lt <= lfilter) {
+            const float lw = logf(v.fb.ba[k] * v.fb.bm[k]) + lt;
+            if (lw > lw_best) {
+              lw_best = lw;
+              best = v.fb.bp[k];
+            }
+          }
+          lt += log1pf(-v.fb.ba[k]);
+        }
+      }
+    }
+    if (decided || nh < KR) break;
+    t_last = v.fb.bt[KR - 1];
+    p_last = v.fb.bp[KR - 1];
+  }
+  return best;
+}
+
 // Further rounds for the rays k_prefix could not settle (one thread per ray).
 template <int KB>
 __global__ void __launch_bounds__(128, kBounceMinBlocks) k_rounds(TraceArgs a, const RoundRec* __restrict__ more,
@@ -678,8 +748,8 @@ __global__ void __launch_bounds__(128, kBounceMinBlocks) k_rounds(TraceArgs a, c
     if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
     Ray r;
     make_ray(r, q0.x, q0.y, q0.z, __ldg(a.dirs + 3 * s), __ldg(a.dirs + 3 * s + 1), __ldg(a.dirs + 3 * s + 2));
-    const int best = index_search<KB>(a, r, root, self, rs, false, rec.t_hor, nullptr, rec.t_last, rec.p_last,
-                                      rec.lt_base, rec.best, rec.lw_best);
+    const int best = index_search_all<kRoundHits>(a, r, root, self, rs, rec.t_hor, rec.t_last, rec.p_last,
+                                                  rec.lt_base, rec.best, rec.lw_best);
     a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
   }
   if (a.stats) {
