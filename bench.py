@@ -299,12 +299,7 @@ def run_ours(args):
         e2e_ms += e0.elapsed_time(e1)
     clocks = sampler.stop()
     assert status.read() == 0
-    t_local = np.array([total_ms, e2e_ms, stage_ms[1]])
-    if world > 1:
-        tt = torch.tensor(t_local, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_local = tt.cpu().numpy()
-    total_ms, e2e_ms, transfer_ms = (float(x) for x in t_local)
+    total_ms, e2e_ms, transfer_ms = reduce_max_over_ranks([total_ms, e2e_ms, stage_ms[1]], dev)
     rays_per_step = g.n * S_
     value = world * rays_per_step * args.steps / (total_ms / 1e3)
     e2e_value = world * rays_per_step * args.steps / (e2e_ms / 1e3)
@@ -334,8 +329,8 @@ def run_ours(args):
     if hits_per_ray is not None:
         flops = traced * (hits_per_ray * 40.0 + 2.0 * C)
         achieved = flops / (transfer_ms / args.steps / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_trace (+k_bounce), per transfer call", "achieved": achieved,
-                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+        roof = {"bound": "alu", "kernel": "transfer call: k_trace, k_prefix, k_rounds, k_bounce", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": transfer_traffic_bytes(),
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz ({pk_kind} max clock)",
                 "algorithmic_flops_per_launch": flops}
     launches = launches_per_step(g.n, n_pairs, cam)
@@ -358,12 +353,37 @@ def run_ours(args):
         dist.barrier()
 
 
-def launches_per_step(n, n_pairs, cam):
-    """Kernel launches of one step, following the launch sequence of the library."""
+def reduce_max_over_ranks(values, device=None):
+    """Element-wise max of a list of floats over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def transfer_traffic_bytes():
+    """DRAM bytes per transfer call from the committed ncu summary (None if absent)."""
+    p = os.path.join(ROOT, "profiles", "dram_transfer_surface-100k.md")
+    try:
+        for line in open(p):
+            if line.startswith("traffic_bytes_per_transfer_call:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def launches_per_step(n, n_pairs, cam, n_dirs=256, bounce=True):
+    """Kernel launches of one bench step, following the launch sequence of the library."""
     scan = 3
-    sort_pass = 1 + scan + 1
-    bvh = 3 + 4 * sort_pass + 2 + 1  # bounds init/bounds/morton, 4 passes, karras + roots, pack/refit
-    transfer = 2  # trace, bounce
+    sort_pass = 1 + scan + 1  # histogram, scan, scatter
+    bvh = 3 + 4 * sort_pass + 3  # bounds init/bounds/morton, 4 passes of 8 key bits, karras + roots + pack/refit
+    batches = math.ceil(n / max(1, (1 << 23) // n_dirs)) if bounce else 1
+    transfer = batches * (1 + (scan + 3 if bounce else 0)) + (1 if bounce else 0)  # trace (+ compact/prefix/rounds), bounce
     relight = 1
     tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
     tile_bits = max(1, math.ceil(math.log2(tiles)))

@@ -31,7 +31,7 @@ constexpr int kBounceMinBlocks = 4;
 #endif
 constexpr int kRoundHits = PRTGS_ROUND_HITS;  // hits per round in k_rounds
 constexpr int kTraceThreads = 32 * kTraceWarps;
-constexpr int kDefaultIndexBuffer = 8;
+constexpr int kDefaultIndexBuffer = 4;
 constexpr int kMaxDirs = 1024;
 
 struct TraceArgs {

@@ -1,0 +1,61 @@
+"""Host logic of bench.py on CPU: max-over-ranks timing with two gloo ranks, launch counting."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        vals = bench.reduce_max_over_ranks([10.0 + rank, 5.0 - rank, rank * 3.0])
+        out[rank] = vals
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
+    for r in range(world):
+        assert out[r] == [11.0, 5.0, 3.0]
+
+
+def test_max_over_ranks_without_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.reduce_max_over_ranks([1.5, 2]) == [1.5, 2.0]
+
+
+def test_launch_count_and_traffic_file():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2408_03538_gb300 import scenes as S
+
+    cam = S.make_camera("surface-100k")
+    n = bench.launches_per_step(100_000, 2_000_000, cam)
+    assert 50 < n < 200
+    t = bench.transfer_traffic_bytes()
+    assert t is None or t > 0
