@@ -472,3 +472,67 @@ def test_radix_tree_batched_roots(oracle_mod):
         _check_radix_tree(out["keys"], out["children"], out["roots"][b], pos, pos + p.n - 1, out["order"])
         assert set(out["order"][pos:pos + p.n]) == set(range(offs[b], offs[b + 1]))
         pos += p.n
+
+
+# ------------------------------------------------------------------------------------------
+# Differentiable transfer (gradient oracle of the transfer backward)
+# ------------------------------------------------------------------------------------------
+def _crowd(n, seed):
+    sc = S.surface_scene(n, seed)
+    sc.means *= 0.25  # crowd them so that rays meet many occluders
+    sc.scales *= 1.5
+    return sc
+
+
+def test_torch_transfer_equals_c_oracle(oracle_mod):
+    import torch
+
+    from oracle import transfer_torch as TT
+
+    sc = _crowd(60, 3)
+    dirs = S.direction_set(48, 2)
+    ref = oracle_mod.transfer(sc, dirs, 3, np.arange(sc.n), t_min=0.0)
+    t = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    P = TT.transfer_P(t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(sc.normals), dirs,
+                      oracle_mod.sh(3, dirs)).numpy()
+    np.testing.assert_allclose(P, ref["P"], atol=1e-12)
+    assert ref["hits"].mean() > 3
+    # a receiver subset gives the same rows (every Gaussian still occludes)
+    recv = np.array([7, 0, 59, 31])
+    Ps = TT.transfer_P(t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(sc.normals), dirs,
+                       oracle_mod.sh(3, dirs), recv=recv).numpy()
+    np.testing.assert_allclose(Ps, ref["P"][recv], atol=1e-12)
+
+
+def test_torch_transfer_autograd_matches_central_differences(oracle_mod):
+    import torch
+
+    from oracle import transfer_torch as TT
+
+    sc = _crowd(40, 4)
+    dirs = S.direction_set(32, 3)
+    Y = oracle_mod.sh(2, dirs)
+    rng = np.random.default_rng(9)
+    wP = torch.as_tensor(rng.standard_normal((sc.n, 9)))
+    ps = [torch.tensor(np.asarray(getattr(sc, f), np.float64), requires_grad=True)
+          for f in ("means", "scales", "quats", "opacity", "normals")]
+
+    def f(p):
+        return (TT.transfer_P(*p, dirs, Y) * wP).sum()
+
+    grads = torch.autograd.grad(f(ps), ps)
+    h = 1e-7
+    checked = 0
+    for pi, p in enumerate(ps):
+        for k in rng.choice(p.numel(), size=6, replace=False):
+            pp = [q.detach().clone() for q in ps]
+            pm = [q.detach().clone() for q in ps]
+            pp[pi].reshape(-1)[k] += h
+            pm[pi].reshape(-1)[k] -= h
+            with torch.no_grad():
+                fd = (f(pp) - f(pm)).item() / (2 * h)
+            g = grads[pi].reshape(-1)[k].item()
+            assert abs(fd - g) <= 1e-5 * max(1.0, abs(fd)), (pi, k, fd, g)
+            checked += 1
+    assert checked == 30
+    assert float(grads[3].abs().sum()) > 0  # opacity matters
