@@ -184,6 +184,28 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
                               void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Transfer backward: gradients of a loss through P (the shadowed diffuse transfer of Eq. 29
+ * projected by Eq. 9) to the Gaussians, for optimising geometry against relit images
+ * (Sec. 4.4). Each traced ray is walked again twice in the forward's order -- once for
+ * V_is, once pushing dL/dalpha_j = -g V_is / (1 - alpha_j) to every occluder up to the same
+ * early exit -- so no per-ray hit list is stored. The hit set (t* > 0, D^2 <= 9) and the
+ * hemisphere test are held fixed (non-differentiable boundaries); the gradient flows through
+ * opacity_j exp(-D^2/2), D^2 at the closest approach (to mu_j, s_j, q_j and, via the ray
+ * origin, mu_i) and the cosine max(0, n_i.w) (to the raw normal n_i).
+ *   dP[n,C]      in (device)
+ *   d_means[n,3], d_scales[n,3], d_quats[n,4], d_opacity[n], d_normals[n,3]  out (device;
+ *                overwritten; accumulated with float atomics, so the last bits vary run to run)
+ * p->flags must be PRTGS_SHADOW or 0 (unshadowed: only d_normals is non-zero); PRTGS_BOUNCE or
+ * PRTGS_GLOSSY -> PRTGS_ERR_UNSUPPORTED. The bvh must have been built from the same g.
+ * Errors: as prtgs_precompute_transfer.
+ */
+size_t prtgs_transfer_backward_workspace_size(int64_t n, const prtgs_transfer_params* p);
+int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                       const float* dP, float* d_means, float* d_scales, float* d_quats,
+                                       float* d_opacity, float* d_normals, int32_t* status, void* workspace,
+                                       size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
  * Relight (Eq. 14; glossy Eq. 41):
  *   colors[k,n,3] = (albedo_i/pi) * (T_i[c] . L[k,c,:]) per channel c,
  * with T [n,C] (t_channels = 1) or [n,3,C] (t_channels = 3). Glossy splats (n_glossy > 0,

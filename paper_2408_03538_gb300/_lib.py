@@ -64,6 +64,10 @@ _SIGS = {
     "prtgs_transfer_workspace_size": (c_size_t, [c_int64, c_int64, P(TransferParams)]),
     "prtgs_precompute_transfer": (c_int32, [P(Gaussians), P(BVH), P(TransferParams), c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_int64, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_transfer_backward_workspace_size": (c_size_t, [c_int64, P(TransferParams)]),
+    "prtgs_precompute_transfer_backward": (c_int32, [P(Gaussians), P(BVH), P(TransferParams), c_void_p, c_void_p,
+                                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                     c_size_t, c_void_p]),
     "prtgs_relight_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "prtgs_relight": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t,

@@ -164,6 +164,31 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
     return res
 
 
+def precompute_transfer_backward(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int, dP: torch.Tensor,
+                                 shadow: bool = True, t_min: float = DEFAULT_T_MIN, status: Status | None = None,
+                                 stats: torch.Tensor | None = None):
+    """Gradients of a loss through P [n,C] (shadowed diffuse transfer) to the Gaussians:
+    dict of d_means [n,3], d_scales [n,3], d_quats [n,4], d_opacity [n], d_normals [n,3]."""
+    lib = L.load()
+    dev = g.means.device
+    n = g.n
+    f32 = dict(dtype=torch.float32, device=dev)
+    grads = {"d_means": torch.empty((n, 3), **f32), "d_scales": torch.empty((n, 3), **f32),
+             "d_quats": torch.empty((n, 4), **f32), "d_opacity": torch.empty((n,), **f32),
+             "d_normals": torch.empty((n, 3), **f32)}
+    dP = dP.contiguous()
+    p = L.TransferParams(order, int(dirs.shape[0]), _ptr(dirs), float(t_min), 1.0, L.SHADOW if shadow else 0, 0,
+                         _ptr(stats))
+    ws, nb = _ws(lib.prtgs_transfer_backward_workspace_size(n, ctypes.byref(p)), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_precompute_transfer_backward(
+        ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(dP), _ptr(grads["d_means"]),
+        _ptr(grads["d_scales"]), _ptr(grads["d_quats"]), _ptr(grads["d_opacity"]), _ptr(grads["d_normals"]),
+        status.ptr() if status else None, _ptr(ws), nb, _stream()), "prtgs_precompute_transfer_backward")
+    grads["_ws"] = ws
+    return grads
+
+
 # ------------------------------------------------------------------------------------------
 # Relight
 # ------------------------------------------------------------------------------------------

@@ -132,6 +132,32 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
                                     reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t prtgs_transfer_backward_workspace_size(int64_t n, const prtgs_transfer_params* p) {
+  if (!p || n < 0) return 0;
+  return transfer_backward_workspace(n, p);
+}
+
+int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                       const float* dP, float* d_means, float* d_scales, float* d_quats,
+                                       float* d_opacity, float* d_normals, int32_t* status, void* workspace,
+                                       size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
+  if ((rc = check_order(p->sh_order))) return rc;
+  if (p->flags & ~PRTGS_SHADOW) return PRTGS_ERR_UNSUPPORTED;
+  if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!p->dirs || !(p->t_min >= 0.f)) return PRTGS_ERR_INVALID_ARG;
+  if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
+  if (g->n == 0) return PRTGS_OK;
+  if (!dP || !g->normals || !d_means || !d_scales || !d_quats || !d_opacity || !d_normals)
+    return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, transfer_backward_workspace(g->n, p));
+  if (rc) return rc;
+  return finish(precompute_transfer_backward(g, bvh, p, dP, d_means, d_scales, d_quats, d_opacity, d_normals, status,
+                                             workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // ---- relight ----
 size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision) {
   if (n < 0 || k < 0) return 0;

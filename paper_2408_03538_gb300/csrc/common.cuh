@@ -142,4 +142,25 @@ __device__ __forceinline__ int find_scene(const int64_t* offsets, int n_scenes, 
   return lo;
 }
 
+// Gradient of a loss with respect to the (unnormalised) quaternion q = (w,x,y,z) given the
+// gradient gR with respect to R(q / |q|), R the rotation matrix of Eq. 2.
+__device__ __forceinline__ void quat_backward(float qw0, float qx0, float qy0, float qz0, const float gR[3][3],
+                                              float gq[4]) {
+  const float qn = sqrtf(qw0 * qw0 + qx0 * qx0 + qy0 * qy0 + qz0 * qz0);
+  const float qw = qw0 / qn, qx = qx0 / qn, qy = qy0 / qn, qz = qz0 / qn;
+  const float gw = 2.f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] +
+                          qx * gR[2][1]);
+  const float gx = 2.f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.f * qx * gR[1][1] - qw * gR[1][2] +
+                          qz * gR[2][0] + qw * gR[2][1] - 2.f * qx * gR[2][2]);
+  const float gy = 2.f * (-2.f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] + qz * gR[1][2] -
+                          qw * gR[2][0] + qz * gR[2][1] - 2.f * qy * gR[2][2]);
+  const float gz = 2.f * (-2.f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] -
+                          2.f * qz * gR[1][1] + qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
+  const float dot = qw * gw + qx * gx + qy * gy + qz * gz;
+  gq[0] = (gw - qw * dot) / qn;
+  gq[1] = (gx - qx * dot) / qn;
+  gq[2] = (gy - qy * dot) / qn;
+  gq[3] = (gz - qz * dot) / qn;
+}
+
 }  // namespace prtgs

@@ -30,6 +30,11 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
                         float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
                         cudaStream_t stream);
 
+size_t transfer_backward_workspace(int64_t n, const prtgs_transfer_params* p);
+int precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                 const float* dP, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream);
+
 // relight.cu
 size_t relight_workspace(int64_t n, int32_t order, int32_t k, int32_t precision);
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,

@@ -771,6 +771,267 @@ __global__ void k_compact_pending(int64_t count, const uint32_t* __restrict__ pe
   if (i < count && pending[i]) list[incl[i] - 1] = (uint32_t)i;
 }
 
+static int device_sms();
+
+// ---- transfer backward: dP -> the Gaussians (recomputed walks, no stored hit lists) ---------
+// Geometry of a hit needed by the gradient: the closest-approach offset w = p - mu in world
+// space and a = A w in the whitened frame (D^2 = |a|^2, stationary in t*).
+struct HitGeom {
+  float t, alpha, G;
+  float w[3], a[3], A[9];
+};
+
+__device__ __forceinline__ bool gauss_hit_geom(const float4* __restrict__ recs, int pos, const Ray& r, HitGeom& h) {
+  const float4 q0 = __ldg(recs + 4 * pos);
+  const float4 q1 = __ldg(recs + 4 * pos + 1);
+  const float4 q2 = __ldg(recs + 4 * pos + 2);
+  const float4 q3 = __ldg(recs + 4 * pos + 3);
+  float ux, uy, uz, ex, ey, ez;
+  two_sum(r.ox, -q0.x, ux, ex);
+  two_sum(r.oy, -q0.y, uy, ey);
+  two_sum(r.oz, -q0.z, uz, ez);
+  const float A[9] = {q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w, q3.x};
+  float da[3], ua[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    da[k] = fmaf(A[3 * k], r.dx, fmaf(A[3 * k + 1], r.dy, A[3 * k + 2] * r.dz));
+    ua[k] = fmaf(A[3 * k], ux, fmaf(A[3 * k + 1], uy, A[3 * k + 2] * uz));
+  }
+  const float dd = fmaf(da[0], da[0], fmaf(da[1], da[1], da[2] * da[2]));
+  const float rdd = 1.0f / dd;
+  const float t0 = -fmaf(ua[0], da[0], fmaf(ua[1], da[1], ua[2] * da[2])) * rdd;
+  const float w0[3] = {fmaf(t0, r.dx, ux) + ex, fmaf(t0, r.dy, uy) + ey, fmaf(t0, r.dz, uz) + ez};
+  float wa[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) wa[k] = fmaf(A[3 * k], w0[0], fmaf(A[3 * k + 1], w0[1], A[3 * k + 2] * w0[2]));
+  const float wd = fmaf(wa[0], da[0], fmaf(wa[1], da[1], wa[2] * da[2]));
+  const float dt = -wd * rdd;
+  const float ts = t0 + dt;
+  // the same decision as gauss_hit: D^2 from the refined closest point
+  const float d2 = fmaxf(fmaf(wa[0], wa[0], fmaf(wa[1], wa[1], wa[2] * wa[2])) + dt * wd, 0.0f);
+  if (!(ts > 0.0f) || !(d2 <= 9.0f)) return false;
+  h.t = ts;
+  h.G = expf(-0.5f * d2);
+  h.alpha = q0.w * h.G;
+  // offset and whitened offset at the refined closest point
+  h.w[0] = fmaf(dt, r.dx, w0[0]);
+  h.w[1] = fmaf(dt, r.dy, w0[1]);
+  h.w[2] = fmaf(dt, r.dz, w0[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    h.a[k] = fmaf(dt, da[k], wa[k]);
+    h.A[3 * k] = A[3 * k];
+    h.A[3 * k + 1] = A[3 * k + 1];
+    h.A[3 * k + 2] = A[3 * k + 2];
+  }
+  return true;
+}
+
+struct GradArgs {
+  const float* quats;
+  const float* dP;
+  float* d_means;
+  float* d_scales;
+  float* d_quats;
+  float* d_opacity;
+  float* d_normals;
+};
+
+// Second walk of a ray: the same hits, in the same order and up to the same early exit as
+// the visibility walk, each receiving dL/dalpha_j = g_V dV/dalpha_j = -g_V V / (1 - alpha_j).
+struct BwdVis {
+  const TraceArgs& a;
+  const GradArgs& g;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float T;      // running product (replays the forward cut-off)
+  float gVV;    // g_V * V
+  float go[3];  // gradient with respect to the ray origin (the receiver's mean)
+  __device__ float t_hi() const { return FLT_MAX; }
+  __device__ bool stop() const { return T < a.t_min; }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    HitGeom h;
+    if (!gauss_hit_geom(a.recs, pos, r, h)) return;
+    ++st.hits;
+    const float g_alpha = -gVV / (1.0f - h.alpha);
+    T *= 1.0f - h.alpha;
+    const int gid = a.order[pos];
+    atomicAdd(&g.d_opacity[gid], g_alpha * h.G);
+    const float g_d2 = g_alpha * (-0.5f * h.alpha);
+    // dD^2/dmu_j = -2 A^T a, dD^2/do = 2 A^T a
+    float at[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) at[k] = h.A[k] * h.a[0] + h.A[3 + k] * h.a[1] + h.A[6 + k] * h.a[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(&g.d_means[3 * gid + k], -2.0f * g_d2 * at[k]);
+      go[k] += 2.0f * g_d2 * at[k];
+    }
+    // A = diag(1/s) R^T: s_k = 1/|A_k.|, R[:,k] = s_k A_k.; dD^2/ds_k = -2 a_k^2 / s_k,
+    // dD^2/dR[j][k] = 2 a_k w_j / s_k
+    float gR[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float inv_s = sqrtf(h.A[3 * k] * h.A[3 * k] + h.A[3 * k + 1] * h.A[3 * k + 1] +
+                                h.A[3 * k + 2] * h.A[3 * k + 2]);  // 1 / s_k
+      atomicAdd(&g.d_scales[3 * gid + k], g_d2 * (-2.0f * h.a[k] * h.a[k] * inv_s));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gR[j][k] = g_d2 * 2.0f * h.a[k] * h.w[j] * inv_s;
+    }
+    float gq[4];
+    quat_backward(g.quats[4 * gid], g.quats[4 * gid + 1], g.quats[4 * gid + 2], g.quats[4 * gid + 3], gR, gq);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&g.d_quats[4 * gid + k], gq[k]);
+  }
+};
+
+__global__ void __launch_bounds__(kTraceThreads, kBounceMinBlocks) k_trace_bwd(TraceArgs a, GradArgs g) {
+  extern __shared__ float smem[];
+  float* sdir = smem;                                                               // [S*3]
+  unsigned short* slist = reinterpret_cast<unsigned short*>(sdir + 3 * a.S);         // [warps][S]
+  __shared__ unsigned int s_next[kTraceWarps];
+  for (int i = threadIdx.x; i < 3 * a.S; i += blockDim.x) sdir[i] = a.dirs[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned short* list = slist + warp * a.S;
+  const int C = sh_count(a.sh_order);
+  const float wq = 4.0f * kPi / (float)a.S;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  RayStats rs{0u, 0u, 0u, 0u, 0u};
+  for (;;) {
+    unsigned int wk = 0;
+    if (lane == 0) wk = atomicAdd(a.work, 1u);
+    wk = __shfl_sync(0xffffffffu, wk, 0);
+    if ((int64_t)wk >= a.n) break;
+    const int self = (int)wk;
+    const float4 q0 = __ldg(a.recs + 4 * self);
+    const float4 q3 = __ldg(a.recs + 4 * self + 3);
+    const int gid = a.order[self];
+    int root = a.roots[find_scene(a.offsets, a.n_scenes, gid)];
+    if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
+    float dP[kMaxC];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kMaxC; ++k) {
+      dP[k] = k < C ? g.dP[(int64_t)gid * C + k] : 0.f;
+      any |= dP[k] != 0.0f;
+    }
+    if (!any) continue;  // a receiver with dP_i = 0 contributes nothing (warp-uniform)
+    int cnt = 0;
+    for (int base = 0; base < a.S; base += 32) {
+      const int s = base + lane;
+      const float c = s < a.S ? ray_cos(q3.y, q3.z, q3.w, sdir + 3 * s) : 0.0f;
+      const bool up = c > 0.0f;
+      const unsigned m = __ballot_sync(0xffffffffu, up);
+      if (up) list[cnt + __popc(m & lt_mask)] = (unsigned short)s;
+      cnt += __popc(m);
+    }
+    if (lane == 0) s_next[warp] = 0;
+    __syncwarp();
+    float gn[3] = {0.f, 0.f, 0.f}, go[3] = {0.f, 0.f, 0.f};
+    for (;;) {
+      const unsigned t = atomicAdd(&s_next[warp], 1u);
+      if ((int)t >= cnt) break;
+      const int s = list[t];
+      const float* d = sdir + 3 * s;
+      const float c = ray_cos(q3.y, q3.z, q3.w, d);
+      float Y[kMaxC];
+      sh_eval_dyn(a.sh_order, d[0], d[1], d[2], Y);
+      float gsum = 0.f;  // w * sum_k dP_k Y_k
+#pragma unroll
+      for (int k = 0; k < kMaxC; ++k) gsum = fmaf(dP[k], Y[k], gsum);
+      gsum *= wq;
+      Ray r;
+      make_ray(r, q0.x, q0.y, q0.z, d[0], d[1], d[2]);
+      float V = 1.0f;
+      if (a.flags & PRTGS_SHADOW) {
+        ShadowVis sv{a, r, self, rs, 1.0f};
+        traverse(a, r, root, 0.0f, sv, rs, rs.nodes);
+        V = sv.T;
+      }
+      // dP/dc = w V Y: the receiver's normal (c = n . w)
+      gn[0] += gsum * V * d[0];
+      gn[1] += gsum * V * d[1];
+      gn[2] += gsum * V * d[2];
+      const float gV = gsum * c;
+      if ((a.flags & PRTGS_SHADOW) && gV != 0.0f) {
+        BwdVis bv{a, g, r, self, rs, 1.0f, gV * V, {0.f, 0.f, 0.f}};
+        traverse(a, r, root, 0.0f, bv, rs, rs.search_nodes);
+        go[0] += bv.go[0];
+        go[1] += bv.go[1];
+        go[2] += bv.go[2];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float vn = warp_sum(gn[k]);
+      const float vo = warp_sum(go[k]);
+      if (lane == 0) {
+        atomicAdd(&g.d_normals[3 * gid + k], vn);
+        atomicAdd(&g.d_means[3 * gid + k], vo);
+      }
+    }
+    __syncwarp();
+  }
+  if (a.stats) {
+    unsigned long long c0 = warp_sum_u64(rs.nodes), c1 = warp_sum_u64(rs.search_nodes),
+                       c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits);
+    if (lane == 0) {
+      atomicAdd(a.stats + 0, c0);
+      atomicAdd(a.stats + 1, c1);
+      atomicAdd(a.stats + 2, c2);
+      atomicAdd(a.stats + 3, c3);
+    }
+  }
+}
+
+int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                 const float* dP, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream) {
+  const int64_t n = gs->n;
+  cudaMemsetAsync(d_means, 0, sizeof(float) * 3 * n, stream);
+  cudaMemsetAsync(d_scales, 0, sizeof(float) * 3 * n, stream);
+  cudaMemsetAsync(d_quats, 0, sizeof(float) * 4 * n, stream);
+  cudaMemsetAsync(d_opacity, 0, sizeof(float) * n, stream);
+  cudaMemsetAsync(d_normals, 0, sizeof(float) * 3 * n, stream);
+  if (n == 0) return PRTGS_OK;
+  Carver c(ws);
+  unsigned int* work = c.take<unsigned int>(1);
+  cudaMemsetAsync(work, 0, sizeof(unsigned int), stream);
+  TraceArgs a{};
+  a.nodes = reinterpret_cast<const float4*>(bvh->nodes);
+  a.recs = reinterpret_cast<const float4*>(bvh->records);
+  a.order = bvh->order;
+  a.roots = bvh->roots;
+  a.offsets = bvh->scene_offsets;
+  a.n_scenes = bvh->n_scenes;
+  a.n = n;
+  a.dirs = p->dirs;
+  a.S = p->n_dirs;
+  a.sh_order = p->sh_order;
+  a.t_min = p->t_min;
+  a.filter_t = p->same_surface_t;
+  a.flags = p->flags;
+  a.status = status;
+  a.work = work;
+  a.stats = p->stats;
+  a.r0 = 0;
+  a.r1 = n;
+  GradArgs g{gs->quats, dP, d_means, d_scales, d_quats, d_opacity, d_normals};
+  const size_t smem = sizeof(float) * 3 * p->n_dirs + kTraceWarps * (size_t)p->n_dirs * 2;
+  int per_sm = 0;
+  cudaFuncSetAttribute(k_trace_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bwd, kTraceThreads, smem);
+  k_trace_bwd<<<device_sms() * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a, g);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
+size_t transfer_backward_workspace(int64_t, const prtgs_transfer_params*) { return align_up(sizeof(unsigned int)); }
+
 // ---- one-bounce self-transfer (Eq. 33) -------------------------------------------------------
 __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs, const float* __restrict__ normals,
                          const float* __restrict__ albedo, const float* __restrict__ P,

@@ -229,3 +229,116 @@ def test_glossy_matrices():
     M, allow = oracle.glossy(sc, dirs, 3, gids, tr["V"], Vallow)
     floor = 1e-3 * np.median(np.linalg.norm(M.reshape(len(M), -1), axis=1))
     _check_norm(out["M"], M, allow, floor)
+
+
+# ---- transfer backward (gradients of P through the recomputed walks) ----------------------
+_GRAD_FIELDS = ("means", "scales", "quats", "opacity", "normals")
+
+
+def _crowded(n, seed, f=0.4):
+    sc = S.surface_scene(n, seed)
+    sc.means *= f
+    sc.scales *= 1.5
+    return sc
+
+
+def _transfer_grads(sc, dirs, order, wP, shadow=True, t_min=0.0):
+    """(GPU gradients, FP64 autograd gradients) of L = sum(wP * P)."""
+    from oracle import transfer_torch as TT
+
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    d = torch.from_numpy(dirs).cuda()
+    out = api.precompute_transfer_backward(g, bvh, d, order, torch.from_numpy(wP).cuda(), shadow=shadow,
+                                           t_min=t_min, status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    gpu = {f: out["d_" + f].cpu().numpy().astype(np.float64) for f in _GRAD_FIELDS}
+    ps = [torch.tensor(np.asarray(getattr(sc, f), np.float64), requires_grad=True) for f in _GRAD_FIELDS]
+    Y = oracle.sh(order, dirs)
+    if shadow:
+        P = TT.transfer_P(*ps, dirs, Y)
+    else:  # unshadowed: V = 1, only the cosine depends on the Gaussians
+        dd = torch.as_tensor(np.asarray(dirs, np.float64))
+        c = ps[4] @ dd.T
+        P = torch.where((c > 0).detach(), 4.0 * math.pi / len(dirs) * c, torch.zeros_like(c)) @ torch.as_tensor(Y)
+    ref = torch.autograd.grad((P * torch.as_tensor(wP.astype(np.float64))).sum(), ps, allow_unused=True)
+    ref = {f: (r.numpy() if r is not None else np.zeros(getattr(sc, f).shape)) for f, r in zip(_GRAD_FIELDS, ref)}
+    return gpu, ref
+
+
+def _check_grads(gpu, ref, tol=2e-3):
+    """Norm-wise and element-wise per field; a field whose exact gradient vanishes (the rotation
+    of an isotropic Gaussian) is held to the FP32 residue, 1e-3 of the largest field's scale."""
+    top = max(np.linalg.norm(ref[f]) for f in _GRAD_FIELDS)
+    top_el = max(np.abs(ref[f]).max() for f in _GRAD_FIELDS)
+    for f in _GRAD_FIELDS:
+        a, b = gpu[f].ravel(), ref[f].ravel()
+        nb = max(np.linalg.norm(b), 1e-3 * top)
+        assert np.linalg.norm(a - b) <= tol * nb, (f, np.linalg.norm(a - b) / nb)
+        # element-wise: every entry within tol of the field's largest entry
+        np.testing.assert_allclose(a, b, rtol=0, atol=tol * max(np.abs(b).max(), 1e-3 * top_el), err_msg=f)
+
+
+@pytest.mark.parametrize("n,order,nd,t_min", [(300, 3, 64, 0.0), (600, 2, 48, api.DEFAULT_T_MIN), (257, 1, 33, 0.0)])
+def test_transfer_backward_matches_autograd(n, order, nd, t_min):
+    """dL/d(Gaussians) for L = sum(wP * P) against FP64 autograd through the brute-force P."""
+    sc = _crowded(n, 11 + n)
+    dirs = S.direction_set(nd, 5)
+    wP = np.random.default_rng(n).standard_normal((sc.n, (order + 1) ** 2)).astype(np.float32)
+    gpu, ref = _transfer_grads(sc, dirs, order, wP, t_min=t_min)
+    _check_grads(gpu, ref)
+    assert np.abs(ref["opacity"]).sum() > 0 and np.abs(ref["means"]).sum() > 0
+
+
+def test_transfer_backward_unshadowed_and_tiny():
+    sc = _crowded(200, 3)
+    dirs = S.direction_set(64, 1)
+    wP = np.random.default_rng(1).standard_normal((sc.n, 16)).astype(np.float32)
+    gpu, ref = _transfer_grads(sc, dirs, 3, wP, shadow=False)
+    _check_grads(gpu, ref)
+    for f in ("means", "scales", "quats", "opacity"):
+        assert not gpu[f].any()
+    # a lone Gaussian has no occluders; two Gaussians shadow each other at most
+    for n in (1, 2):
+        sc = _crowded(n, 4, f=0.01)
+        gpu, ref = _transfer_grads(sc, dirs, 3, wP[:n])
+        _check_grads(gpu, ref)
+
+
+def test_transfer_backward_full_size_sampled_receivers():
+    """diff-300k (300,000 isotropic Gaussians in [-1,1]^3, order 3, S = 128): dP is non-zero on
+    six receivers next to the faces of the cube with their normals facing out (inside it a
+    ray's visibility is ~1e-120, so there is no gradient to check), so the GPU gradient over all 300,000 Gaussians is exactly
+    theirs; FP64 autograd through the brute-force P takes them one at a time."""
+    from oracle import transfer_torch as TT
+
+    sc = S.make_scene("diff-300k")
+    dirs = S.direction_set(128, S.config_seed(3))
+    order = 3
+    rng = np.random.default_rng(21)
+    m = np.asarray(sc.means, np.float64)
+    face = np.argmax(np.abs(m), axis=1)
+    ar = np.arange(sc.n)
+    outward = np.asarray(sc.normals, np.float64)[ar, face] * np.sign(m[ar, face])
+    near_face = np.nonzero((np.abs(m[ar, face]) > 0.99) & (outward > 0.7))[0]
+    recv = np.sort(rng.choice(near_face, size=6, replace=False))
+    wP = np.zeros((sc.n, 16), np.float32)
+    wP[recv] = rng.standard_normal((recv.size, 16))
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    out = api.precompute_transfer_backward(g, bvh, torch.from_numpy(dirs).cuda(), order,
+                                           torch.from_numpy(wP).cuda(), status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    gpu = {f: out["d_" + f].cpu().numpy().astype(np.float64) for f in _GRAD_FIELDS}
+    ps = [torch.tensor(np.asarray(getattr(sc, f), np.float64), requires_grad=True) for f in _GRAD_FIELDS]
+    Y = oracle.sh(order, dirs)
+    for i in recv:
+        P = TT.transfer_P(*ps, dirs, Y, recv=[i])
+        (P * torch.as_tensor(wP[i:i + 1].astype(np.float64))).sum().backward()
+    ref = {f: p.grad.numpy() for f, p in zip(_GRAD_FIELDS, ps)}
+    _check_grads(gpu, ref)
+    assert np.count_nonzero(ref["opacity"]) > 100
