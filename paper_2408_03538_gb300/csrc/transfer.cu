@@ -800,6 +800,14 @@ __device__ __forceinline__ bool gauss_hit_geom(const float4* __restrict__ recs, 
   const float dd = fmaf(da[0], da[0], fmaf(da[1], da[1], da[2] * da[2]));
   const float rdd = 1.0f / dd;
   const float t0 = -fmaf(ua[0], da[0], fmaf(ua[1], da[1], ua[2] * da[2])) * rdd;
+  // the forward's cheap rejections (margins above the error of the first estimate)
+  {
+    const float wx0 = fmaf(t0, da[0], ua[0]), wy0 = fmaf(t0, da[1], ua[1]), wz0 = fmaf(t0, da[2], ua[2]);
+    const float d2a = fmaf(wx0, wx0, fmaf(wy0, wy0, wz0 * wz0));
+    const float un = sqrtf(fmaf(ua[0], ua[0], fmaf(ua[1], ua[1], ua[2] * ua[2])));
+    if (d2a > 9.0f + 1e-3f + 5e-5f * un) return false;
+    if (t0 < -(4e-6f * un * sqrtf(rdd) + 1e-30f)) return false;
+  }
   const float w0[3] = {fmaf(t0, r.dx, ux) + ex, fmaf(t0, r.dy, uy) + ey, fmaf(t0, r.dz, uz) + ez};
   float wa[3];
 #pragma unroll
