@@ -950,7 +950,8 @@ __global__ void __launch_bounds__(kTraceThreads, kBounceMinBlocks) k_trace_bwd(T
       sh_eval_dyn(a.sh_order, d[0], d[1], d[2], Y);
       float gsum = 0.f;  // w * sum_k dP_k Y_k
 #pragma unroll
-      for (int k = 0; k < kMaxC; ++k) gsum = fmaf(dP[k], Y[k], gsum);
+      for (int k = 0; k < kMaxC; ++k)
+        if (k < C) gsum = fmaf(dP[k], Y[k], gsum);  // Y holds only the first C values
       gsum *= wq;
       Ray r;
       make_ray(r, q0.x, q0.y, q0.z, d[0], d[1], d[2]);
