@@ -337,9 +337,9 @@ def l2_loss(image, target):
 class RelitRender(torch.autograd.Function):
     """image = render(relight(T, albedo, L)) with the hand-written backward kernels.
 
-    Differentiable in means, scales, quats, opacity, albedo and the light SH; the
-    precomputed transfer T is a constant (the paper freezes geometry after ray tracing,
-    Sec. 4.4).
+    Differentiable in means, scales, quats, opacity, albedo, the light SH and T. The paper
+    freezes geometry after ray tracing (Sec. 4.4), so T is usually a constant; produced by
+    ShadowedTransfer instead, its gradient reaches the geometry through the transfer too.
     """
 
     @staticmethod
@@ -358,11 +358,39 @@ class RelitRender(torch.autograd.Function):
         g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
                             normals.contiguous(), albedo.contiguous())
         dm, ds, dq, do, dcol = render_backward(g, colors, ctx.cam, ctx.bg, ctx.state, dimage.contiguous())
-        da, _, dL = relight_backward(T.contiguous(), g.albedo, Lsh.contiguous(), ctx.order, dcol)
-        return dm, ds, dq, do, da, dL, None, None, None, None, None, None
+        need_dT = ctx.needs_input_grad[6]
+        da, dT, dL = relight_backward(T.contiguous(), g.albedo, Lsh.contiguous(), ctx.order, dcol, need_dT=need_dT)
+        return dm, ds, dq, do, da, dL, dT, None, None, None, None, None
 
 
 def relit_render(means, scales, quats, opacity, albedo, Lsh, T, normals, cam, order, bg=None, max_pairs=None):
     if bg is None:
         bg = torch.zeros(3, dtype=torch.float32, device=means.device)
     return RelitRender.apply(means, scales, quats, opacity, albedo, Lsh, T, normals, cam, order, bg, max_pairs)
+
+
+class ShadowedTransfer(torch.autograd.Function):
+    """P = shadowed diffuse transfer of every Gaussian (Eq. 29 projected by Eq. 9) with the
+    hand-written backward that recomputes the walks. Differentiable in means, scales, quats,
+    opacity and normals; the hit set and the hemisphere are held fixed."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, normals, albedo, dirs, order, t_min):
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                            normals.contiguous(), albedo.contiguous())
+        st = Status()
+        bvh = build_bvh(g, status=st)
+        P = precompute_transfer(g, bvh, dirs, order, t_min=t_min, status=st)["P"]
+        ctx.g, ctx.bvh, ctx.st, ctx.dirs, ctx.order, ctx.t_min = g, bvh, st, dirs, order, t_min
+        return P
+
+    @staticmethod
+    def backward(ctx, dP):
+        gr = precompute_transfer_backward(ctx.g, ctx.bvh, ctx.dirs, ctx.order, dP.contiguous(), t_min=ctx.t_min,
+                                          status=ctx.st)
+        return (gr["d_means"], gr["d_scales"], gr["d_quats"], gr["d_opacity"], gr["d_normals"], None, None, None,
+                None)
+
+
+def shadowed_transfer(means, scales, quats, opacity, normals, albedo, dirs, order, t_min=DEFAULT_T_MIN):
+    return ShadowedTransfer.apply(means, scales, quats, opacity, normals, albedo, dirs, order, t_min)
