@@ -573,6 +573,20 @@ def run_diff(args):
         total += a.elapsed_time(b)
     clocks = sampler.stop()
     total, = reduce_max_over_ranks([total], dev)
+    # once, outside the timed step: the transfer backward with dP = dL/dT of the step's loss
+    # (the geometry gradient through the transfer; both walks of every traced ray recomputed)
+    colors = api.relight(P, g.albedo, L1, w["order"])
+    img, _ = api.render(g, colors, cam, bg, state=state)
+    _, dimg = api.l2_loss(img, target)
+    dcol = api.render_backward(g, colors, cam, bg, state, dimg)[4]
+    dP = api.relight_backward(P, g.albedo, L1, w["order"], dcol, need_dT=True)[1]
+    api.precompute_transfer_backward(g, bvh, dirs, w["order"], dP)  # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    api.precompute_transfer_backward(g, bvh, dirs, w["order"], dP)
+    e1.record()
+    e1.synchronize()
+    transfer_bwd_ms = e0.elapsed_time(e1)
     traced = int((sc.normals.astype(np.float64) @ dirs.cpu().numpy().astype(np.float64).T > 0).sum())
     line = {"metric": METRIC, "value": world * args.steps / (total / 1e3), "unit": "relit 1080p frames/s (fwd+bwd)",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
@@ -582,6 +596,8 @@ def run_diff(args):
                        "l2": "flushed between steps (256 MB write)"},
             "transfer_once": {"ms": transfer_ms, "rays_per_s": g.n * int(dirs.shape[0]) / (transfer_ms / 1e3),
                               "traced_rays": traced},
+            "transfer_backward_once": {"ms": transfer_bwd_ms,
+                                       "rays_per_s": g.n * int(dirs.shape[0]) / (transfer_bwd_ms / 1e3)},
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
