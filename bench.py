@@ -587,7 +587,11 @@ def run_diff(args):
     e1.record()
     e1.synchronize()
     transfer_bwd_ms = e0.elapsed_time(e1)
-    traced = int((sc.normals.astype(np.float64) @ dirs.cpu().numpy().astype(np.float64).T > 0).sum())
+    up = sc.normals.astype(np.float64) @ dirs.cpu().numpy().astype(np.float64).T > 0
+    traced = int(up.sum())
+    # receivers with dP_i = 0 (no pixel sees them) are skipped by the backward
+    has_grad = (dP.reshape(g.n, -1) != 0).any(dim=1).cpu().numpy()
+    n_grad, traced_grad = int(has_grad.sum()), int(up[has_grad].sum())
     line = {"metric": METRIC, "value": world * args.steps / (total / 1e3), "unit": "relit 1080p frames/s (fwd+bwd)",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -596,8 +600,9 @@ def run_diff(args):
                        "l2": "flushed between steps (256 MB write)"},
             "transfer_once": {"ms": transfer_ms, "rays_per_s": g.n * int(dirs.shape[0]) / (transfer_ms / 1e3),
                               "traced_rays": traced},
-            "transfer_backward_once": {"ms": transfer_bwd_ms,
-                                       "rays_per_s": g.n * int(dirs.shape[0]) / (transfer_bwd_ms / 1e3)},
+            "transfer_backward_once": {"ms": transfer_bwd_ms, "receivers_with_gradient": n_grad,
+                                       "traced_rays": traced_grad,
+                                       "traced_rays_per_s": traced_grad / (transfer_bwd_ms / 1e3)},
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
