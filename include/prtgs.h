@@ -141,9 +141,10 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *                   transmittance in front of it is <= t; 1 disables the filter.
  *   flags           PRTGS_SHADOW | PRTGS_BOUNCE | PRTGS_GLOSSY
  *   index_buffer    tuning: candidates per index-matrix search round (1, 2, 4 or 8; 0 = default)
- *   stats           optional device uint64[6] that the call ADDS its work counters to:
+ *   stats           optional device uint64[8] that the call ADDS its work counters to:
  *                   BVH node visits of the visibility walks, node visits of the index-matrix
- *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays
+ *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays, rays
+ *                   queued for the first index-matrix round, rays that needed later rounds
  *                   (NULL = not gathered)
  */
 typedef struct prtgs_transfer_params {

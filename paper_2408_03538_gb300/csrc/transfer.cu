@@ -604,7 +604,9 @@ __global__ void __launch_bounds__(128, kShadowMinBlocks) k_prefix(TraceArgs a, c
   const float lfilter = logf(a.filter_t);
   const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
   RayStats rs{0u, 0u, 0u, 0u, 0u};
+  unsigned n_first = 0, n_more = 0;
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    ++n_first;
     const QueueRec<KB>& rec = static_cast<const QueueRec<KB>*>(a.queue)[list[q]];
     const int self = rec.self, s = rec.s;
     if (self < 0 || (int64_t)self >= a.n || s < 0 || s >= a.S) {
@@ -651,14 +653,18 @@ __global__ void __launch_bounds__(128, kShadowMinBlocks) k_prefix(TraceArgs a, c
     } else {
       const unsigned m = atomicAdd(more_count, 1u);
       more[m] = RoundRec{self, s, rec.t_hor, fb.bt[KB - 1], fb.bp[KB - 1], lt_next, best, lw_best};
+      ++n_more;
     }
   }
   if (a.stats) {
-    unsigned long long c1 = warp_sum_u64(rs.search_nodes), c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits);
+    unsigned long long c1 = warp_sum_u64(rs.search_nodes), c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits),
+                       c6 = warp_sum_u64(n_first), c7 = warp_sum_u64(n_more);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(a.stats + 1, c1);
       atomicAdd(a.stats + 2, c2);
       atomicAdd(a.stats + 3, c3);
+      atomicAdd(a.stats + 6, c6);
+      atomicAdd(a.stats + 7, c7);
     }
   }
 }
