@@ -213,7 +213,10 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
  * glossy_ids[n_glossy] their Gaussian indices, M[n_glossy,C,C]) use
  *   t_eff[a] = sum_b M[a,b] Y_b(v_i), v_i = normalize(cam_pos - mean_i).
  * L[k,3,C] light SH per light and channel. precision: PRTGS_PREC_*. The tensor-core paths
- * need t_channels = 1 and n_glossy = 0, otherwise PRTGS_ERR_UNSUPPORTED.
+ * take every row through tcgen05 (one MMA of N = 3k for t_channels = 1, three of N = k for
+ * t_channels = 3) and then rewrite the glossy rows in FP32; they need 3k <= 256 (t_channels 1)
+ * or k <= 160 (t_channels 3: three accumulators in the 512 TMEM columns), otherwise
+ * PRTGS_ERR_UNSUPPORTED.
  * cam_pos and means may be NULL when n_glossy == 0.
  */
 size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision);
@@ -227,7 +230,8 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
  * scene_offsets[b+1] (device int64 [n_scenes+1]) and has its own k lights
  * L[b,k,3,C] (device). colors[3 k n] holds one contiguous [k, n_b, 3] block per scene,
  * scene b's block starting at float 3 k scene_offsets[b] (the input layout of prtgs_render
- * for that scene). No workspace. Tensor-core precisions need t_channels = 1 and 3k <= 256.
+ * for that scene). No workspace. Tensor-core precisions need 3k <= 256 (t_channels 1) or
+ * k <= 160 (t_channels 3).
  */
 int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
                           const int64_t* scene_offsets, int32_t n_scenes, const float* L, int32_t k,

@@ -192,7 +192,8 @@ int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
   if (n == 0 || k == 0) return PRTGS_OK;
   if (!T || !albedo || !L || !colors || !scene_offsets) return PRTGS_ERR_INVALID_ARG;
-  if (precision != PRTGS_PREC_FP32 && 3 * k > 256) return PRTGS_ERR_UNSUPPORTED;
+  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_shape(k, t_channels, nullptr, nullptr))
+    return PRTGS_ERR_UNSUPPORTED;
   return finish(relight_batched(n, sh_order, T, t_channels, albedo, scene_offsets, n_scenes, L, k, precision,
                                 colors, reinterpret_cast<cudaStream_t>(stream)));
 }

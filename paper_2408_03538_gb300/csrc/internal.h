@@ -43,6 +43,12 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
 int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                     const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
                     float* colors, cudaStream_t stream);
+// relight_tc.cu
+int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad, int* tmem_cols);
+int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,
+               int32_t k, int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors,
+               cudaStream_t stream);
+
 size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k);
 int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                      const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,

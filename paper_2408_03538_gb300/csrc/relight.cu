@@ -9,7 +9,9 @@ namespace prtgs {
 constexpr int kRelightThreads = 256;
 constexpr int kMaxLightsSmem = 256;
 
-// One thread per Gaussian; the lights sit in shared memory.
+// One thread per Gaussian; the lights sit in shared memory. (Staging each warp's 384-byte
+// rows through shared memory for 16-byte stores measured slower here: L2 merges the
+// 12-byte-stride stores.)
 template <int C, int TCH>
 __global__ void __launch_bounds__(kRelightThreads) k_relight(int64_t n, const float* __restrict__ T,
                                                              const float* __restrict__ albedo,
@@ -98,14 +100,14 @@ static void launch_relight_c(int64_t n, const float* T, int tch, const float* al
                              float* colors, cudaStream_t stream) {
   size_t smem = sizeof(float) * k * 3 * C;
   unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
-  if (tch == 3)
+  if (tch == 3) {
+    cudaFuncSetAttribute(k_relight<C, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_relight<C, 3><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
-  else
+  } else {
+    cudaFuncSetAttribute(k_relight<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_relight<C, 1><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
+  }
 }
-
-int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
-               int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors, cudaStream_t stream);
 
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
             const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
@@ -113,16 +115,18 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
   if (n == 0 || k == 0) return PRTGS_OK;
   if (k > kMaxLightsSmem) return PRTGS_ERR_UNSUPPORTED;
   if (precision != PRTGS_PREC_FP32) {
-    if (t_channels != 1 || n_glossy > 0) return PRTGS_ERR_UNSUPPORTED;
-    return relight_tc(n, order, T, albedo, L, k, precision, nullptr, 1, colors, stream);
+    // every row on the tensor cores; glossy rows are then rewritten by the glossy kernel
+    const int rc = relight_tc(n, order, T, t_channels, albedo, L, k, precision, nullptr, 1, colors, stream);
+    if (rc != PRTGS_OK) return rc;
+  } else {
+    switch (order) {
+      case 1: launch_relight_c<4>(n, T, t_channels, albedo, L, k, colors, stream); break;
+      case 2: launch_relight_c<9>(n, T, t_channels, albedo, L, k, colors, stream); break;
+      case 3: launch_relight_c<16>(n, T, t_channels, albedo, L, k, colors, stream); break;
+      default: return PRTGS_ERR_UNSUPPORTED;
+    }
+    PRTGS_CHECK_LAUNCH();
   }
-  switch (order) {
-    case 1: launch_relight_c<4>(n, T, t_channels, albedo, L, k, colors, stream); break;
-    case 2: launch_relight_c<9>(n, T, t_channels, albedo, L, k, colors, stream); break;
-    case 3: launch_relight_c<16>(n, T, t_channels, albedo, L, k, colors, stream); break;
-    default: return PRTGS_ERR_UNSUPPORTED;
-  }
-  PRTGS_CHECK_LAUNCH();
   if (n_glossy > 0) {
     const int C = sh_count(order);
     size_t smem = sizeof(float) * k * 3 * C;
@@ -193,10 +197,8 @@ int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels
                     const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
                     float* colors, cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
-  if (precision != PRTGS_PREC_FP32) {
-    if (t_channels != 1) return PRTGS_ERR_UNSUPPORTED;
-    return relight_tc(n, order, T, albedo, L, k, precision, offsets, n_scenes, colors, stream);
-  }
+  if (precision != PRTGS_PREC_FP32)
+    return relight_tc(n, order, T, t_channels, albedo, L, k, precision, offsets, n_scenes, colors, stream);
   switch (order) {
     case 1: launch_relight_batched_c<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
     case 2: launch_relight_batched_c<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;

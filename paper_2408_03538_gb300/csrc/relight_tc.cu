@@ -1,7 +1,9 @@
 // Relight contraction on the 5th-generation tensor cores (tcgen05), Eq. 14:
-//   D[i, (l,c)] = sum_m T[i,m] L[l,c,m],   colors[l,i,c] = (rho_i[c] / pi) D[i, (l,c)]
-// as a [128 x K'] x [K' x N] product per tile of 128 Gaussians, N = 3k padded to a multiple
-// of 16 (<= 256), accumulated in FP32 in tensor memory.
+//   scalar T [n,C]:   D[i, 3l+c] = sum_m T[i,m] L[l,c,m]       (one MMA, N = 3k)
+//   RGB T [n,3,C]:    D_c[i, l]  = sum_m T[i,c,m] L[l,c,m]     (three MMAs, N = k each)
+//   colors[l,i,c] = (rho_i[c] / pi) D
+// per tile of 128 Gaussians, N padded to a multiple of 16 (<= 256), accumulated in FP32 in
+// tensor memory.
 //
 // Precision. PRTGS_PREC_BF16 feeds bf16(T) and bf16(L) (one K = 16 slab). PRTGS_PREC_BF16X3
 // splits both operands into three BF16 terms, x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1),
@@ -11,11 +13,13 @@
 // higher-precision computations", 2019). The dropped terms are below 2^-24 relative.
 //
 // Data movement. The operands are transformed on the way in (split into BF16 terms), so they
-// are staged with ordinary coalesced loads and stores into shared memory in the canonical
-// no-swizzle K-major layout: 8-row x 16-byte core matrices, core matrices adjacent in K
-// 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride byte offset).
-// One elected thread issues the MMAs; completion is signalled through an mbarrier
-// (tcgen05.commit); each warp then reads its 32 accumulator lanes with tcgen05.ld.
+// are staged with ordinary loads (16-byte loads of the T rows) and stores into shared memory in
+// the canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, core matrices
+// adjacent in K 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride
+// byte offset). One elected thread issues the MMAs; completion is signalled through an
+// mbarrier (tcgen05.commit); each warp then reads its 32 accumulator lanes with tcgen05.ld,
+// eight lights (24 columns) at a time, and stores each row's three channels directly (staging
+// the rows through shared memory for 16-byte stores measured slower: L2 merges them).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -64,44 +68,53 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
   c = __float2bfloat16_rn(r);
 }
 
+// Two BF16 values as one 32-bit word, the first in the low half (the lower K index).
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 // Which split term of T and of L each K slab multiplies (BF16X3).
 __device__ __forceinline__ int a_term(int slab) { return slab == 2 || slab == 4 ? 1 : (slab == 5 ? 2 : 0); }
 __device__ __forceinline__ int b_term(int slab) { return slab == 1 || slab == 4 ? 1 : (slab == 3 ? 2 : 0); }
 
-// B operand (the split light SH of one scene) into shared memory.
-template <int C>
-__device__ __forceinline__ void load_lights(unsigned char* sB, const float* __restrict__ L, int nout, int n_pad,
+// B operand (the split light SH of one scene) into shared memory: for scalar T one group
+// whose row o = 3l + c is L[l][c][:]; for RGB T group c whose row l is L[l][c][:].
+template <int C, int TCH>
+__device__ __forceinline__ void load_lights(unsigned char* sB, const float* __restrict__ L, int k, int n_pad,
                                             int slabs) {
-  for (int e = threadIdx.x; e < slabs * n_pad * 16; e += kTcThreads) {
-    const int slab = e / (n_pad * 16), rem = e % (n_pad * 16);
+  const int rows = TCH == 1 ? 3 * k : k;
+  const int per_group = slabs * n_pad * 16;
+  for (int e = threadIdx.x; e < TCH * per_group; e += kTcThreads) {
+    const int g = e / per_group, rem0 = e % per_group;
+    const int slab = rem0 / (n_pad * 16), rem = rem0 % (n_pad * 16);
     const int row = rem / 16, kk = rem % 16;
     float v = 0.f;
-    if (row < nout && kk < C) v = L[(int64_t)row * C + kk];  // L[l][c][m] with row = 3l + c
+    if (row < rows && kk < C) v = TCH == 1 ? L[(int64_t)row * C + kk] : L[((int64_t)row * 3 + g) * C + kk];
     __nv_bfloat16 t1, t2, t3;
     split3(v, t1, t2, t3);
     const int term = slabs == 1 ? 0 : b_term(slab);
     const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
-    *reinterpret_cast<__nv_bfloat16*>(sB + slab * n_pad * 32 + kmajor_offset(row, kk)) = sel;
+    *reinterpret_cast<__nv_bfloat16*>(sB + (g * slabs + slab) * n_pad * 32 + kmajor_offset(row, kk)) = sel;
   }
 }
 
 // offsets == nullptr: one scene with lights L. Otherwise scene b (rows offsets[b] ..
 // offsets[b+1]) uses lights L + b * k * 3 * C; a tile that straddles scenes is run once per
-// scene with the other rows zeroed.
-template <int C>
+// scene with the other rows zeroed. n_pad: N of each MMA; TMEM group g starts at column
+// g * n_pad.
+template <int C, int TCH>
 __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const float* __restrict__ T,
                                                            const float* __restrict__ albedo,
                                                            const float* __restrict__ L, int k, int n_pad, int slabs,
                                                            int tmem_cols, const int64_t* __restrict__ offsets,
                                                            int n_scenes, float* __restrict__ colors) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // layout: [A slabs][B slabs], each region 1024-aligned
+  // layout: [A groups x slabs][B groups x slabs]
   unsigned char* sA = smem_raw;
-  unsigned char* sB = smem_raw + slabs * kSlabBytesA;
+  unsigned char* sB = smem_raw + TCH * slabs * kSlabBytesA;
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nout = 3 * k;
+  const int tid = threadIdx.x, warp = tid >> 5;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -117,6 +130,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16(kTcRows, n_pad);
+  const bool t_vec = (reinterpret_cast<uintptr_t>(T) & 15) == 0;  // 16-byte row loads need it
   uint32_t phase = 0;
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
   int cached = -1;
@@ -126,9 +140,25 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const int b_first = offsets ? find_scene(offsets, n_scenes, row0) : 0;
     const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
     const int64_t gi = row0 + tid;
-    float tv[16];
+    float tv[TCH][16];
+    if (C == 16 && t_vec && gi < n) {
+      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) tv[m] = (gi < n && m < C) ? __ldg(T + gi * C + m) : 0.f;
+      for (int g = 0; g < TCH; ++g)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = __ldg(src + 4 * g + q);
+          tv[g][4 * q] = v.x;
+          tv[g][4 * q + 1] = v.y;
+          tv[g][4 * q + 2] = v.z;
+          tv[g][4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+      for (int g = 0; g < TCH; ++g)
+#pragma unroll
+        for (int m = 0; m < 16; ++m) tv[g][m] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
+    }
     float rho[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
 #pragma unroll
@@ -139,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t hi = offsets ? (offsets[b + 1] < row_end ? offsets[b + 1] : row_end) : row_end;
       if (hi <= lo) continue;  // empty scene (uniform over the block)
       if (b != cached) {
-        load_lights<C>(sB, L + (int64_t)b * k * 3 * C, nout, n_pad, slabs);
+        load_lights<C, TCH>(sB, L + (int64_t)b * k * 3 * C, k, n_pad, slabs);
         cached = b;
       }
       const bool mine = gi >= lo && gi < hi;
@@ -147,15 +177,27 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t ob = offsets ? offsets[b] : 0;
       const int64_t nb = offsets ? offsets[b + 1] - ob : n;
       float* cb = colors + 3 * (int64_t)k * ob;
-      // A operand: this thread's row, split into BF16 terms (zero outside the scene)
+      // A operand: this thread's row(s), split into BF16 terms (zero outside the scene). In the
+      // K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte runs: two 16-byte
+      // stores per slab.
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        __nv_bfloat16 t1, t2, t3;
-        split3(mine ? tv[m] : 0.f, t1, t2, t3);
+      for (int g = 0; g < TCH; ++g) {
+        uint32_t pk[3][8];  // term x (pairs of K)
+#pragma unroll
+        for (int m = 0; m < 16; m += 2) {
+          __nv_bfloat16 a1, a2, a3, b1, b2, b3;
+          split3(mine ? tv[g][m] : 0.f, a1, a2, a3);
+          split3(mine ? tv[g][m + 1] : 0.f, b1, b2, b3);
+          pk[0][m / 2] = pack_bf16x2(a1, b1);
+          pk[1][m / 2] = pack_bf16x2(a2, b2);
+          pk[2][m / 2] = pack_bf16x2(a3, b3);
+        }
         for (int slab = 0; slab < slabs; ++slab) {
           const int term = slabs == 1 ? 0 : a_term(slab);
-          const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
-          *reinterpret_cast<__nv_bfloat16*>(sA + slab * kSlabBytesA + kmajor_offset(tid, m)) = sel;
+          unsigned char* base = sA + (g * slabs + slab) * kSlabBytesA;
+          const uint32_t* q = term == 0 ? pk[0] : (term == 1 ? pk[1] : pk[2]);
+          *reinterpret_cast<uint4*>(base + kmajor_offset(tid, 0)) = make_uint4(q[0], q[1], q[2], q[3]);
+          *reinterpret_cast<uint4*>(base + kmajor_offset(tid, 8)) = make_uint4(q[4], q[5], q[6], q[7]);
         }
       }
       // make the generic-proxy stores visible to the tensor core's async proxy
@@ -163,15 +205,16 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int slab = 0; slab < slabs; ++slab) {
-          const uint64_t da = smem_desc(smem_u32(sA + slab * kSlabBytesA), 128, 256);
-          const uint64_t db = smem_desc(smem_u32(sB + slab * n_pad * 32), 128, 256);
-          const uint32_t acc = slab > 0 ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc));
-        }
+        for (int g = 0; g < TCH; ++g)
+          for (int slab = 0; slab < slabs; ++slab) {
+            const uint64_t da = smem_desc(smem_u32(sA + (g * slabs + slab) * kSlabBytesA), 128, 256);
+            const uint64_t db = smem_desc(smem_u32(sB + (g * slabs + slab) * n_pad * 32), 128, 256);
+            const uint32_t acc = slab > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(g * n_pad)),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&mbar)));
       }
@@ -188,24 +231,36 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       }
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // epilogue: this thread holds accumulator row tid (TMEM lane tid)
-      for (int col = 0; col < n_pad; col += 8) {
-        uint32_t r[8];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (mine) {
+      // epilogue: this thread holds accumulator row tid (TMEM lane tid); eight lights at a time
+      for (int l0 = 0; l0 < k; l0 += 8) {
+        uint32_t r[24];
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int o = col + j;
-            if (o < nout) {
-              const int l = o / 3, c = o % 3;
-              cb[((int64_t)l * nb + (gi - ob)) * 3 + c] =
-                  done ? __uint_as_float(r[j]) * rho[c] : __int_as_float(0x7fc00000);
-            }
+        for (int j = 0; j < 3; ++j) {
+          // scalar T: columns 3 l0 + 8 j .. (lights l0..l0+7, channel-minor); RGB T: group j
+          const uint32_t col = TCH == 1 ? (uint32_t)(3 * l0 + 8 * j) : (uint32_t)(j * n_pad + l0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+              : "=r"(r[8 * j]), "=r"(r[8 * j + 1]), "=r"(r[8 * j + 2]), "=r"(r[8 * j + 3]), "=r"(r[8 * j + 4]),
+                "=r"(r[8 * j + 5]), "=r"(r[8 * j + 6]), "=r"(r[8 * j + 7])
+              : "r"(lane_base + col));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int ll = 0; ll < 8; ++ll) {
+          const int l = l0 + ll;
+          if (l >= k) break;  // uniform
+          float v[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const uint32_t bits = TCH == 1 ? r[3 * ll + c] : r[8 * c + ll];
+            v[c] = done ? __uint_as_float(bits) * rho[c] : __int_as_float(0x7fc00000);
+          }
+          if (mine) {
+            float* out = cb + ((int64_t)l * nb + (gi - ob)) * 3;
+            out[0] = v[0];
+            out[1] = v[1];
+            out[2] = v[2];
           }
         }
       }
@@ -215,46 +270,73 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
-  (void)lane;
 }
 
 }  // namespace
 
-int relight_tc(int64_t n, int32_t order, const float* T, const float* albedo, const float* L, int32_t k,
-               int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors, cudaStream_t stream) {
+template <int C, int TCH>
+static void launch_tc(int grid, size_t smem, cudaStream_t stream, int64_t n, const float* T, const float* albedo,
+                      const float* L, int k, int n_pad, int slabs, int tmem_cols, const int64_t* offsets,
+                      int n_scenes, float* colors) {
+  cudaFuncSetAttribute(k_relight_tc<C, TCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_relight_tc<C, TCH><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
+                                                            n_scenes, colors);
+}
+
+// Tensor-core shape of a relight: N of each MMA and the TMEM columns (a power of two >= 32
+// holding every group and the 24 columns the epilogue reads per eight lights), or 0 when the
+// shape does not fit one MMA (N <= 256) or the 512 TMEM columns.
+int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad_out, int* tmem_cols_out) {
+  if (k <= 0 || (t_channels != 1 && t_channels != 3)) return 0;
+  const int k8 = (k + 7) / 8 * 8;
+  const int n_pad = t_channels == 1 ? (3 * k + 15) / 16 * 16 : (k + 15) / 16 * 16;
+  if (n_pad > kMaxN) return 0;
+  int need = t_channels == 1 ? (n_pad > 3 * k8 ? n_pad : 3 * k8) : 3 * n_pad;
+  int cols = 32;
+  while (cols < need) cols <<= 1;
+  if (cols > 512) return 0;
+  if (n_pad_out) *n_pad_out = n_pad;
+  if (tmem_cols_out) *tmem_cols_out = cols;
+  return 1;
+}
+
+int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,
+               int32_t k, int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors,
+               cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
-  const int nout = 3 * k;
-  const int n_pad = (nout + 15) / 16 * 16;
-  if (n_pad > kMaxN) return PRTGS_ERR_UNSUPPORTED;
-  int tmem_cols = 32;
-  while (tmem_cols < n_pad) tmem_cols <<= 1;
+  int n_pad = 0, tmem_cols = 0;
+  if (!relight_tc_shape(k, t_channels, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
   const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
-  const size_t smem = (size_t)slabs * kSlabBytesA + (size_t)slabs * n_pad * 32 + 1024;
+  const int tch = t_channels;
+  const size_t smem = (size_t)tch * slabs * kSlabBytesA + (size_t)tch * slabs * n_pad * 32 + 1024;
+  if (smem > 227 * 1024) return PRTGS_ERR_UNSUPPORTED;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
   // resident CTAs per SM bounded by the 512 TMEM columns (allocations beyond that would wait
-  // for a CTA to finish) and kept at <= 4 so that one CTA's epilogue overlaps another's MMA
+  // for a CTA to finish), by shared memory, and kept at <= 4 so that one CTA's epilogue
+  // overlaps another's MMA
   int per_sm = 512 / tmem_cols;
+  const int by_smem = (int)((228 * 1024) / (smem + 1024));
+  if (per_sm > by_smem) per_sm = by_smem;
   if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) per_sm = 1;
   const int64_t want = (int64_t)sms * per_sm;
   const int grid = (int)(tiles < want ? tiles : want);
+  const bool rgb = tch == 3;
   switch (order) {
     case 1:
-      cudaFuncSetAttribute(k_relight_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<4><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
-                                                         n_scenes, colors);
+      if (rgb) launch_tc<4, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      else launch_tc<4, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
       break;
     case 2:
-      cudaFuncSetAttribute(k_relight_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<9><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
-                                                         n_scenes, colors);
+      if (rgb) launch_tc<9, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      else launch_tc<9, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
       break;
     default:
-      cudaFuncSetAttribute(k_relight_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_relight_tc<16><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
-                                                          n_scenes, colors);
+      if (rgb) launch_tc<16, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      else launch_tc<16, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
       break;
   }
   PRTGS_CHECK_LAUNCH();

@@ -187,12 +187,15 @@ def test_relit_render_autograd_end_to_end():
         assert _rel(got.grad.cpu(), p.grad) < 2e-3, name
 
 
-@pytest.mark.parametrize("order,k,n", [(3, 1, 5003), (3, 64, 20000), (2, 4, 129), (1, 2, 128), (3, 85, 777)])
-def test_relight_tensor_core_bf16x3(order, k, n):
-    """tcgen05 relight with the 3-term BF16 split meets the FP32 bar (1e-4 norm-wise)."""
-    rng = np.random.default_rng(order * 100 + k)
+@pytest.mark.parametrize("order,k,n,tch", [(3, 1, 5003, 1), (3, 64, 20000, 1), (2, 4, 129, 1), (1, 2, 128, 1),
+                                           (3, 85, 777, 1), (3, 64, 20000, 3), (2, 5, 777, 3), (1, 1, 129, 3),
+                                           (3, 160, 3001, 3), (3, 10, 4099, 1)])
+def test_relight_tensor_core_bf16x3(order, k, n, tch):
+    """tcgen05 relight with the 3-term BF16 split meets the FP32 bar (1e-4 norm-wise), for
+    scalar and RGB transfer, ragged row tails and light counts that are not multiples of 8."""
+    rng = np.random.default_rng(order * 100 + k + tch)
     C = (order + 1) ** 2
-    T = rng.standard_normal((n, C)).astype(np.float32)
+    T = rng.standard_normal((n, C) if tch == 1 else (n, 3, C)).astype(np.float32)
     alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
     L = rng.standard_normal((k, 3, C)).astype(np.float32)
     col = api.relight(_cuda(T), _cuda(alb), _cuda(L), order, precision=1).cpu().numpy()
@@ -214,13 +217,31 @@ def test_relight_tensor_core_plain_bf16_error_is_bf16_sized():
     assert 1e-5 < np.median(err) < 2e-2  # plain BF16 operands: about 2^-8 relative
 
 
+def test_relight_tensor_core_with_glossy_rows():
+    """BF16x3 tensor cores for every row, then the glossy rows rewritten in FP32 (Eq. 41)."""
+    rng = np.random.default_rng(17)
+    n, C, k = 6000, 16, 64
+    T = rng.standard_normal((n, 3, C)).astype(np.float32)
+    alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    L = rng.standard_normal((k, 3, C)).astype(np.float32)
+    gids = np.sort(rng.choice(n, size=1800, replace=False)).astype(np.int32)
+    M = rng.standard_normal((gids.size, C, C)).astype(np.float32) * 0.2
+    means = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    cam = np.array([0.5, -3.0, 1.0], np.float32)
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), 3, precision=1, glossy_ids=_cuda(gids, torch.int32),
+                      M=_cuda(M), means=_cuda(means), cam_pos=_cuda(cam)).cpu().numpy()
+    ref = oracle.relight(T, alb, L, glossy_ids=gids, M=M, means=means, cam_pos=cam, order=3)
+    err = oracle.norm_err(col.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
+    assert err.max() < 1e-4, err.max()
+
+
 def test_relight_tensor_core_rejects_unsupported():
-    T = torch.zeros((10, 3, 16), device="cuda")
-    with pytest.raises(Exception):
-        api.relight(T, torch.zeros((10, 3), device="cuda"), torch.zeros((1, 3, 16), device="cuda"), 3, precision=1)
-    with pytest.raises(Exception):  # 3k > 256 output columns
+    with pytest.raises(Exception):  # 3k > 256 output columns for scalar transfer
         api.relight(torch.zeros((10, 16), device="cuda"), torch.zeros((10, 3), device="cuda"),
                     torch.zeros((90, 3, 16), device="cuda"), 3, precision=1)
+    with pytest.raises(Exception):  # more lights than one launch holds
+        api.relight(torch.zeros((10, 3, 16), device="cuda"), torch.zeros((10, 3), device="cuda"),
+                    torch.zeros((300, 3, 16), device="cuda"), 3, precision=1)
 
 
 def test_relit_render_through_transfer_end_to_end():
