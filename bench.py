@@ -39,9 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched-32", "diff-300k"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched-32", "diff-300k", "tiled-1m-glossy"],
                     help="batched-32: 32 isotropic scenes, one graph-captured step (measurement of batching); "
-                         "diff-300k: differentiable relight + 1080p render of 300k isotropic splats")
+                         "diff-300k: differentiable relight + 1080p render of 300k isotropic splats; "
+                         "tiled-1m-glossy: 1M splats, 30 %% glossy, 64 lights on the tensor cores")
     ap.add_argument("--case", default=None, choices=["kernels-small"],
                     help="run the small profiling case used for the ncu captures instead of the bench")
     return ap.parse_args()
@@ -608,6 +609,96 @@ def run_diff(args):
         print(json.dumps(line), flush=True)
 
 
+def run_tiled(args):
+    """The 1M-splat tiled glossy workload (the surface scene tiled 5 x 2, 30 % glossy, order 3,
+    S = 256): a step is BVH build -> transfer (shadow + bounce + the 16 x 16 glossy matrices) ->
+    relight under 64 lights on the tensor cores (BF16x3, glossy rows in FP32) -> 64 composites at
+    1920x1080. Reports nominal transfer rays/s of the whole step; frames/s counts the 64 relit
+    1080p images of a step."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = S.WORKLOADS["tiled-1m-glossy"]
+    seed = S.config_seed(w["config"])
+    sc = S.make_scene("tiled-1m-glossy")
+    g = api.GaussianTensors.from_scene(sc, dev)
+    dirs = torch.from_numpy(S.direction_set(w["n_dirs"], seed)).to(dev)
+    cam = S.make_camera("tiled-1m-glossy")
+    order, k = w["order"], w["lights"]
+    Lsh = torch.from_numpy(S.env_lights(k, order, seed + 1)).to(dev)
+    gids = torch.from_numpy(np.nonzero(sc.glossy_mask)[0].astype(np.int32)).to(dev)
+    cam_pos = torch.from_numpy((-np.asarray(cam.rot).T @ np.asarray(cam.trans)).astype(np.float32)).to(dev)
+    bg = torch.zeros(3, device=dev)
+    status = api.Status(dev)
+    bvh0 = api.build_bvh(g, status=status)
+    tr0 = api.precompute_transfer(g, bvh0, dirs, order, bounce=True, glossy=True, status=status)
+    col0 = api.relight(tr0["T"], g.albedo, Lsh[:1], order)
+    _, st0 = api.render(g, col0, cam, bg, max_pairs=60_000_000, status=status)
+    torch.cuda.synchronize()
+    n_pairs = st0.n_pairs()
+    state = api.RenderState(g.n, cam.width, cam.height, int(n_pairs * 1.25) + 4096, dev)
+    del tr0, col0, st0, bvh0
+    C = (order + 1) ** 2
+    bufs = {"P": torch.empty((g.n, C), device=dev), "T": torch.empty((g.n, 3, C), device=dev),
+            "idx": torch.empty((g.n, int(dirs.shape[0])), dtype=torch.int32, device=dev)}
+    colors = torch.empty((k, g.n, 3), device=dev)
+    stream = torch.cuda.current_stream()
+    names = ["bvh", "transfer", "relight", "render"]
+
+    def step(ev):
+        ev[0].record(stream)
+        bvh = api.build_bvh(g, status=status)
+        ev[1].record(stream)
+        out = api.precompute_transfer(g, bvh, dirs, order, bounce=True, glossy=True, status=status, out=bufs)
+        ev[2].record(stream)
+        api.relight(out["T"], g.albedo, Lsh, order, precision=1, glossy_ids=gids, M=out["M"], means=g.means,
+                    cam_pos=cam_pos, out=colors)
+        ev[3].record(stream)
+        img, _ = api.render(g, colors, cam, bg, state=state, status=status)
+        ev[4].record(stream)
+        return img
+
+    for _ in range(args.warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(5)])
+    torch.cuda.synchronize()
+    assert status.read() == 0, "device status reported an error"
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    stage_ms = np.zeros(4)
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        step(ev)
+        ev[4].synchronize()
+        for i in range(4):
+            stage_ms[i] += ev[i].elapsed_time(ev[i + 1])
+        total += ev[0].elapsed_time(ev[4])
+    clocks = sampler.stop()
+    assert status.read() == 0
+    total, = reduce_max_over_ranks([total], dev)
+    rays = g.n * int(dirs.shape[0])
+    line = {"metric": METRIC, "value": world * rays * args.steps / (total / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (relight bf16x3 on tensor cores)",
+            "data": "synthetic",
+            "config": {"workload": "tiled-1m-glossy", "n_gaussians": g.n, "n_glossy": int(gids.numel()),
+                       "sh_order": order, "n_dirs": int(dirs.shape[0]), "transfer": "shadow+bounce+glossy",
+                       "lights": k, "image": f"{cam.width}x{cam.height}", "pairs_per_frame": n_pairs,
+                       "l2": "flushed between steps (256 MB write)"},
+            "frames_per_s": world * k * args.steps / (total / 1e3),
+            "stages_ms": {nm: float(v / args.steps) for nm, v in zip(names, stage_ms)},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.case == "kernels-small":
@@ -618,6 +709,8 @@ def main():
         run_batched(args)
     elif args.workload == "diff-300k":
         run_diff(args)
+    elif args.workload == "tiled-1m-glossy":
+        run_tiled(args)
     else:
         run_ours(args)
 

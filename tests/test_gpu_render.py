@@ -339,3 +339,28 @@ def test_diff_300k_central_differences_on_64_parameters():
         if abs(fd - gv) > 2e-2 * abs(fd) + 1e-3 * scale[field]:
             bad.append((field, ix, fd, gv))
     assert not bad, bad[:8]
+
+
+def test_relight_1m_64_lights_tensor_cores_full_size():
+    """The 1M-splat, 64-light relight of the tiled glossy workload on the tensor cores (BF16x3,
+    RGB transfer, 30 % glossy rows rewritten in FP32): sampled rows against the oracle."""
+    rng = np.random.default_rng(64)
+    n, C, k = 1_000_000, 16, 64
+    T = (rng.standard_normal((n, 3, C)) * 0.3).astype(np.float32)
+    T[:, :, 0] += 1.5
+    alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    L = S.env_lights(k, 3, 99)
+    gids = np.nonzero(rng.random(n) < 0.3)[0].astype(np.int32)
+    M = (rng.standard_normal((gids.size, C, C)) * 0.1).astype(np.float32)
+    means = rng.uniform(-20, 20, (n, 3)).astype(np.float32)
+    cam = np.array([0.0, -40.0, 14.0], np.float32)
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), 3, precision=1, glossy_ids=_cuda(gids, torch.int32),
+                      M=_cuda(M), means=_cuda(means), cam_pos=_cuda(cam))
+    rows = np.sort(rng.choice(n, 4096, replace=False))
+    got = col[:, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    gsel = np.isin(gids, rows)
+    ref = oracle.relight(T[rows], alb[rows], L, glossy_ids=np.searchsorted(rows, gids[gsel]), M=M[gsel],
+                         means=means[rows], cam_pos=cam, order=3)
+    err = oracle.norm_err(got.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
+    assert gsel.sum() > 1000
+    assert err.max() < 1e-4, err.max()

@@ -342,3 +342,30 @@ def test_transfer_backward_full_size_sampled_receivers():
     ref = {f: p.grad.numpy() for f, p in zip(_GRAD_FIELDS, ps)}
     _check_grads(gpu, ref)
     assert np.count_nonzero(ref["opacity"]) > 100
+
+
+def test_tiled_1m_glossy_full_size_sampled():
+    """1,000,000 Gaussians (the surface scene tiled 5 x 2 with a random rotation per instance,
+    30 % glossy), order 3, S = 256, shadow + bounce + glossy in one call: sampled diffuse and
+    glossy receivers against the oracle (P, T, the index matrix, the 16 x 16 matrices M)."""
+    sc = S.make_scene("tiled-1m-glossy")
+    dirs = S.direction_set(256, S.config_seed(2))
+    out = _transfer_gpu(sc, dirs, 3, bounce=True, glossy=True)
+    rng = np.random.default_rng(12)
+    gl = np.nonzero(sc.glossy_mask)[0]
+    assert out["n_glossy"] == gl.size
+    recv = np.sort(np.concatenate([rng.choice(np.nonzero(sc.glossy_mask == 0)[0], 5, replace=False),
+                                   rng.choice(gl, 5, replace=False)]))
+    ref = oracle.transfer(sc, dirs, 3, recv, bounce=True)
+    floor = 1e-3 * oracle.unoccluded_norm(3)
+    _check_norm(out["P"][recv], ref["P"], ref["allow_P"], floor)
+    _check_norm(out["T"][recv], ref["T"], ref["allow_T"].max(axis=1), floor)
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    np.testing.assert_array_equal(out["idx"][recv][clean], ref["idx"][clean])
+    g_recv = recv[sc.glossy_mask[recv] != 0]
+    rows = np.searchsorted(gl, g_recv)
+    sel = np.isin(recv, g_recv)
+    Vallow = ref["dV"][sel] + np.where((ref["flags"][sel] & oracle.RF_TRACED) != 0, api.DEFAULT_T_MIN, 0.0)
+    M, allow = oracle.glossy(sc, dirs, 3, g_recv, ref["V"][sel], Vallow)
+    _check_norm(out["M"][rows], M, allow, 1e-3 * np.median(np.linalg.norm(M.reshape(len(M), -1), axis=1)))
+    assert np.all(np.isfinite(out["M"])) and np.all(np.isfinite(out["T"]))
