@@ -398,8 +398,9 @@ def launches_per_step(n, n_pairs, cam, n_dirs=256, bounce=True):
 
 def run_kernels_small():
     """Small case for `ncu --set full`: transfer with bounce on a 20k-splat surface scene (S = 64),
-    relight of 1M splats x 64 lights on the tensor cores and on the CUDA cores, and a 1280x720
-    render forward + backward of the 100k surface scene."""
+    relight of 1M splats x 64 lights on the tensor cores and on the CUDA cores, a 1280x720
+    render forward + backward of the 100k surface scene, and the transfer backward of the 20k
+    scene."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -423,6 +424,8 @@ def run_kernels_small():
     bg = torch.zeros(3, device="cuda")
     img, st = api.render(g2, colors, cam, bg, max_pairs=4_000_000)
     api.render_backward(g2, colors, cam, bg, st, torch.randn(img.shape, device="cuda", generator=gen))
+    dP = torch.randn((g.n, 16), device="cuda", generator=gen)
+    api.precompute_transfer_backward(g, bvh, dirs, 3, dP)
     torch.cuda.synchronize()
     print(json.dumps({"case": "kernels-small", "idx_max": int(out["idx"].max()),
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
