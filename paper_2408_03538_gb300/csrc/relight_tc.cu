@@ -30,7 +30,7 @@ namespace prtgs {
 namespace {
 
 constexpr int kTcRows = 128;       // MMA M (one Gaussian per TMEM lane)
-constexpr int kTcThreads = 128;    // 4 warps: warp w owns TMEM lanes 32w..32w+31
+constexpr int kTcThreads = 256;    // 8 warps: warps w and w + 4 share TMEM lanes 32w..32w+31
 constexpr int kSlabBytesA = kTcRows * 16 * 2;  // one K = 16 slab of A: 4 KB
 constexpr int kMaxN = 256;
 constexpr unsigned kWaitLimit = 1u << 26;
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kTcRows - 1), khalf = tid >> 7;  // tile row; K half and light half
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -139,14 +140,14 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const int64_t row_end = row0 + kTcRows < n ? row0 + kTcRows : n;
     const int b_first = offsets ? find_scene(offsets, n_scenes, row0) : 0;
     const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
-    const int64_t gi = row0 + tid;
-    float tv[TCH][16];
+    const int64_t gi = row0 + row;
+    float tv[TCH][8];  // this thread's half of the row's K = 16
     if (C == 16 && t_vec && gi < n) {
-      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C);
+      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + 8 * khalf);
 #pragma unroll
       for (int g = 0; g < TCH; ++g)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
           const float4 v = __ldg(src + 4 * g + q);
           tv[g][4 * q] = v.x;
           tv[g][4 * q + 1] = v.y;
@@ -157,7 +158,10 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 #pragma unroll
       for (int g = 0; g < TCH; ++g)
 #pragma unroll
-        for (int m = 0; m < 16; ++m) tv[g][m] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
+        for (int j = 0; j < 8; ++j) {
+          const int m = 8 * khalf + j;
+          tv[g][j] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
+        }
     }
     float rho[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
@@ -177,27 +181,26 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t ob = offsets ? offsets[b] : 0;
       const int64_t nb = offsets ? offsets[b + 1] - ob : n;
       float* cb = colors + 3 * (int64_t)k * ob;
-      // A operand: this thread's row(s), split into BF16 terms (zero outside the scene). In the
-      // K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte runs: two 16-byte
-      // stores per slab.
+      // A operand: this thread's half row, split into BF16 terms (zero outside the scene). In
+      // the K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte runs: one
+      // 16-byte store per slab.
 #pragma unroll
       for (int g = 0; g < TCH; ++g) {
-        uint32_t pk[3][8];  // term x (pairs of K)
+        uint32_t pk[3][4];  // term x (pairs of K)
 #pragma unroll
-        for (int m = 0; m < 16; m += 2) {
+        for (int j = 0; j < 8; j += 2) {
           __nv_bfloat16 a1, a2, a3, b1, b2, b3;
-          split3(mine ? tv[g][m] : 0.f, a1, a2, a3);
-          split3(mine ? tv[g][m + 1] : 0.f, b1, b2, b3);
-          pk[0][m / 2] = pack_bf16x2(a1, b1);
-          pk[1][m / 2] = pack_bf16x2(a2, b2);
-          pk[2][m / 2] = pack_bf16x2(a3, b3);
+          split3(mine ? tv[g][j] : 0.f, a1, a2, a3);
+          split3(mine ? tv[g][j + 1] : 0.f, b1, b2, b3);
+          pk[0][j / 2] = pack_bf16x2(a1, b1);
+          pk[1][j / 2] = pack_bf16x2(a2, b2);
+          pk[2][j / 2] = pack_bf16x2(a3, b3);
         }
         for (int slab = 0; slab < slabs; ++slab) {
           const int term = slabs == 1 ? 0 : a_term(slab);
           unsigned char* base = sA + (g * slabs + slab) * kSlabBytesA;
           const uint32_t* q = term == 0 ? pk[0] : (term == 1 ? pk[1] : pk[2]);
-          *reinterpret_cast<uint4*>(base + kmajor_offset(tid, 0)) = make_uint4(q[0], q[1], q[2], q[3]);
-          *reinterpret_cast<uint4*>(base + kmajor_offset(tid, 8)) = make_uint4(q[4], q[5], q[6], q[7]);
+          *reinterpret_cast<uint4*>(base + kmajor_offset(row, 8 * khalf)) = make_uint4(q[0], q[1], q[2], q[3]);
         }
       }
       // make the generic-proxy stores visible to the tensor core's async proxy
@@ -231,10 +234,11 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       }
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // epilogue: this thread holds accumulator row tid (TMEM lane tid); eight lights at a time
-      for (int l0 = 0; l0 < k; l0 += 8) {
+      // epilogue: this thread holds accumulator row `row` (TMEM lane row); eight lights at a
+      // time, the two warps of a lane quarter taking alternate groups of eight
+      for (int l0 = 8 * khalf; l0 < k; l0 += 16) {
         uint32_t r[24];
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           // scalar T: columns 3 l0 + 8 j .. (lights l0..l0+7, channel-minor); RGB T: group j
