@@ -30,7 +30,12 @@ namespace prtgs {
 namespace {
 
 constexpr int kTcRows = 128;       // MMA M (one Gaussian per TMEM lane)
-constexpr int kTcThreads = 256;    // 8 warps: warps w and w + 4 share TMEM lanes 32w..32w+31
+#ifndef PRTGS_TC_KSPLIT
+#define PRTGS_TC_KSPLIT 2
+#endif
+constexpr int kKSplit = PRTGS_TC_KSPLIT;  // threads per tile row (each stages 16 / kKSplit of K)
+constexpr int kKW = 16 / kKSplit;
+constexpr int kTcThreads = 128 * kKSplit;  // warps w, w + 4, ... share TMEM lanes 32(w%4)..+31
 constexpr int kSlabBytesA = kTcRows * 16 * 2;  // one K = 16 slab of A: 4 KB
 constexpr int kMaxN = 256;
 constexpr unsigned kWaitLimit = 1u << 26;
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (kTcRows - 1), khalf = tid >> 7;  // tile row; K half and light half
+  const int row = tid & (kTcRows - 1), khalf = tid >> 7;  // tile row; K part and light share
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -141,13 +146,13 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const int b_first = offsets ? find_scene(offsets, n_scenes, row0) : 0;
     const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
     const int64_t gi = row0 + row;
-    float tv[TCH][8];  // this thread's half of the row's K = 16
+    float tv[TCH][kKW];  // this thread's part of the row's K = 16
     if (C == 16 && t_vec && gi < n) {
-      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + 8 * khalf);
+      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + kKW * khalf);
 #pragma unroll
       for (int g = 0; g < TCH; ++g)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kKW / 4; ++q) {
           const float4 v = __ldg(src + 4 * g + q);
           tv[g][4 * q] = v.x;
           tv[g][4 * q + 1] = v.y;
@@ -158,8 +163,8 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 #pragma unroll
       for (int g = 0; g < TCH; ++g)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int m = 8 * khalf + j;
+        for (int j = 0; j < kKW; ++j) {
+          const int m = kKW * khalf + j;
           tv[g][j] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
         }
     }
@@ -181,14 +186,14 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t ob = offsets ? offsets[b] : 0;
       const int64_t nb = offsets ? offsets[b + 1] - ob : n;
       float* cb = colors + 3 * (int64_t)k * ob;
-      // A operand: this thread's half row, split into BF16 terms (zero outside the scene). In
-      // the K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte runs: one
-      // 16-byte store per slab.
+      // A operand: this thread's part of the row, split into BF16 terms (zero outside the
+      // scene). In the K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte
+      // runs: one 16-byte (or 8-byte) store per slab.
 #pragma unroll
       for (int g = 0; g < TCH; ++g) {
-        uint32_t pk[3][4];  // term x (pairs of K)
+        uint32_t pk[3][kKW / 2];  // term x (pairs of K)
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
+        for (int j = 0; j < kKW; j += 2) {
           __nv_bfloat16 a1, a2, a3, b1, b2, b3;
           split3(mine ? tv[g][j] : 0.f, a1, a2, a3);
           split3(mine ? tv[g][j + 1] : 0.f, b1, b2, b3);
@@ -200,7 +205,10 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
           const int term = slabs == 1 ? 0 : a_term(slab);
           unsigned char* base = sA + (g * slabs + slab) * kSlabBytesA;
           const uint32_t* q = term == 0 ? pk[0] : (term == 1 ? pk[1] : pk[2]);
-          *reinterpret_cast<uint4*>(base + kmajor_offset(row, 8 * khalf)) = make_uint4(q[0], q[1], q[2], q[3]);
+          if constexpr (kKW == 8)
+            *reinterpret_cast<uint4*>(base + kmajor_offset(row, 8 * khalf)) = make_uint4(q[0], q[1], q[2], q[3]);
+          else
+            *reinterpret_cast<uint2*>(base + kmajor_offset(row, kKW * khalf)) = make_uint2(q[0], q[1]);
         }
       }
       // make the generic-proxy stores visible to the tensor core's async proxy
@@ -235,8 +243,8 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
       // epilogue: this thread holds accumulator row `row` (TMEM lane row); eight lights at a
-      // time, the two warps of a lane quarter taking alternate groups of eight
-      for (int l0 = 8 * khalf; l0 < k; l0 += 16) {
+      // time, the warps of a lane quarter taking groups of eight in turn
+      for (int l0 = 8 * khalf; l0 < k; l0 += 8 * kKSplit) {
         uint32_t r[24];
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
