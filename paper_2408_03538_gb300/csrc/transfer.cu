@@ -23,9 +23,14 @@ namespace prtgs {
 constexpr int kTraceWarps = 4;
 // Resident 128-thread blocks per SM the kernels are compiled for (register caps chosen by
 // measurement on the 100k surface workload: the visibility-only walk is fastest at 64
-// registers, the bounce walk and the resolve kernel at 128).
+// registers; the bounce walk at 72 (7 blocks: 335 ms for the transfer against 345, 360 and 374 ms
+// at 6, 5 and 4 blocks, 342 ms at 8); the later index rounds at 128).
 constexpr int kShadowMinBlocks = 8;
-constexpr int kBounceMinBlocks = 4;
+#ifndef PRTGS_BOUNCE_MIN_BLOCKS
+#define PRTGS_BOUNCE_MIN_BLOCKS 7
+#endif
+constexpr int kBounceMinBlocks = PRTGS_BOUNCE_MIN_BLOCKS;
+constexpr int kRoundsMinBlocks = 4;
 #ifndef PRTGS_ROUND_HITS
 #define PRTGS_ROUND_HITS 16
 #endif
@@ -737,7 +742,7 @@ __device__ int index_search_all(const TraceArgs& a, const Ray& r, int root, int 
 
 // Further rounds for the rays k_prefix could not settle (one thread per ray).
 template <int KB>
-__global__ void __launch_bounds__(128, kBounceMinBlocks) k_rounds(TraceArgs a, const RoundRec* __restrict__ more,
+__global__ void __launch_bounds__(128, kRoundsMinBlocks) k_rounds(TraceArgs a, const RoundRec* __restrict__ more,
                                                                   const unsigned int* __restrict__ more_count) {
   const unsigned count = *more_count;
   RayStats rs{0u, 0u, 0u, 0u, 0u};
@@ -902,7 +907,7 @@ struct BwdVis {
   }
 };
 
-__global__ void __launch_bounds__(kTraceThreads, kBounceMinBlocks) k_trace_bwd(TraceArgs a, GradArgs g) {
+__global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(TraceArgs a, GradArgs g) {
   extern __shared__ float smem[];
   float* sdir = smem;                                                               // [S*3]
   unsigned short* slist = reinterpret_cast<unsigned short*>(sdir + 3 * a.S);         // [warps][S]
