@@ -31,6 +31,10 @@ constexpr int kShadowMinBlocks = 8;
 #endif
 constexpr int kBounceMinBlocks = PRTGS_BOUNCE_MIN_BLOCKS;
 constexpr int kRoundsMinBlocks = 4;
+#ifndef PRTGS_PREFIX_MIN_BLOCKS
+#define PRTGS_PREFIX_MIN_BLOCKS 8  // the first index round: 336 ms against 340 / 350 at 6 / 4
+#endif
+constexpr int kPrefixMinBlocks = PRTGS_PREFIX_MIN_BLOCKS;
 #ifndef PRTGS_ROUND_HITS
 #define PRTGS_ROUND_HITS 16
 #endif
@@ -602,7 +606,7 @@ struct RoundRec {
 // candidates found by the visibility walk and the decision. Rays that need more rounds go to
 // a second queue for k_rounds.
 template <int KB>
-__global__ void __launch_bounds__(128, kShadowMinBlocks) k_prefix(TraceArgs a, const uint32_t* __restrict__ list,
+__global__ void __launch_bounds__(128, kPrefixMinBlocks) k_prefix(TraceArgs a, const uint32_t* __restrict__ list,
                                                                   RoundRec* __restrict__ more,
                                                                   unsigned int* __restrict__ more_count) {
   const unsigned count = *a.queue_count;
