@@ -400,7 +400,8 @@ def run_kernels_small():
     """Small case for `ncu --set full`: transfer with bounce on a 20k-splat surface scene (S = 64),
     relight of 1M splats x 64 lights on the tensor cores and on the CUDA cores, a 1280x720
     render forward + backward of the 100k surface scene, and the transfer backward of the 20k
-    scene."""
+    scene; then every other kernel of the library once (shadow-only walk, glossy matrices,
+    relight with RGB transfer and glossy rows, batched relight, loss, relight backward)."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -426,6 +427,29 @@ def run_kernels_small():
     api.render_backward(g2, colors, cam, bg, st, torch.randn(img.shape, device="cuda", generator=gen))
     dP = torch.randn((g.n, 16), device="cuda", generator=gen)
     api.precompute_transfer_backward(g, bvh, dirs, 3, dP)
+    # the remaining kernels once each: shadow-only walk, glossy matrices, relight with RGB transfer
+    # and glossy rows, batched relight, loss, relight backward
+    api.precompute_transfer(g, bvh, dirs, 3)
+    rng = np.random.default_rng(3)
+    sc.glossy_mask = (rng.random(sc.n) < 0.3).astype(np.uint8)
+    gg = api.GaussianTensors.from_scene(sc)
+    outg = api.precompute_transfer(gg, api.build_bvh(gg), dirs, 3, bounce=True, glossy=True)
+    gids = torch.from_numpy(np.nonzero(sc.glossy_mask)[0].astype(np.int32)).cuda()
+    cam_pos = torch.tensor([0.0, -7.0, 3.0], device="cuda")
+    L8 = torch.randn((8, 3, 16), device="cuda", generator=gen)
+    for prec in (0, 1):
+        api.relight(outg["T"], gg.albedo, L8, 3, precision=prec, glossy_ids=gids, M=outg["M"], means=gg.means,
+                    cam_pos=cam_pos)
+    offs = torch.tensor([0, 7000, gg.n], dtype=torch.int64, device="cuda")
+    L2s = torch.randn((2, 8, 3, 16), device="cuda", generator=gen)
+    for prec in (0, 1):
+        api.relight_batched(outg["T"], gg.albedo, offs, L2s, 3, precision=prec)
+    img2, st2 = api.render(g2, colors, cam, bg, max_pairs=4_000_000)
+    loss, dimg = api.l2_loss(img2, torch.rand(img2.shape, device="cuda", generator=gen))
+    dcol = api.render_backward(g2, colors, cam, bg, st2, dimg)[4]
+    Lb = torch.randn((1, 3, 16), device="cuda", generator=gen)
+    Tb = torch.randn((g2.n, 3, 16), device="cuda", generator=gen)
+    api.relight_backward(Tb, g2.albedo, Lb, 3, dcol, need_dT=True)
     torch.cuda.synchronize()
     print(json.dumps({"case": "kernels-small", "idx_max": int(out["idx"].max()),
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
