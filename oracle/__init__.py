@@ -234,10 +234,13 @@ def brdf_kernel(n, wi, wo, roughness, metallic):
 
     Reading: Eq. 15 names D, F, G but not their forms. D = GGX with alpha = r^2,
     F = Schlick with F0 = 0.04 on (w_o . h), G = Smith-Schlick with k = alpha/2 for both
-    directions (Burley 2012; Karis 2013). Zero unless n.w_i > 0 and n.w_o > 0. Arrays
-    broadcast: wi [..., 3], wo [..., 3].
+    directions (Burley 2012; Karis 2013). Zero unless n.w_i > 0 and n.w_o > 0. n is taken as
+    n / |n|. Arrays broadcast: wi [..., 3], wo [..., 3].
     """
     a = roughness * roughness
+    # the BRDF takes the unit normal: an FP32 normal is unit only to rounding, and near a sharp
+    # GGX peak 1 - (n.h)^2 would turn that 1e-7 into a relative change of 1e-4 in D
+    n = n / np.linalg.norm(n, axis=-1, keepdims=True)
     ni = (wi * n).sum(-1)
     no = (wo * n).sum(-1)
     h = wi + wo

@@ -1106,26 +1106,43 @@ constexpr int kGlossyThreads = 128;
 
 // k(w_i, w_o) = (1 - m) + pi f_s, f_s = D F G / (4 (n.w_i)(n.w_o)); GGX D (alpha = r^2),
 // Schlick F (F0 = 0.04, on w_o.h), Smith-Schlick G (k = alpha / 2). ni, no > 0.
+// a b - c d without cancellation (Kahan's difference of products with an FMA: the rounding
+// error of c d is recovered exactly and added back).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+  const float w = c * d;
+  const float e = fmaf(-c, d, w);
+  return fmaf(a, b, -w) + e;
+}
+
+// k(w_i, w_o) of Eq. 15 times pi for the unit normal n / |n|. ni, no: n . w_i, n . w_o (> 0).
+// The GGX denominator (n.h)^2 (a^2 - 1) + 1 is evaluated as (a^2 (n.v)^2 + |n x v|^2) / (|n|^2 |v|^2)
+// with v = w_i + w_o kept unnormalised (exactly, as a TwoSum pair) and n x v formed without
+// cancellation: near a sharp lobe peak 1 - (n.h)^2 is tiny, and neither the rounding of h nor an
+// FP32 normal that is unit only to rounding may leak into it.
 __device__ __forceinline__ float brdf_kernel(float nx, float ny, float nz, const float* wi, const float* wo,
                                              float ni, float no, float alpha, float metal) {
-  float hx = wi[0] + wo[0], hy = wi[1] + wo[1], hz = wi[2] + wo[2];
-  float rh = rsqrtf(fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
-  hx *= rh; hy *= rh; hz *= rh;
-  float nh = fmaf(nx, hx, fmaf(ny, hy, nz * hz));
-  float oh = fminf(fmaxf(fmaf(wo[0], hx, fmaf(wo[1], hy, wo[2] * hz)), 0.f), 1.f);
-  // GGX denominator nh^2 (a^2 - 1) + 1 written as a^2 nh^2 + |n x h|^2: no cancellation
-  // near the lobe peak, where 1 - nh^2 is tiny.
-  float cx = ny * hz - nz * hy, cy = nz * hx - nx * hz, cz = nx * hy - ny * hx;
-  float s2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-  float a2 = alpha * alpha;
-  float den = fmaf(a2 * nh, nh, s2);
-  float D = a2 / (kPi * den * den);
-  float x = 1.0f - oh;
-  float x2 = x * x;
-  float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
-  float kk = 0.5f * alpha;
-  float gi = 1.0f / fmaf(ni, 1.0f - kk, kk);
-  float go = 1.0f / fmaf(no, 1.0f - kk, kk);
+  float vx, vy, vz, ex, ey, ez;
+  two_sum(wi[0], wo[0], vx, ex);
+  two_sum(wi[1], wo[1], vy, ey);
+  two_sum(wi[2], wo[2], vz, ez);
+  const float cx = diff_prod(ny, vz, nz, vy) + (ny * ez - nz * ey);
+  const float cy = diff_prod(nz, vx, nx, vz) + (nz * ex - nx * ez);
+  const float cz = diff_prod(nx, vy, ny, vx) + (nx * ey - ny * ex);
+  const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
+  const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float a2 = alpha * alpha;
+  const float den = fmaf(a2 * nv, nv, cc) / (nn * vv);
+  const float D = a2 / (kPi * den * den);
+  const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
+  const float x = 1.0f - oh;
+  const float x2 = x * x;
+  const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
+  const float rn = rsqrtf(nn);
+  const float kk = 0.5f * alpha;
+  const float gi = 1.0f / fmaf(ni * rn, 1.0f - kk, kk);
+  const float go = 1.0f / fmaf(no * rn, 1.0f - kk, kk);
   return (1.0f - metal) + kPi * 0.25f * D * F * gi * go;
 }
 
