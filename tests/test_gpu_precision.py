@@ -1,0 +1,114 @@
+"""Error of every output of the path against the FP64 oracle, measured on one seeded scene.
+
+A 3,000-splat surface scene (30 % glossy), order 3, S = 128, shadow + bounce + glossy; relight
+under 8 lights in each precision; a 160x120 composite; the L2-loss gradient of the relit image.
+Each output is held to the bar the other tests use, and the measured errors are written as JSON
+to the path in PRTGS_PRECISION_REPORT when that variable is set (the figures quoted beside the
+precision choices).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import render as OR
+from paper_2408_03538_gb300 import api, scenes as S
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def _cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _stats(err):
+    err = np.asarray(err, np.float64).ravel()
+    return {"max": float(err.max()), "median": float(np.median(err)), "p99": float(np.quantile(err, 0.99))}
+
+
+def _within(gpu, ref, allow, floor, tol=TOL):
+    """Norm-wise per row: ||gpu - ref|| <= tol max(||ref||, floor) + allow (the allowance bounds
+    what a rounding-ambiguous hit or argmax decision can change)."""
+    d = np.linalg.norm((gpu - ref).reshape(len(ref), -1), axis=1)
+    r = np.maximum(np.linalg.norm(ref.reshape(len(ref), -1), axis=1), floor)
+    return bool(np.all(d <= tol * r + allow)), d / r
+
+
+def test_error_of_each_output_against_fp64():
+    rep = {}
+    sc = S.surface_scene(3000, 21)
+    sc.means *= 0.6
+    rng = np.random.default_rng(21)
+    sc.glossy_mask = (rng.random(sc.n) < 0.3).astype(np.uint8)
+    sc.roughness = rng.uniform(0.1, 0.6, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    dirs = S.direction_set(128, 21)
+    order = 3
+    g = api.GaussianTensors.from_scene(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    out = api.precompute_transfer(g, bvh, _cuda(dirs), order, bounce=True, glossy=True, status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    P, T, idx, M = (out[k].cpu().numpy() for k in ("P", "T", "idx", "M"))
+    ref = oracle.transfer(sc, dirs, order, np.arange(sc.n), bounce=True)
+    floor = 1e-3 * oracle.unoccluded_norm(order)
+    okP, eP = _within(P, ref["P"], ref["allow_P"], floor)
+    okT, eT = _within(T, ref["T"], ref["allow_T"].max(axis=1), floor)
+    rep["P (transfer vector, norm-wise per splat)"] = _stats(eP)
+    rep["T (with one bounce, norm-wise per splat)"] = _stats(eT)
+    flagged = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) != 0
+    rep["index matrix: unflagged entries differing"] = int((idx[~flagged] != ref["idx"][~flagged]).sum())
+    rep["index matrix: share of rays flagged rounding-ambiguous"] = float(flagged.mean())
+    gids = np.nonzero(sc.glossy_mask)[0]
+    Vallow = ref["dV"][gids] + np.where((ref["flags"][gids] & oracle.RF_TRACED) != 0, api.DEFAULT_T_MIN, 0.0)
+    Mref, Mallow = oracle.glossy(sc, dirs, order, gids, ref["V"][gids], Vallow)
+    okM, eM = _within(M, Mref, Mallow, 1e-3 * np.median(np.linalg.norm(Mref.reshape(len(Mref), -1), axis=1)))
+    rep["M (glossy 16x16, norm-wise per splat)"] = _stats(eM)
+    # relight of the oracle's own T and M in each precision (the contraction's error alone)
+    L = S.env_lights(8, order, 22)
+    cam = S.look_at_camera((0, -4.0, 2.0), (0, 0, 0.4), 45, 160, 120)
+    cam_pos = np.array([0.0, -4.0, 2.0], np.float32)
+    Tr = ref["T"].astype(np.float32)
+    Mr = Mref.astype(np.float32)
+    cref = oracle.relight(Tr, sc.albedo, L, glossy_ids=gids, M=Mr, means=sc.means, cam_pos=cam_pos, order=order)
+    relight_ok = {}
+    for prec, name in ((0, "FP32 CUDA cores"), (1, "BF16x3 tensor cores"), (2, "BF16 tensor cores")):
+        col = api.relight(_cuda(Tr), g.albedo, _cuda(L), order, precision=prec, glossy_ids=_cuda(gids, torch.int32),
+                          M=_cuda(Mr), means=g.means, cam_pos=_cuda(cam_pos)).cpu().numpy()
+        e = oracle.norm_err(col.transpose(1, 0, 2), cref.transpose(1, 0, 2), 1e-3)
+        rep[f"relight colours, {name} (norm-wise per splat)"] = _stats(e)
+        relight_ok[name] = e.max() < (TOL if prec < 2 else 3e-2)
+    # image and gradient of the relit render (FP32 path)
+    colors = api.relight(_cuda(Tr), g.albedo, _cuda(L[:1]), order)
+    img, _ = api.render(g, colors, cam, torch.zeros(3, device="cuda"))
+    t = lambda a: torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+    ps = [t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(sc.albedo), t(L[:1])]
+    imr = OR.render(*ps[:4], OR.relight_torch(torch.as_tensor(Tr, dtype=torch.float64), ps[4], ps[5]), cam)
+    psnr = OR.psnr(img.cpu().numpy(), imr.detach().numpy(), peak=1.0)
+    rep["image (PSNR dB against the FP64 image, peak 1)"] = psnr
+    target = rng.uniform(0, 0.5, tuple(imr.shape)).astype(np.float32)
+    leaves = [g.means.clone().requires_grad_(), g.scales.clone().requires_grad_(), g.quats.clone().requires_grad_(),
+              g.opacity.clone().requires_grad_(), g.albedo.clone().requires_grad_(), _cuda(L[:1]).requires_grad_()]
+    im = api.relit_render(*leaves, _cuda(Tr), g.normals, cam, order)
+    _, dimg = api.l2_loss(im.detach().contiguous(), _cuda(target))
+    im.backward(dimg)
+    ((imr - torch.as_tensor(target, dtype=torch.float64)) ** 2).mean().backward()
+    grad_err = {}
+    for leaf, p, name in zip(leaves, ps, ("means", "scales", "quats", "opacity", "albedo", "light SH")):
+        a, b = leaf.grad.cpu().numpy().astype(np.float64), p.grad.numpy()
+        grad_err[name] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+        rep[f"gradient d loss / d {name} (norm-wise)"] = grad_err[name]
+    path = os.environ.get("PRTGS_PRECISION_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(rep, f, indent=1)
+    assert okP and okT and okM
+    assert rep["index matrix: unflagged entries differing"] == 0
+    assert all(relight_ok.values()), relight_ok
+    assert psnr >= 50.0
+    assert max(grad_err.values()) < 2e-3, grad_err
