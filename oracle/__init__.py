@@ -184,7 +184,7 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
                     alt = (rho[cj][:, None] / math.pi) * Pj[int(cj)][0][None, :]
                     worst = np.maximum(worst, np.linalg.norm(alt - best, axis=1))
                 allow_T[r] += w * c[r, s] * worst
-    res.update(T=T, allow_T=allow_T)
+    res.update(T=T, allow_T=allow_T, cand=tr["cand"])
     return res
 
 
@@ -276,6 +276,50 @@ def glossy(scene, dirs, order: int, recv, V, allow_V=None):
         if allow_V is not None:
             allow[r] = np.sum(w * c * allow_V[r] * np.linalg.norm(Y, axis=1) * np.linalg.norm(B, axis=1))
     return M, allow
+
+
+def multi_bounce(scene, dirs, order: int, tr, n_bounces: int, tol: float = 1e-4):
+    """n-bounce self-transfer (Eq. 34-35) over an index matrix.
+
+    ``tr`` is ``transfer(scene, dirs, order, np.arange(N), bounce=True)`` (every Gaussian a
+    receiver, so every index target is present) or any dict with the same P, allow_P, idx,
+    flags, cand. With T^0 = P (the diffuse transfer, the same for the three channels):
+        T^k_i = sum_s w (n_i.w_s)^+ (rho_j / pi) T^{k-1}_j,   j = idx[i, s] >= 0, per channel,
+    and the total is T = P + sum_{k=1..n} T^k [N,3,C] (Eq. 35). One bounce gives Eq. 33.
+    The allowance [N,3] carries each bounce's: the previous bounce's allowance and relative
+    tolerance through the weights, plus, for a ray whose argmax is flagged, the largest change
+    switching to another candidate (or to no hit) would make.
+    """
+    P = np.asarray(tr["P"], dtype=np.float64)
+    idx = np.asarray(tr["idx"])
+    N, S = idx.shape
+    w = 4.0 * math.pi / S
+    c = _cos_weights(scene, dirs, np.arange(N))
+    rho = np.asarray(scene.albedo, dtype=np.float64) / math.pi  # [N,3]
+    valid = idx >= 0
+    jj = np.where(valid, idx, 0)
+    coef = w * c * valid  # [N,S]
+    amb = np.nonzero((np.asarray(tr["flags"]) & RF_AMBIG_ARGMAX) != 0)
+    cand = np.asarray(tr["cand"]) if "cand" in tr else None
+    prev = np.repeat(P[:, None, :], 3, axis=1)
+    aprev = np.repeat(np.asarray(tr["allow_P"], dtype=np.float64)[:, None], 3, axis=1)
+    total, atot = prev.copy(), aprev.copy()
+    for _ in range(n_bounces):
+        G = rho[jj][:, :, :, None] * prev[jj]  # [N,S,3,C]: (rho_j/pi) T^{k-1}_j
+        cur = (coef[:, :, None, None] * G).sum(axis=1)
+        nrm = np.linalg.norm(prev, axis=2)  # [N,3]
+        acur = (coef[:, :, None] * rho[jj] * (aprev[jj] + tol * nrm[jj])).sum(axis=1)
+        for i, sidx in zip(*amb):
+            best = G[i, sidx] if valid[i, sidx] else np.zeros_like(G[i, sidx])
+            worst = np.linalg.norm(best, axis=1)
+            for cj in (cand[i, sidx] if cand is not None else ()):
+                if cj >= 0:
+                    worst = np.maximum(worst, np.linalg.norm(rho[cj][:, None] * prev[cj] - best, axis=1))
+            acur[i] += w * c[i, sidx] * worst
+        total += cur
+        atot += acur
+        prev, aprev = cur, acur
+    return total, atot
 
 
 # ------------------------------------------------------------------------------------------

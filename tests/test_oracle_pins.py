@@ -536,3 +536,73 @@ def test_torch_transfer_autograd_matches_central_differences(oracle_mod):
             checked += 1
     assert checked == 30
     assert float(grads[3].abs().sum()) > 0  # opacity matters
+
+
+# ---- n-bounce self-transfer (Eq. 34-35) -----------------------------------------------------
+def test_multi_bounce_one_bounce_is_eq33(oracle_mod):
+    """One bounce of the recursion is the one-bounce transfer T (and its allowance)."""
+    sc = _crowd(120, 8)
+    dirs = S.direction_set(48, 4)
+    tr = oracle_mod.transfer(sc, dirs, 2, np.arange(sc.n), bounce=True)
+    T1, a1 = oracle_mod.multi_bounce(sc, dirs, 2, tr, 1)
+    np.testing.assert_allclose(T1, tr["T"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a1, tr["allow_T"], rtol=1e-12, atol=1e-15)
+    assert (tr["idx"] >= 0).sum() > 100
+
+
+class _TwoSplats:
+    def __init__(self, normals, albedo):
+        self.normals = np.asarray(normals, np.float64)
+        self.albedo = np.asarray(albedo, np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6])
+def test_multi_bounce_two_facing_splats_closed_form(oracle_mod, n):
+    """Two splats whose one ray each hits the other: the bounces alternate, so with
+    a = w c_A rho_B / pi and b = w c_B rho_A / pi (per channel)
+    T_A = P_A sum_{m <= n/2} (ab)^m + a P_B sum_{m <= (n-1)/2} (ab)^m."""
+    dirs = np.array([[0, 0, 1.0], [0, 0, -1.0], [1.0, 0, 0], [0, 1.0, 0]])
+    nA, nB = np.array([0.0, 0.6, 0.8]), np.array([0.0, 0.28, -0.96])
+    sc = _TwoSplats([nA, nB], [[0.9, 0.5, 0.2], [0.3, 0.7, 0.6]])
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal((2, 9))
+    idx = -np.ones((2, 4), np.int64)
+    idx[0, 0] = 1  # A's ray along +z hits B
+    idx[1, 1] = 0  # B's ray along -z hits A
+    tr = dict(P=P, allow_P=np.zeros(2), idx=idx, flags=np.zeros((2, 4), np.int32))
+    T, _ = oracle_mod.multi_bounce(sc, dirs, 2, tr, n)
+    w = 4 * math.pi / 4
+    a = w * max(nA @ dirs[0], 0) * sc.albedo[1] / math.pi
+    b = w * max(nB @ dirs[1], 0) * sc.albedo[0] / math.pi
+    geo_even = sum((a * b) ** m for m in range(n // 2 + 1))
+    geo_odd = sum((a * b) ** m for m in range((n - 1) // 2 + 1))
+    TA = geo_even[:, None] * P[0][None, :] + (a * geo_odd)[:, None] * P[1][None, :]
+    TB = geo_even[:, None] * P[1][None, :] + (b * geo_odd)[:, None] * P[0][None, :]
+    np.testing.assert_allclose(T[0], TA, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(T[1], TB, rtol=1e-13, atol=1e-14)
+
+
+def test_multi_bounce_converges_to_the_resolvent(oracle_mod):
+    """With every bounce kept, T = sum_k W^k P = (I - W)^{-1} P per channel, W[i,j] the summed
+    weights w (n_i.w_s)^+ rho_j / pi of receiver i's rays whose index is j."""
+    rng = np.random.default_rng(5)
+    N, Sd, C = 40, 24, 4
+    dirs = S.direction_set(Sd, 6)
+    normals = rng.standard_normal((N, 3))
+    normals /= np.linalg.norm(normals, axis=1, keepdims=True)
+    sc = _TwoSplats(normals, rng.uniform(0.1, 0.6, (N, 3)))
+    idx = rng.integers(-N // 2, N, (N, Sd))
+    idx[idx < 0] = -1
+    P = rng.standard_normal((N, C))
+    tr = dict(P=P, allow_P=np.zeros(N), idx=idx, flags=np.zeros((N, Sd), np.int32))
+    T, _ = oracle_mod.multi_bounce(sc, dirs, 1, tr, 80)
+    w = 4 * math.pi / Sd
+    cosw = np.maximum(normals @ dirs.T, 0)
+    for ch in range(3):
+        W = np.zeros((N, N))
+        for i in range(N):
+            for s_ in range(Sd):
+                if idx[i, s_] >= 0:
+                    W[i, idx[i, s_]] += w * cosw[i, s_] * sc.albedo[idx[i, s_], ch] / math.pi
+        assert np.max(np.abs(np.linalg.eigvals(W))) < 0.7
+        np.testing.assert_allclose(T[:, ch, :], np.linalg.solve(np.eye(N) - W, P), rtol=1e-10, atol=1e-10)
