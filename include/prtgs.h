@@ -141,6 +141,10 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *                   transmittance in front of it is <= t; 1 disables the filter.
  *   flags           PRTGS_SHADOW | PRTGS_BOUNCE | PRTGS_GLOSSY
  *   index_buffer    tuning: candidates per index-matrix search round (1, 2, 4 or 8; 0 = default)
+ *   n_bounces       self-transfer bounces with PRTGS_BOUNCE (Eq. 34-35): T = P + T^1 + ... + T^n,
+ *                   T^k_i = sum_s w (n_i.w_s)^+ (rho_j/pi) T^{k-1}_j over the index matrix, T^0 = P;
+ *                   0 or 1 = one bounce (Eq. 33), at most 64; more than one needs 3nC floats of
+ *                   workspace per extra buffer (two at most)
  *   stats           optional device uint64[8] that the call ADDS its work counters to:
  *                   BVH node visits of the visibility walks, node visits of the index-matrix
  *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays, rays
@@ -156,6 +160,7 @@ typedef struct prtgs_transfer_params {
   uint32_t flags;
   int32_t index_buffer;
   unsigned long long* stats;
+  int32_t n_bounces;
 } prtgs_transfer_params;
 
 size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);

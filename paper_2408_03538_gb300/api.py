@@ -133,9 +133,10 @@ def build_bvh(g: GaussianTensors, scene_offsets: torch.Tensor | None = None, sta
 def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int, shadow: bool = True,
                         bounce: bool = False, glossy: bool = False, t_min: float = DEFAULT_T_MIN,
                         same_surface_t: float = 1.0, status: Status | None = None, out: dict | None = None,
-                        stats: torch.Tensor | None = None, index_buffer: int = 0):
-    """Transfer vectors P [n,C], and with ``bounce`` T [n,3,C] and idx [n,S]; with ``glossy``
-    the C x C matrices M [n_glossy,C,C] of the glossy splats (in increasing index order)."""
+                        stats: torch.Tensor | None = None, index_buffer: int = 0, n_bounces: int = 1):
+    """Transfer vectors P [n,C], and with ``bounce`` T [n,3,C] (``n_bounces`` self-transfer
+    bounces over the index matrix) and idx [n,S]; with ``glossy`` the C x C matrices
+    M [n_glossy,C,C] of the glossy splats (in increasing index order)."""
     lib = L.load()
     dev = g.means.device
     S = int(dirs.shape[0])
@@ -150,7 +151,8 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
         idx = out.get("idx") if out.get("idx") is not None else torch.empty((g.n, S), dtype=torch.int32, device=dev)
     if glossy:
         M = torch.empty((max(n_glossy, 1), C, C), dtype=torch.float32, device=dev)
-    p = L.TransferParams(order, S, _ptr(dirs), float(t_min), float(same_surface_t), flags, int(index_buffer), _ptr(stats))
+    p = L.TransferParams(order, S, _ptr(dirs), float(t_min), float(same_surface_t), flags, int(index_buffer),
+                         _ptr(stats), int(n_bounces))
     ws, nb = _ws(lib.prtgs_transfer_workspace_size(g.n, n_glossy, ctypes.byref(p)), dev)
     gs = g.struct()
     L.check(lib.prtgs_precompute_transfer(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(P), _ptr(T),

@@ -1056,10 +1056,16 @@ int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh
 
 size_t transfer_backward_workspace(int64_t, const prtgs_transfer_params*) { return align_up(sizeof(unsigned int)); }
 
-// ---- one-bounce self-transfer (Eq. 33) -------------------------------------------------------
+// ---- self-transfer bounces (Eq. 33; n bounces Eq. 34-35) ----------------------------------------
+// One bounce k: T^k_i = sum_s w (n_i.w_s)^+ (rho_j / pi) T^{k-1}_j over the index matrix, per
+// channel, with T^0 = P (FROM_P: the same for the three channels). FROM_P writes
+// T = P + T^1; later bounces add T^k to T. Tcur (nullable) receives T^k for the next bounce.
+// One warp per receiver: lanes 0-15 and 16-31 take alternate rays, lane & 15 the coefficient.
+template <bool FROM_P>
 __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs, const float* __restrict__ normals,
                          const float* __restrict__ albedo, const float* __restrict__ P,
-                         const int32_t* __restrict__ idx, float* __restrict__ T, int32_t* status) {
+                         const float* __restrict__ Tprev, const int32_t* __restrict__ idx, float* __restrict__ T,
+                         float* __restrict__ Tcur, int32_t* status) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -1082,22 +1088,41 @@ __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs
       int j = __shfl_sync(0xffffffffu, jl, src);
       float c = __shfl_sync(0xffffffffu, cl, src);
       if (j < 0) continue;
-      float coef = wq * c * (1.0f / kPi);
-      float pj = k < C ? __ldg(P + (int64_t)j * C + k) : 0.f;
-      float cp = coef * pj;
-      acc0 = fmaf(cp, __ldg(albedo + 3 * j), acc0);
-      acc1 = fmaf(cp, __ldg(albedo + 3 * j + 1), acc1);
-      acc2 = fmaf(cp, __ldg(albedo + 3 * j + 2), acc2);
+      const float coef = wq * c * (1.0f / kPi);
+      if (FROM_P) {
+        const float cp = coef * (k < C ? __ldg(P + (int64_t)j * C + k) : 0.f);
+        acc0 = fmaf(cp, __ldg(albedo + 3 * j), acc0);
+        acc1 = fmaf(cp, __ldg(albedo + 3 * j + 1), acc1);
+        acc2 = fmaf(cp, __ldg(albedo + 3 * j + 2), acc2);
+      } else if (k < C) {
+        const float* tj = Tprev + (int64_t)j * 3 * C + k;
+        acc0 = fmaf(coef * __ldg(albedo + 3 * j), __ldg(tj), acc0);
+        acc1 = fmaf(coef * __ldg(albedo + 3 * j + 1), __ldg(tj + C), acc1);
+        acc2 = fmaf(coef * __ldg(albedo + 3 * j + 2), __ldg(tj + 2 * C), acc2);
+      }
     }
   }
   acc0 += __shfl_xor_sync(0xffffffffu, acc0, 16);
   acc1 += __shfl_xor_sync(0xffffffffu, acc1, 16);
   acc2 += __shfl_xor_sync(0xffffffffu, acc2, 16);
   if (half == 0 && k < C) {
-    float p = P[i * C + k];
-    T[(i * 3 + 0) * C + k] = p + acc0;
-    T[(i * 3 + 1) * C + k] = p + acc1;
-    T[(i * 3 + 2) * C + k] = p + acc2;
+    float* t = T + i * 3 * C + k;
+    if (FROM_P) {
+      const float p = P[i * C + k];
+      t[0] = p + acc0;
+      t[C] = p + acc1;
+      t[2 * C] = p + acc2;
+    } else {
+      t[0] += acc0;
+      t[C] += acc1;
+      t[2 * C] += acc2;
+    }
+    if (Tcur) {
+      float* u = Tcur + i * 3 * C + k;
+      u[0] = acc0;
+      u[C] = acc1;
+      u[2 * C] = acc2;
+    }
   }
 }
 
@@ -1241,6 +1266,8 @@ static int64_t trace_batch(int64_t n, int S) {
 
 static size_t queue_rec_bytes(int kb) { return 16 + 16 * (size_t)kb; }
 
+static int n_bounces_of(const prtgs_transfer_params* p) { return p->n_bounces > 1 ? p->n_bounces : 1; }
+
 static int index_buffer_of(const prtgs_transfer_params* p) {
   const int kb = p->index_buffer > 0 ? p->index_buffer : kDefaultIndexBuffer;
   return kb <= 1 ? 1 : (kb <= 2 ? 2 : (kb <= 4 ? 4 : 8));
@@ -1252,6 +1279,9 @@ size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_para
     const size_t rays = (size_t)trace_batch(n, p->n_dirs) * p->n_dirs;
     b += align_up(queue_rec_bytes(index_buffer_of(p)) * rays) + 3 * align_up(sizeof(uint32_t) * rays) +
          scan_workspace((int64_t)rays) + align_up(sizeof(RoundRec) * rays) + align_up(sizeof(unsigned int));
+    const size_t tbytes = align_up(sizeof(float) * (size_t)n * 3 * sh_count(p->sh_order));
+    if (n_bounces_of(p) > 1) b += tbytes;
+    if (n_bounces_of(p) > 2) b += tbytes;
   }
   if (p->flags & PRTGS_GLOSSY) {
     b += 2 * align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + scan_workspace(n) +
@@ -1318,6 +1348,9 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   void* rscan_ws = bounce ? c.take<char>(scan_workspace((int64_t)batch_rays)) : nullptr;
   RoundRec* more = bounce ? c.take<RoundRec>(batch_rays) : nullptr;
   unsigned int* more_count = bounce ? c.take<unsigned int>(1) : nullptr;
+  float* tb[2] = {nullptr, nullptr};  // ping-pong bounce buffers [n,3,C] for n_bounces > 1
+  if (bounce && n_bounces_of(p) > 1) tb[0] = c.take<float>((size_t)n * 3 * C);
+  if (bounce && n_bounces_of(p) > 2) tb[1] = c.take<float>((size_t)n * 3 * C);
   int32_t* slot = nullptr;
   int32_t* gids = nullptr;
   float* Vg = nullptr;
@@ -1377,8 +1410,17 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   if (rct != PRTGS_OK) return rct;
   PRTGS_CHECK_LAUNCH();
   if (bounce) {
-    k_bounce<<<(unsigned)((n + 7) / 8), 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, idx, T,
-                                                         status);
+    const int nb = n_bounces_of(p);
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    float* cur = nb > 1 ? tb[0] : nullptr;
+    k_bounce<true><<<blocks, 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, nullptr, idx, T, cur,
+                                               status);
+    for (int b = 2; b <= nb; ++b) {  // Eq. 34-35: each bounce gathers the previous one
+      float* prev = cur;
+      cur = b < nb ? tb[(b - 1) & 1] : nullptr;
+      k_bounce<false><<<blocks, 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, prev, idx, T, cur,
+                                                  status);
+    }
     PRTGS_CHECK_LAUNCH();
   }
   if (glossy) {

@@ -38,7 +38,7 @@ def test_struct_sizes_match_c_layout():
     # sizes implied by include/prtgs.h on LP64
     assert ctypes.sizeof(L.Gaussians) == 8 + 9 * 8
     assert ctypes.sizeof(L.BVH) == 8 + 4 + 4 + 7 * 8
-    assert ctypes.sizeof(L.TransferParams) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8
+    assert ctypes.sizeof(L.TransferParams) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4  # n_bounces + tail padding
     assert ctypes.sizeof(L.Camera) == 4 * (9 + 3 + 4) + 4 * 2 + 4 + 4 * 3
     assert ctypes.sizeof(L.RenderState) == 8 + 8 + 4 * 4 + 11 * 8
 

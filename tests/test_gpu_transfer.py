@@ -369,3 +369,50 @@ def test_tiled_1m_glossy_full_size_sampled():
     M, allow = oracle.glossy(sc, dirs, 3, g_recv, ref["V"][sel], Vallow)
     _check_norm(out["M"][rows], M, allow, 1e-3 * np.median(np.linalg.norm(M.reshape(len(M), -1), axis=1)))
     assert np.all(np.isfinite(out["M"])) and np.all(np.isfinite(out["T"]))
+
+
+# ---- n-bounce self-transfer (Eq. 34-35) -----------------------------------------------------
+@pytest.mark.parametrize("nb", [2, 3, 5])
+def test_multi_bounce_matches_oracle(nb):
+    """T = P + T^1 + ... + T^n over the index matrix, every receiver of a crowded 400-splat
+    scene, against the oracle's recursion (norm-wise 1e-4 + the carried allowance)."""
+    sc = _crowded(400, 17)
+    dirs = S.direction_set(64, 9)
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    T = api.precompute_transfer(g, bvh, torch.from_numpy(dirs).cuda(), 2, bounce=True, n_bounces=nb,
+                                status=st)["T"].cpu().numpy()
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    tr = oracle.transfer(sc, dirs, 2, np.arange(sc.n), bounce=True)
+    Tref, allow = oracle.multi_bounce(sc, dirs, 2, tr, nb)
+    _check_norm(T, Tref, allow.max(axis=1), 1e-3 * oracle.unoccluded_norm(2))
+    # the later bounces matter here: the n-bounce T differs from the one-bounce T
+    assert np.linalg.norm(Tref - tr["T"]) > 1e-3 * np.linalg.norm(tr["T"])
+
+
+def test_multi_bounce_full_size_is_polynomial_in_albedo():
+    """At the 100k surface workload size: the index matrix does not depend on albedo, so with
+    all albedos scaled by s the bounce part of a two-bounce T is exactly a s + b s^2; three
+    scales fix it, a fourth is predicted. One bounce requested explicitly equals the default."""
+    sc = S.make_scene("surface-100k")
+    dirs = torch.from_numpy(S.direction_set(256, S.config_seed(1))).cuda()
+    g = _gt(sc)
+    bvh = api.build_bvh(g)
+    t1 = api.precompute_transfer(g, bvh, dirs, 3, bounce=True)
+    t1b = api.precompute_transfer(g, bvh, dirs, 3, bounce=True, n_bounces=1)
+    assert torch.equal(t1["T"], t1b["T"]) and torch.equal(t1["idx"], t1b["idx"])
+    P = t1["P"].double()[:, None, :]
+    D = {}
+    for s_ in (1.0, 0.5, 0.25):
+        gs = api.GaussianTensors(g.means, g.scales, g.quats, g.opacity, g.normals, (g.albedo * s_).contiguous())
+        out = api.precompute_transfer(gs, bvh, dirs, 3, bounce=True, n_bounces=2)
+        assert torch.equal(out["idx"], t1["idx"])
+        D[s_] = out["T"].double() - P
+    b = 2.0 * (D[1.0] - 2.0 * D[0.5])
+    a = D[1.0] - b
+    pred = a / 4 + b / 16
+    err = (D[0.25] - pred).norm() / D[0.25].norm()
+    assert float(err) < 1e-5, float(err)
+    assert float(b.norm()) > 1e-3 * float(a.norm())  # the second bounce is there
