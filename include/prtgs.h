@@ -326,6 +326,26 @@ int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const
                  size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Relight of many lights in pixel space (the composite of Eq. 4 is linear in the splat colours
+ * of Eq. 14): the splats' features (rho_i/pi) T_i (glossy splats: (rho_i/pi) M_i Y(v_i), Eq. 41,
+ * v_i towards cam->pos) are composited once as C "lights" into a transfer image TI[C,3,H,W]
+ * (this fills *st like prtgs_render), then every light's image is
+ *   image[l,c,p] = sum_m TI[m,c,p] L[l,c,m] + bg[c] final_T[p]
+ * one [H*W x C] x [C x k] contraction per channel: on tcgen05 (PRTGS_PREC_BF16X3 / _BF16, k <= 160)
+ * or FP32 CUDA cores (k <= 256). Same result as prtgs_relight + prtgs_render up to rounding, at
+ * the cost of one 3C-channel composite instead of k 3-channel ones.
+ *   T[n,t_channels,C], albedo from g; glossy as prtgs_relight; L[k,3,C]; bg[3] (device);
+ *   image[k,3,H,W] out. Workspace: prtgs_render_relit_workspace_size.
+ */
+size_t prtgs_render_relit_workspace_size(int64_t n, int32_t sh_order, int32_t width, int32_t height,
+                                         int64_t max_pairs);
+int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* T, int32_t t_channels,
+                       int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* L, int32_t k,
+                       int32_t precision, const prtgs_camera* cam, const float* bg, float* image,
+                       prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                       prtgs_stream_t stream);
+
+/*
  * Render backward: dimage[k,3,H,W] in; gradients out (overwritten): d_means[n,3],
  * d_scales[n,3], d_quats[n,4], d_opacity[n], d_colors[k,n,3]. Uses the state written by the
  * matching prtgs_render call. Gradients of the discrete decisions (culling, tile binning,

@@ -303,6 +303,31 @@ def render(g: GaussianTensors, colors: torch.Tensor, cam, bg: torch.Tensor, stat
     return image, state
 
 
+def render_relit(g: GaussianTensors, T: torch.Tensor, Lsh: torch.Tensor, cam, order: int, bg: torch.Tensor = None,
+                 precision: int = L.PREC_BF16X3, glossy_ids=None, M=None, state: RenderState | None = None,
+                 max_pairs: int | None = None, status: Status | None = None, out=None):
+    """image [k,3,H,W] of every light at once in pixel space: one composite of the splats'
+    (rho/pi) T (glossy: (rho/pi) M Y(v)) features, then a per-pixel contraction with the lights."""
+    lib = L.load()
+    dev = g.means.device
+    n, k = g.n, int(Lsh.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    if bg is None:
+        bg = torch.zeros(3, dtype=torch.float32, device=dev)
+    if state is None:
+        state = RenderState(n, cam.width, cam.height, max_pairs or max(16 * n, 1 << 16), dev)
+    image = out if out is not None else torch.empty((k, 3, cam.height, cam.width), dtype=torch.float32, device=dev)
+    ng = int(glossy_ids.numel()) if glossy_ids is not None else 0
+    ws, nb = _ws(lib.prtgs_render_relit_workspace_size(n, order, cam.width, cam.height, state.max_pairs), dev)
+    gs = g.struct()
+    cs = camera_struct(cam)
+    L.check(lib.prtgs_render_relit(ctypes.byref(gs), order, _ptr(T), tch, ng, _ptr(glossy_ids), _ptr(M), _ptr(Lsh),
+                                   k, precision, ctypes.byref(cs), _ptr(bg), _ptr(image), ctypes.byref(state.s),
+                                   status.ptr() if status else None, _ptr(ws), nb, _stream()), "prtgs_render_relit")
+    state._ws = ws
+    return image, state
+
+
 def render_backward(g: GaussianTensors, colors, cam, bg, state: RenderState, dimage):
     lib = L.load()
     k = int(colors.shape[0])

@@ -247,6 +247,35 @@ static int check_camera(const prtgs_camera* cam) {
   return PRTGS_OK;
 }
 
+size_t prtgs_render_relit_workspace_size(int64_t n, int32_t sh_order, int32_t width, int32_t height,
+                                         int64_t max_pairs) {
+  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0 || check_order(sh_order)) return 0;
+  return render_relit_workspace(n, sh_order, width, height, max_pairs);
+}
+
+int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* T, int32_t t_channels,
+                       int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* L, int32_t k,
+                       int32_t precision, const prtgs_camera* cam, const float* bg, float* image,
+                       prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                       prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if ((rc = check_camera(cam))) return rc;
+  if ((rc = check_order(sh_order))) return rc;
+  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
+  if (n_glossy < 0 || n_glossy > g->n) return PRTGS_ERR_SHAPE;
+  if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
+  if (k < 1 || k > 256 || !L || !bg || !image || (g->n > 0 && (!T || !g->albedo))) return PRTGS_ERR_INVALID_ARG;
+  if (n_glossy > 0 && (!glossy_ids || !M || !g->means)) return PRTGS_ERR_INVALID_ARG;
+  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_shape(k, 3, nullptr, nullptr)) return PRTGS_ERR_UNSUPPORTED;
+  rc = check_ws(workspace, workspace_bytes,
+                render_relit_workspace(g->n, sh_order, cam->width, cam->height, st->max_pairs));
+  if (rc) return rc;
+  return finish(render_relit(g, sh_order, T, t_channels, n_glossy, glossy_ids, M, L, k, precision, cam, bg, image,
+                             st, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
                  const float* bg, float* image, prtgs_render_state* st, int32_t* status, void* workspace,
                  size_t workspace_bytes, prtgs_stream_t stream) {

@@ -144,6 +144,131 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
   return PRTGS_OK;
 }
 
+// ---- pixel-space relight of many lights (composite once, contract per pixel) ------------------
+// The composite is linear in the splat colours: with colours (rho_i/pi) (T_i . L_l) every
+// light's image is sum_m TI[m,c,p] L[l,c,m] + bg[c] final_T[p], TI the composite of the
+// features F[m,i,c] = (rho_i[c]/pi) T_i[c][m] (glossy splats: t_eff = M_i Y(v_i), Eq. 41).
+template <int TCH>
+__global__ void k_transfer_features(int64_t n, int C, const float* __restrict__ T, const float* __restrict__ albedo,
+                                    float* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+  for (int m = 0; m < C; ++m)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[((int64_t)m * n + i) * 3 + c] = r[c] * __ldg(T + (i * TCH + (TCH > 1 ? c : 0)) * C + m);
+}
+
+template <int ORDER>
+__global__ void k_glossy_features(int64_t n, int64_t n_glossy, const int32_t* __restrict__ ids,
+                                  const float* __restrict__ M, const float* __restrict__ means, float cx, float cy,
+                                  float cz, const float* __restrict__ albedo, float* __restrict__ F) {
+  constexpr int C = (ORDER + 1) * (ORDER + 1);
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_glossy) return;
+  const int64_t i = ids[g];
+  const float vx = cx - means[3 * i], vy = cy - means[3 * i + 1], vz = cz - means[3 * i + 2];
+  const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+  float Y[kMaxC];
+  sh_eval<ORDER>(vx * rn, vy * rn, vz * rn, Y);
+  float r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+#pragma unroll
+  for (int a = 0; a < C; ++a) {
+    float te = 0.f;
+#pragma unroll
+    for (int b = 0; b < C; ++b) te = fmaf(__ldg(M + (g * C + a) * C + b), Y[b], te);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[((int64_t)a * n + i) * 3 + c] = r[c] * te;
+  }
+}
+
+// FP32 form: one thread per pixel, the lights in shared memory.
+template <int C>
+__global__ void __launch_bounds__(kRelightThreads) k_pixel_relight(int64_t n_pix, const float* __restrict__ TI,
+                                                                   const float* __restrict__ final_T,
+                                                                   const float* __restrict__ bg,
+                                                                   const float* __restrict__ L, int k,
+                                                                   float* __restrict__ image) {
+  extern __shared__ float sL[];  // [k][3][C]
+  for (int e = threadIdx.x; e < k * 3 * C; e += blockDim.x) sL[e] = L[e];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  float t[3][C];
+#pragma unroll
+  for (int m = 0; m < C; ++m)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c][m] = __ldg(TI + ((int64_t)m * 3 + c) * n_pix + p);
+  const float ft = __ldg(final_T + p);
+  float b[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) b[c] = bg[c] * ft;
+  for (int l = 0; l < k; ++l) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* Ll = sL + (l * 3 + c) * C;
+      float d = b[c];
+#pragma unroll
+      for (int m = 0; m < C; ++m) d = fmaf(t[c][m], Ll[m], d);
+      image[((int64_t)l * 3 + c) * n_pix + p] = d;
+    }
+  }
+}
+
+size_t render_relit_workspace(int64_t n, int32_t order, int32_t width, int32_t height, int64_t max_pairs) {
+  const int C = sh_count(order);
+  const int64_t n_pix = (int64_t)width * height;
+  return align_up(sizeof(float) * (size_t)C * n * 3) + align_up(sizeof(float) * (size_t)C * 3 * n_pix) +
+         align_up(sizeof(float) * 4) + render_workspace(n, width, height, max_pairs);
+}
+
+int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_t t_channels, int64_t n_glossy,
+                 const int32_t* glossy_ids, const float* M, const float* L, int32_t k, int32_t precision,
+                 const prtgs_camera* cam, const float* bg, float* image, prtgs_render_state* st, int32_t* status,
+                 void* ws, cudaStream_t stream) {
+  const int64_t n = g->n;
+  const int C = sh_count(order);
+  const int64_t n_pix = (int64_t)cam->width * cam->height;
+  Carver cv(ws);
+  float* F = cv.take<float>((size_t)C * n * 3);
+  float* TI = cv.take<float>((size_t)C * 3 * n_pix);
+  float* zero = cv.take<float>(4);
+  void* rws = static_cast<char*>(ws) + cv.off;
+  cudaMemsetAsync(zero, 0, sizeof(float) * 4, stream);
+  if (n > 0) {
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (t_channels == 3) k_transfer_features<3><<<blocks, 256, 0, stream>>>(n, C, T, g->albedo, F);
+    else k_transfer_features<1><<<blocks, 256, 0, stream>>>(n, C, T, g->albedo, F);
+    if (n_glossy > 0) {
+      const unsigned gb = (unsigned)((n_glossy + 255) / 256);
+      const float px = cam->pos[0], py = cam->pos[1], pz = cam->pos[2];
+      switch (order) {
+        case 1: k_glossy_features<1><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        case 2: k_glossy_features<2><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        default: k_glossy_features<3><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+      }
+    }
+    PRTGS_CHECK_LAUNCH();
+  }
+  int rc = render(g, F, C, cam, zero, TI, st, status, rws, stream);
+  if (rc != PRTGS_OK) return rc;
+  if (precision != PRTGS_PREC_FP32)
+    return relight_tc_pixels(n_pix, order, TI, st->final_T, bg, L, k, precision, image, stream);
+  const size_t smem = sizeof(float) * k * 3 * C;
+  const unsigned blocks = (unsigned)((n_pix + kRelightThreads - 1) / kRelightThreads);
+  switch (order) {
+    case 1: k_pixel_relight<4><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    case 2: k_pixel_relight<9><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    default: k_pixel_relight<16><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+  }
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
 // ---- many scenes in one launch: scene b (Gaussians offsets[b] .. offsets[b+1]) has its own
 // k lights L[b] --------------------------------------------------------------------------------
 template <int C, int TCH>

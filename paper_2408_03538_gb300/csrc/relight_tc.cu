@@ -107,12 +107,16 @@ __device__ __forceinline__ void load_lights(unsigned char* sB, const float* __re
 // offsets[b+1]) uses lights L + b * k * 3 * C; a tile that straddles scenes is run once per
 // scene with the other rows zeroed. n_pad: N of each MMA; TMEM group g starts at column
 // g * n_pad.
-template <int C, int TCH>
+// PIXEL: the rows are the n pixels of a transfer image TI[C][3][n] (the composite of the splats'
+// (rho/pi) T); colors is the image [k][3][n] and receives D + bg[c] final_T[p] (albedo holds
+// final_T); otherwise rows are splats, T is [n][TCH][C] and colors [k][n][3] gets rho/pi D.
+template <int C, int TCH, bool PIXEL = false>
 __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const float* __restrict__ T,
                                                            const float* __restrict__ albedo,
                                                            const float* __restrict__ L, int k, int n_pad, int slabs,
                                                            int tmem_cols, const int64_t* __restrict__ offsets,
-                                                           int n_scenes, float* __restrict__ colors) {
+                                                           int n_scenes, float* __restrict__ colors,
+                                                           const float* __restrict__ bgv = nullptr) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // layout: [A groups x slabs][B groups x slabs]
   unsigned char* sA = smem_raw;
@@ -147,7 +151,15 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
     const int64_t gi = row0 + row;
     float tv[TCH][kKW];  // this thread's part of the row's K = 16
-    if (C == 16 && t_vec && gi < n) {
+    if (PIXEL) {
+#pragma unroll
+      for (int g = 0; g < TCH; ++g)
+#pragma unroll
+        for (int j = 0; j < kKW; ++j) {
+          const int m = kKW * khalf + j;
+          tv[g][j] = (gi < n && m < C) ? __ldg(T + ((int64_t)m * 3 + g) * n + gi) : 0.f;
+        }
+    } else if (C == 16 && t_vec && gi < n) {
       const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + kKW * khalf);
 #pragma unroll
       for (int g = 0; g < TCH; ++g)
@@ -168,10 +180,19 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
           tv[g][j] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
         }
     }
-    float rho[3] = {0.f, 0.f, 0.f};
+    float rho[3] = {0.f, 0.f, 0.f}, add[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
+      if (PIXEL) {
+        const float ft = __ldg(albedo + gi);  // final transmittance of the pixel
 #pragma unroll
-      for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * gi + c) * (1.0f / kPi);
+        for (int c = 0; c < 3; ++c) {
+          rho[c] = 1.0f;
+          add[c] = bgv ? bgv[c] * ft : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * gi + c) * (1.0f / kPi);
+      }
     }
     for (int b = b_first; b <= b_last; ++b) {
       const int64_t lo = offsets ? (offsets[b] > row0 ? offsets[b] : row0) : row0;
@@ -266,9 +287,14 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const uint32_t bits = TCH == 1 ? r[3 * ll + c] : r[8 * c + ll];
-            v[c] = done ? __uint_as_float(bits) * rho[c] : __int_as_float(0x7fc00000);
+            v[c] = done ? fmaf(__uint_as_float(bits), rho[c], add[c]) : __int_as_float(0x7fc00000);
           }
-          if (mine) {
+          if (PIXEL) {
+            if (mine) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) colors[((int64_t)l * 3 + c) * n + gi] = v[c];
+            }
+          } else if (mine) {
             float* out = cb + ((int64_t)l * nb + (gi - ob)) * 3;
             out[0] = v[0];
             out[1] = v[1];
@@ -310,6 +336,40 @@ int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad_out, int* tmem_co
   if (n_pad_out) *n_pad_out = n_pad;
   if (tmem_cols_out) *tmem_cols_out = cols;
   return 1;
+}
+
+// Pixel-space relight on the tensor cores: image[l,c,p] = sum_m TI[m,c,p] L[l,c,m] + bg[c] final_T[p].
+int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float* final_T, const float* bg,
+                      const float* L, int32_t k, int32_t precision, float* image, cudaStream_t stream) {
+  if (n_pix == 0 || k == 0) return PRTGS_OK;
+  int n_pad = 0, tmem_cols = 0;
+  if (!relight_tc_shape(k, 3, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
+  const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
+  const size_t smem = (size_t)3 * slabs * kSlabBytesA + (size_t)3 * slabs * n_pad * 32 + 1024;
+  if (smem > 227 * 1024) return PRTGS_ERR_UNSUPPORTED;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (n_pix + kTcRows - 1) / kTcRows;
+  int per_sm = 512 / tmem_cols;
+  const int by_smem = (int)((228 * 1024) / (smem + 1024));
+  if (per_sm > by_smem) per_sm = by_smem;
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t want = (int64_t)sms * per_sm;
+  const int grid = (int)(tiles < want ? tiles : want);
+#define PRTGS_PIX_LAUNCH(CC)                                                                                     \
+  cudaFuncSetAttribute(k_relight_tc<CC, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+  k_relight_tc<CC, 3, true><<<grid, kTcThreads, smem, stream>>>(n_pix, TI, final_T, L, k, n_pad, slabs, tmem_cols, \
+                                                                nullptr, 1, image, bg)
+  switch (order) {
+    case 1: PRTGS_PIX_LAUNCH(4); break;
+    case 2: PRTGS_PIX_LAUNCH(9); break;
+    default: PRTGS_PIX_LAUNCH(16); break;
+  }
+#undef PRTGS_PIX_LAUNCH
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
 }
 
 int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,

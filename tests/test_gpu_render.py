@@ -364,3 +364,72 @@ def test_relight_1m_64_lights_tensor_cores_full_size():
     err = oracle.norm_err(got.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
     assert gsel.sum() > 1000
     assert err.max() < 1e-4, err.max()
+
+
+# ---- pixel-space relight of many lights ----------------------------------------------------
+@pytest.mark.parametrize("precision,bar", [(0, 50.0), (1, 50.0), (2, 30.0)])
+def test_render_relit_matches_oracle(precision, bar):
+    """Composite the splats' (rho/pi) T once, contract per pixel with 12 lights: equals the FP64
+    oracle's relight + composite of each light (30 % glossy splats, RGB transfer, background)."""
+    sc = S.surface_scene(1500, 44)
+    sc.means *= 0.5
+    rng = np.random.default_rng(44)
+    n, C, k = sc.n, 16, 12
+    T = (rng.standard_normal((n, 3, C)) * 0.3 + np.eye(C)[0] * 1.2).astype(np.float32)
+    L = S.env_lights(k, 3, 45)
+    gids = np.sort(rng.choice(n, 450, replace=False)).astype(np.int32)
+    M = (rng.standard_normal((gids.size, C, C)) * 0.1 + np.eye(C) * 0.8).astype(np.float32)
+    cam = S.look_at_camera((0, -4.0, 2.0), (0, 0, 0.4), 45, 96, 80)
+    bg = np.array([0.05, 0.1, 0.2], np.float32)
+    g = api.GaussianTensors.from_scene(sc)
+    st = api.Status()
+    img, _ = api.render_relit(g, _cuda(T), _cuda(L), cam, 3, bg=_cuda(bg), precision=precision,
+                              glossy_ids=_cuda(gids, torch.int32), M=_cuda(M), status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    col = oracle.relight(T, sc.albedo, L, glossy_ids=gids, M=M, means=sc.means, cam_pos=np.asarray(cam.position),
+                         order=3)
+    t = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    ref = OR.render(t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(col), cam, tuple(bg)).numpy()
+    img = img.cpu().numpy()
+    peak = float(np.abs(ref).max())
+    for l in range(k):
+        assert OR.psnr(img[l], ref[l], peak=peak) >= bar, l
+    assert img.std() > 1e-3
+
+
+def test_render_relit_full_size_64_lights_equals_per_light_path():
+    """1M tiled glossy splats, 64 lights, 1920x1080: the pixel-space relight (tcgen05 BF16x3)
+    equals relight + 64 composites (FP32) to >= 50 dB on every light, and is timed beside it."""
+    sc = S.make_scene("tiled-1m-glossy")
+    cam = S.make_camera("tiled-1m-glossy")
+    rng = np.random.default_rng(8)
+    n, C, k = sc.n, 16, 64
+    T = torch.from_numpy((rng.standard_normal((n, 3, C)) * 0.3 + np.eye(C)[0] * 1.2).astype(np.float32)).cuda()
+    L = _cuda(S.env_lights(k, 3, 9))
+    gids = torch.from_numpy(np.nonzero(sc.glossy_mask)[0].astype(np.int32)).cuda()
+    M = torch.from_numpy((rng.standard_normal((gids.numel(), C, C)) * 0.1 + np.eye(C) * 0.8)
+                         .astype(np.float32)).cuda()
+    g = api.GaussianTensors.from_scene(sc)
+    bg = _cuda(np.array([0.05, 0.1, 0.2], np.float32))
+    cam_pos = _cuda(np.asarray(cam.position, np.float32))
+    st = api.Status()
+    state = api.RenderState(n, cam.width, cam.height, 40_000_000)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    img_px, _ = api.render_relit(g, T, L, cam, 3, bg=bg, precision=1, glossy_ids=gids, M=M, state=state, status=st)
+    ev[0].record()
+    img_px, _ = api.render_relit(g, T, L, cam, 3, bg=bg, precision=1, glossy_ids=gids, M=M, state=state, status=st,
+                                 out=img_px)
+    ev[1].record()
+    col = api.relight(T, g.albedo, L, 3, glossy_ids=gids, M=M, means=g.means, cam_pos=cam_pos)
+    img_pl, _ = api.render(g, col, cam, bg, state=state, status=st)
+    ev[2].record()
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    ms_px, ms_pl = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    print(f"pixel-space {ms_px:.2f} ms, per-light {ms_pl:.2f} ms")
+    a, b = img_px.double(), img_pl.double()
+    peak = float(b.abs().max())
+    for l in range(k):
+        mse = float(((a[l] - b[l]) ** 2).mean())
+        assert mse == 0 or 10 * math.log10(peak * peak / mse) >= 50.0, l
