@@ -639,9 +639,10 @@ def run_diff(args):
 def run_tiled(args):
     """The 1M-splat tiled glossy workload (the surface scene tiled 5 x 2, 30 % glossy, order 3,
     S = 256): a step is BVH build -> transfer (shadow + bounce + the 16 x 16 glossy matrices) ->
-    relight under 64 lights on the tensor cores (BF16x3, glossy rows in FP32) -> 64 composites at
-    1920x1080. Reports nominal transfer rays/s of the whole step; frames/s counts the 64 relit
-    1080p images of a step."""
+    the 64 lights' 1920x1080 images in pixel space (one composite of the transfer features, one
+    tcgen05 BF16x3 contraction). Reports nominal transfer rays/s of the whole step; frames/s
+    counts the 64 relit 1080p images of a step. The per-light form (relight + 64 composites) is
+    timed beside it."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -674,7 +675,9 @@ def run_tiled(args):
             "idx": torch.empty((g.n, int(dirs.shape[0])), dtype=torch.int32, device=dev)}
     colors = torch.empty((k, g.n, 3), device=dev)
     stream = torch.cuda.current_stream()
-    names = ["bvh", "transfer", "relight", "render"]
+    names = ["bvh", "transfer", "relight_render_64_lights"]
+
+    image = torch.empty((k, 3, cam.height, cam.width), device=dev)
 
     def step(ev):
         ev[0].record(stream)
@@ -682,32 +685,44 @@ def run_tiled(args):
         ev[1].record(stream)
         out = api.precompute_transfer(g, bvh, dirs, order, bounce=True, glossy=True, status=status, out=bufs)
         ev[2].record(stream)
-        api.relight(out["T"], g.albedo, Lsh, order, precision=1, glossy_ids=gids, M=out["M"], means=g.means,
-                    cam_pos=cam_pos, out=colors)
+        # all 64 lights in pixel space: one composite of the transfer features, one contraction
+        api.render_relit(g, out["T"], Lsh, cam, order, bg=bg, precision=1, glossy_ids=gids, M=out["M"],
+                         state=state, status=status, out=image)
         ev[3].record(stream)
-        img, _ = api.render(g, colors, cam, bg, state=state, status=status)
-        ev[4].record(stream)
-        return img
+        return out
 
     for _ in range(args.warmup):
-        step([torch.cuda.Event(enable_timing=True) for _ in range(5)])
+        out = step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
     torch.cuda.synchronize()
     assert status.read() == 0, "device status reported an error"
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    stage_ms = np.zeros(4)
+    stage_ms = np.zeros(3)
     total = 0.0
     for _ in range(args.steps):
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        step(ev)
-        ev[4].synchronize()
-        for i in range(4):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        out = step(ev)
+        ev[3].synchronize()
+        for i in range(3):
             stage_ms[i] += ev[i].elapsed_time(ev[i + 1])
-        total += ev[0].elapsed_time(ev[4])
+        total += ev[0].elapsed_time(ev[3])
     clocks = sampler.stop()
+    # the per-light form beside it (outside the timed step): relight of every splat under each
+    # light, then one composite per light
+    per_light = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.relight(out["T"], g.albedo, Lsh, order, precision=1, glossy_ids=gids, M=out["M"], means=g.means,
+                    cam_pos=cam_pos, out=colors)
+        api.render(g, colors, cam, bg, state=state, status=status, out=image)
+        e1.record(stream)
+        e1.synchronize()
+        per_light.append(e0.elapsed_time(e1))
     assert status.read() == 0
     total, = reduce_max_over_ranks([total], dev)
     rays = g.n * int(dirs.shape[0])
@@ -721,6 +736,7 @@ def run_tiled(args):
                        "l2": "flushed between steps (256 MB write)"},
             "frames_per_s": world * k * args.steps / (total / 1e3),
             "stages_ms": {nm: float(v / args.steps) for nm, v in zip(names, stage_ms)},
+            "per_light_relight_render_ms": float(np.median(per_light)),
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
