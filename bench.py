@@ -401,7 +401,8 @@ def run_kernels_small():
     relight of 1M splats x 64 lights on the tensor cores and on the CUDA cores, a 1280x720
     render forward + backward of the 100k surface scene, and the transfer backward of the 20k
     scene; then every other kernel of the library once (shadow-only walk, glossy matrices,
-    relight with RGB transfer and glossy rows, batched relight, loss, relight backward)."""
+    relight with RGB transfer and glossy rows, batched relight, loss, relight backward,
+    three-bounce self-transfer, pixel-space relight)."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -450,6 +451,11 @@ def run_kernels_small():
     Lb = torch.randn((1, 3, 16), device="cuda", generator=gen)
     Tb = torch.randn((g2.n, 3, 16), device="cuda", generator=gen)
     api.relight_backward(Tb, g2.albedo, Lb, 3, dcol, need_dT=True)
+    # three-bounce self-transfer and the pixel-space relight of 8 lights (FP32 and tensor cores)
+    api.precompute_transfer(gg, api.build_bvh(gg), dirs, 3, bounce=True, n_bounces=3)
+    for prec in (0, 1):
+        api.render_relit(gg, outg["T"], L8, cam, 3, bg=bg, precision=prec, glossy_ids=gids, M=outg["M"],
+                         max_pairs=4_000_000)
     torch.cuda.synchronize()
     print(json.dumps({"case": "kernels-small", "idx_max": int(out["idx"].max()),
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
