@@ -346,6 +346,17 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
                        prtgs_stream_t stream);
 
 /*
+ * Depth and normal maps of the splats (Eq. 23 and Eq. 25): front-to-back composites, with the
+ * blending weights of prtgs_render, of each splat's view-space depth d_i (the z of its mean in
+ * camera space) and of its normal n_i as given. Background 0. Fills *st like prtgs_render.
+ *   depth[H,W], normal[3,H,W] out (device). Workspace: prtgs_render_geometry_workspace_size.
+ */
+size_t prtgs_render_geometry_workspace_size(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+int prtgs_render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* depth, float* normal,
+                          prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                          prtgs_stream_t stream);
+
+/*
  * Render backward: dimage[k,3,H,W] in; gradients out (overwritten): d_means[n,3],
  * d_scales[n,3], d_quats[n,4], d_opacity[n], d_colors[k,n,3]. Uses the state written by the
  * matching prtgs_render call. Gradients of the discrete decisions (culling, tile binning,

@@ -73,6 +73,9 @@ _SIGS = {
     "prtgs_render_relit": (c_int32, [P(Gaussians), c_int32, c_void_p, c_int32, c_int64, c_void_p, c_void_p,
                                      c_void_p, c_int32, c_int32, P(Camera), c_void_p, c_void_p, P(RenderState),
                                      c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_render_geometry_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int64]),
+    "prtgs_render_geometry": (c_int32, [P(Gaussians), P(Camera), c_void_p, c_void_p, P(RenderState), c_void_p,
+                                        c_void_p, c_size_t, c_void_p]),
     "prtgs_relight_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "prtgs_relight": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t,

@@ -328,6 +328,26 @@ def render_relit(g: GaussianTensors, T: torch.Tensor, Lsh: torch.Tensor, cam, or
     return image, state
 
 
+def render_geometry(g: GaussianTensors, cam, state: RenderState | None = None, max_pairs: int | None = None,
+                    status: Status | None = None):
+    """Depth map [H,W] and normal map [3,H,W]: composites of the splats' view-space depth and
+    normal (Eq. 23, Eq. 25)."""
+    lib = L.load()
+    dev = g.means.device
+    if state is None:
+        state = RenderState(g.n, cam.width, cam.height, max_pairs or max(16 * g.n, 1 << 16), dev)
+    depth = torch.empty((cam.height, cam.width), dtype=torch.float32, device=dev)
+    normal = torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=dev)
+    ws, nb = _ws(lib.prtgs_render_geometry_workspace_size(g.n, cam.width, cam.height, state.max_pairs), dev)
+    gs = g.struct()
+    cs = camera_struct(cam)
+    L.check(lib.prtgs_render_geometry(ctypes.byref(gs), ctypes.byref(cs), _ptr(depth), _ptr(normal),
+                                      ctypes.byref(state.s), status.ptr() if status else None, _ptr(ws), nb,
+                                      _stream()), "prtgs_render_geometry")
+    state._ws = ws
+    return depth, normal, state
+
+
 def render_backward(g: GaussianTensors, colors, cam, bg, state: RenderState, dimage):
     lib = L.load()
     k = int(colors.shape[0])

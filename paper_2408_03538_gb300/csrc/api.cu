@@ -276,6 +276,24 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
                              st, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t prtgs_render_geometry_workspace_size(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {
+  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0) return 0;
+  return render_geometry_workspace(n, width, height, max_pairs);
+}
+
+int prtgs_render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* depth, float* normal,
+                          prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                          prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if ((rc = check_camera(cam))) return rc;
+  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (!depth || !normal || (g->n > 0 && !g->normals)) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, render_geometry_workspace(g->n, cam->width, cam->height, st->max_pairs));
+  if (rc) return rc;
+  return finish(render_geometry(g, cam, depth, normal, st, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
                  const float* bg, float* image, prtgs_render_state* st, int32_t* status, void* workspace,
                  size_t workspace_bytes, prtgs_stream_t stream) {

@@ -69,6 +69,9 @@ int render_state_layout(void* buffer, int64_t n, int32_t width, int32_t height, 
 size_t render_workspace(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
 int render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam, const float* bg,
            float* image, prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream);
+size_t render_geometry_workspace(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+int render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* depth, float* normal,
+                    prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream);
 size_t render_backward_workspace(int64_t n, int32_t k);
 int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
                     const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,

@@ -620,6 +620,51 @@ __global__ void k_preprocess_bwd(int64_t n, const float* __restrict__ means, con
   for (int k2 = 0; k2 < 4; ++k2) d_quats[4 * i + k2] = gq[k2];
 }
 
+// ---- depth and normal maps (Eq. 23, Eq. 25): the composite of d_i and n_i -------------------------
+// Features for render() with two "lights": light 0 carries (d_i, 0, 0), d_i the view-space
+// depth of the splat's mean; light 1 carries the raw normal n_i.
+__global__ void k_geometry_features(int64_t n, Cam c, const float* __restrict__ means,
+                                    const float* __restrict__ normals, float* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = means[3 * i], y = means[3 * i + 1], z = means[3 * i + 2];
+  const float d = fmaf(c.r[6], x, fmaf(c.r[7], y, fmaf(c.r[8], z, c.t[2])));
+  F[3 * i] = d;
+  F[3 * i + 1] = 0.f;
+  F[3 * i + 2] = 0.f;
+  float* Fn = F + 3 * n;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Fn[3 * i + k] = normals[3 * i + k];
+}
+
+size_t render_geometry_workspace(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {
+  return align_up(sizeof(float) * 6 * (size_t)n) + align_up(sizeof(float) * 6 * (size_t)width * height) +
+         align_up(sizeof(float) * 4) + render_workspace(n, width, height, max_pairs);
+}
+
+int render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* depth, float* normal,
+                    prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream) {
+  const int64_t n = g->n;
+  const int64_t n_pix = (int64_t)cam->width * cam->height;
+  Carver cv(ws);
+  float* F = cv.take<float>(6 * (size_t)n);
+  float* img = cv.take<float>(6 * (size_t)n_pix);
+  float* zero = cv.take<float>(4);
+  void* rws = static_cast<char*>(ws) + cv.off;
+  cudaMemsetAsync(zero, 0, sizeof(float) * 4, stream);
+  if (n > 0) {
+    k_geometry_features<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, make_cam(cam), g->means, g->normals, F);
+    PRTGS_CHECK_LAUNCH();
+  }
+  const int rc = render(g, F, 2, cam, zero, img, st, status, rws, stream);
+  if (rc != PRTGS_OK) return rc;
+  // image [2][3][H][W]: depth is light 0's first channel, the normal light 1's three channels
+  cudaMemcpyAsync(depth, img, sizeof(float) * n_pix, cudaMemcpyDeviceToDevice, stream);
+  cudaMemcpyAsync(normal, img + 3 * n_pix, sizeof(float) * 3 * n_pix, cudaMemcpyDeviceToDevice, stream);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
 size_t render_backward_workspace(int64_t n, int32_t) {
   return align_up(sizeof(float) * 2 * n) + align_up(sizeof(float) * 3 * n);
 }

@@ -433,3 +433,27 @@ def test_render_relit_full_size_64_lights_equals_per_light_path():
     for l in range(k):
         mse = float(((a[l] - b[l]) ** 2).mean())
         assert mse == 0 or 10 * math.log10(peak * peak / mse) >= 50.0, l
+
+
+def test_depth_and_normal_maps_match_oracle():
+    """Eq. 23 and Eq. 25: composites of each splat's view-space depth and normal (background 0)
+    against the FP64 oracle's composite of the same per-splat values."""
+    sc = S.surface_scene(2000, 51)
+    sc.means *= 0.5
+    cam = S.look_at_camera((0, -4.0, 2.0), (0, 0, 0.4), 45, 120, 90)
+    g = api.GaussianTensors.from_scene(sc)
+    st = api.Status()
+    depth, normal, _ = api.render_geometry(g, cam, status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    m = np.asarray(sc.means, np.float64)
+    d = m @ np.asarray(cam.rot, np.float64)[2] + float(np.asarray(cam.trans, np.float64)[2])
+    feats = np.zeros((2, sc.n, 3))
+    feats[0, :, 0] = d
+    feats[1] = np.asarray(sc.normals, np.float64)
+    t = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    ref = OR.render(t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(feats), cam).numpy()
+    dref, nref = ref[0, 0], ref[1]
+    assert OR.psnr(depth.cpu().numpy(), dref, peak=float(np.abs(dref).max())) >= 60.0
+    assert OR.psnr(normal.cpu().numpy(), nref, peak=1.0) >= 60.0
+    assert float(dref.max()) > 1.0 and float(np.abs(nref).max()) > 0.5
