@@ -367,28 +367,31 @@ def test_relight_1m_64_lights_tensor_cores_full_size():
 
 
 # ---- pixel-space relight of many lights ----------------------------------------------------
-@pytest.mark.parametrize("precision,bar", [(0, 50.0), (1, 50.0), (2, 30.0)])
-def test_render_relit_matches_oracle(precision, bar):
+@pytest.mark.parametrize("precision,bar,order,tch", [(0, 50.0, 3, 3), (1, 50.0, 3, 3), (2, 30.0, 3, 3),
+                                                     (1, 50.0, 2, 1), (0, 50.0, 1, 3), (1, 50.0, 1, 1)])
+def test_render_relit_matches_oracle(precision, bar, order, tch):
     """Composite the splats' (rho/pi) T once, contract per pixel with 12 lights: equals the FP64
-    oracle's relight + composite of each light (30 % glossy splats, RGB transfer, background)."""
+    oracle's relight + composite of each light (30 % glossy splats, background; RGB or scalar
+    transfer, SH orders 1-3)."""
     sc = S.surface_scene(1500, 44)
     sc.means *= 0.5
     rng = np.random.default_rng(44)
-    n, C, k = sc.n, 16, 12
-    T = (rng.standard_normal((n, 3, C)) * 0.3 + np.eye(C)[0] * 1.2).astype(np.float32)
-    L = S.env_lights(k, 3, 45)
+    n, C, k = sc.n, (order + 1) ** 2, 12
+    T = (rng.standard_normal((n, 3, C) if tch == 3 else (n, C)) * 0.3).astype(np.float32)
+    T[..., 0] += 1.2
+    L = S.env_lights(k, order, 45)
     gids = np.sort(rng.choice(n, 450, replace=False)).astype(np.int32)
     M = (rng.standard_normal((gids.size, C, C)) * 0.1 + np.eye(C) * 0.8).astype(np.float32)
     cam = S.look_at_camera((0, -4.0, 2.0), (0, 0, 0.4), 45, 96, 80)
     bg = np.array([0.05, 0.1, 0.2], np.float32)
     g = api.GaussianTensors.from_scene(sc)
     st = api.Status()
-    img, _ = api.render_relit(g, _cuda(T), _cuda(L), cam, 3, bg=_cuda(bg), precision=precision,
+    img, _ = api.render_relit(g, _cuda(T), _cuda(L), cam, order, bg=_cuda(bg), precision=precision,
                               glossy_ids=_cuda(gids, torch.int32), M=_cuda(M), status=st)
     torch.cuda.synchronize()
     assert st.read() == 0
     col = oracle.relight(T, sc.albedo, L, glossy_ids=gids, M=M, means=sc.means, cam_pos=np.asarray(cam.position),
-                         order=3)
+                         order=order)
     t = lambda a: torch.as_tensor(np.asarray(a, np.float64))
     ref = OR.render(t(sc.means), t(sc.scales), t(sc.quats), t(sc.opacity), t(col), cam, tuple(bg)).numpy()
     img = img.cpu().numpy()
