@@ -344,33 +344,8 @@ struct ShadowFrontVis {
   }
 };
 
-// Index-matrix round, part A: the KB nearest front-facing hits with key greater than the
-// previous round's last candidate and t* within the horizon.
-template <int KB>
-struct FrontVis {
-  const TraceArgs& a;
-  const Ray& r;
-  int self;
-  RayStats& st;
-  float t_last;
-  int p_last;
-  float t_hor;
-  FrontBuf<KB> fb;
-  __device__ float t_hi() const { return fminf(slack_hi(fb.t_full()), slack_hi(t_hor)); }
-  __device__ bool stop() const { return false; }
-  __device__ void leaf(int pos) {
-    if (pos == self) return;
-    ++st.leaves;
-    float t, al, m;
-    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
-    ++st.hits;
-    if (!(m > 0.f) || !key_less(t_last, p_last, t, pos)) return;
-    fb.insert(t, pos, al, m);
-  }
-};
-
-// Index-matrix round, part B: log prefix transmittance in front of each candidate,
-// lt[j] += log(1 - alpha_k) for every hit k with previous-last < key_k < key_j.
+// Prefix walk of the index-matrix search (k_prefix): log prefix transmittance in front of each
+// candidate, lt[j] += log(1 - alpha_k) for every hit k with previous-last < key_k < key_j.
 template <int KB>
 struct PrefixVis {
   const TraceArgs& a;
@@ -397,57 +372,6 @@ struct PrefixVis {
       if (j < nc && key_less(t, pos, fb.bt[j], fb.bp[j])) lt[j] += l;
   }
 };
-
-// Index-matrix entry of one ray (Sec. 4.4): argmax_j W_j, W_j = alpha_j T_j max(-d.n_j, 0)
-// (Eq. 26), over eligible hits (T_j <= the same-surface threshold) whose prefix
-// transmittance T_j is at least t_min, compared as logarithms. Rounds of (A, B) walk the
-// front-facing hits in key order, KB at a time, until the prefix past the last candidate
-// cannot exceed the best weight or falls below t_min. Round 0 reuses the candidates of the
-// visibility walk when that walk saw every hit.
-template <int KB>
-__device__ int index_search(const TraceArgs& a, const Ray& r, int root, int self, RayStats& st, bool complete,
-                            float t_hor, const FrontBuf<KB>* seed, float t_last, int p_last, float lt_base,
-                            int best, float lw_best) {
-  const float lfilter = logf(a.filter_t);
-  const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
-  for (int64_t round = 0;; ++round) {
-    if (round > a.n / KB + 1) {  // every full round consumes KB front-facing hits
-      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
-      break;
-    }
-    FrontVis<KB> fa{a, r, self, st, t_last, p_last, t_hor};
-    if (round == 0 && complete && seed) {
-      fa.fb = *seed;
-    } else {
-      ++st.rounds;
-      fa.fb.clear();
-      traverse(a, r, root, t_last, fa, st, st.search_nodes);
-    }
-    const int nc = fa.fb.count();
-    if (nc == 0) break;
-    PrefixVis<KB> pb{a, r, self, st, t_last, p_last, fa.fb, nc};
-#pragma unroll
-    for (int k = 0; k < KB; ++k) pb.lt[k] = lt_base;
-    traverse(a, r, root, t_last, pb, st, st.search_nodes);
-#pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      if (k < nc && pb.lt[k] <= lfilter && pb.lt[k] >= lmin) {
-        float lw = logf(fa.fb.ba[k]) + pb.lt[k] + logf(fa.fb.bm[k]);
-        if (lw > lw_best) {
-          lw_best = lw;
-          best = fa.fb.bp[k];
-        }
-      }
-    }
-    if (nc < KB) break;  // no front-facing hit left within the horizon
-    const float lt_next = pb.lt[KB - 1] + log1pf(-fa.fb.ba[KB - 1]);
-    if (lt_next <= lw_best || lt_next < lmin) break;  // later W_j <= T_j < T_next
-    t_last = fa.fb.bt[KB - 1];
-    p_last = fa.fb.bp[KB - 1];
-    lt_base = lt_next;
-  }
-  return best;
-}
 
 __device__ __forceinline__ float ray_cos(float nx, float ny, float nz, const float* d) {
   return fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));
