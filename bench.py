@@ -43,8 +43,9 @@ def parse():
                     help="batched-32: 32 isotropic scenes, one graph-captured step (measurement of batching); "
                          "diff-300k: differentiable relight + 1080p render of 300k isotropic splats; "
                          "tiled-1m-glossy: 1M splats, 30 %% glossy, 64 lights on the tensor cores")
-    ap.add_argument("--case", default=None, choices=["kernels-small"],
-                    help="run the small profiling case used for the ncu captures instead of the bench")
+    ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders"],
+                    help="kernels-small: the small profiling case of the ncu captures; sh-orders: relight + "
+                         "render and transfer times at SH orders 1-6, instead of the bench")
     return ap.parse_args()
 
 
@@ -461,6 +462,50 @@ def run_kernels_small():
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
 
 
+def run_sh_orders():
+    """Relight + 1920x1080 render of the 100k surface scene under one light at SH orders 1-6
+    (the render-time-against-order measurement of the paper's Table 4), and the shadowed
+    transfer (S = 256) at each order. Median of 20 frames, L2 flushed before each."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    sc = S.make_scene(WORKLOAD)
+    g = api.GaussianTensors.from_scene(sc)
+    cam = S.make_camera(WORKLOAD)
+    bg = torch.zeros(3, device="cuda")
+    bvh = api.build_bvh(g)
+    dirs = torch.from_numpy(S.direction_set(256, S.config_seed(1))).cuda()
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    state = api.RenderState(g.n, cam.width, cam.height, 8_000_000)
+    res = {}
+    for order in range(1, 7):
+        C = (order + 1) ** 2
+        tr = api.precompute_transfer(g, bvh, dirs, order)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record()
+        tr = api.precompute_transfer(g, bvh, dirs, order)
+        e1.record()
+        e1.synchronize()
+        t_ms = e0.elapsed_time(e1)
+        Lsh = torch.from_numpy(S.env_lights(1, order, 5)).cuda()
+        frames = []
+        for _ in range(23):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            colors = api.relight(tr["P"], g.albedo, Lsh, order)
+            api.render(g, colors, cam, bg, state=state)
+            b.record()
+            b.synchronize()
+            frames.append(a.elapsed_time(b))
+        res[str(order)] = {"coefficients": C, "relight_render_ms": float(np.median(frames[3:])),
+                           "transfer_ms": t_ms}
+    print(json.dumps({"case": "sh-orders", "workload": WORKLOAD, "image": f"{cam.width}x{cam.height}",
+                      "by_order": res}))
+
+
 def run_batched(args):
     """32 isotropic scenes (Gaussian counts log-uniform in [1e4, 5e5]), order 3, S = 128, shadowed
     transfer, 8 lights per scene relit, 1280x720 render + L2 loss + backward per scene; the whole
@@ -752,6 +797,8 @@ def main():
     args = parse()
     if args.case == "kernels-small":
         run_kernels_small()
+    elif args.case == "sh-orders":
+        run_sh_orders()
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched-32":

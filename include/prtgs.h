@@ -133,7 +133,9 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
 
 /*
  * Transfer precompute parameters (Sec. 4.4-4.5).
- *   sh_order        1..3 (C = (order+1)^2 coefficients)
+ *   sh_order        1..3 (C = (order+1)^2 coefficients); 4..6 (25-49 coefficients, the SH of the
+ *                   direction set tabulated per call) for the shadowed transfer without
+ *                   PRTGS_BOUNCE or PRTGS_GLOSSY (else PRTGS_ERR_UNSUPPORTED)
  *   n_dirs, dirs    S shared world-space directions [S,3] (device); weight 4 pi / S each
  *   t_min           a ray stops once its transmittance falls below t_min (bounded error
  *                   t_min per ray); 0 disables early exit. Suggested 2^-30.
@@ -217,7 +219,8 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
  * with T [n,C] (t_channels = 1) or [n,3,C] (t_channels = 3). Glossy splats (n_glossy > 0,
  * glossy_ids[n_glossy] their Gaussian indices, M[n_glossy,C,C]) use
  *   t_eff[a] = sum_b M[a,b] Y_b(v_i), v_i = normalize(cam_pos - mean_i).
- * L[k,3,C] light SH per light and channel. precision: PRTGS_PREC_*. The tensor-core paths
+ * L[k,3,C] light SH per light and channel. sh_order 1..3, or 4..6 with PRTGS_PREC_FP32 and no
+ * glossy splats. precision: PRTGS_PREC_*. The tensor-core paths
  * take every row through tcgen05 (one MMA of N = 3k for t_channels = 1, three of N = k for
  * t_channels = 3) and then rewrite the glossy rows in FP32; they need 3k <= 256 (t_channels 1)
  * or k <= 160 (t_channels 3: three accumulators in the 512 TMEM columns), otherwise

@@ -24,6 +24,8 @@ int check_gaussians(const prtgs_gaussians* g) {
 }
 
 int check_order(int32_t order) { return (order >= 1 && order <= 3) ? PRTGS_OK : PRTGS_ERR_UNSUPPORTED; }
+// Orders 4-6 (25-49 coefficients) for the shadowed transfer and the FP32 relight.
+static int check_order_high(int32_t order) { return (order >= 1 && order <= 6) ? PRTGS_OK : PRTGS_ERR_UNSUPPORTED; }
 
 int finish(int rc) {
   if (rc != PRTGS_OK) return rc;
@@ -115,7 +117,8 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
   int rc = check_gaussians(g);
   if (rc) return rc;
   if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
-  if ((rc = check_order(p->sh_order))) return rc;
+  if ((rc = check_order_high(p->sh_order))) return rc;
+  if (p->sh_order > 3 && (p->flags & (PRTGS_BOUNCE | PRTGS_GLOSSY))) return PRTGS_ERR_UNSUPPORTED;
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
   if (p->n_bounces < 0 || p->n_bounces > 64) return PRTGS_ERR_INVALID_ARG;
@@ -171,9 +174,10 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
                   void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
   int rc;
   if (n < 0 || k < 0 || n_glossy < 0 || n_glossy > n) return PRTGS_ERR_SHAPE;
-  if ((rc = check_order(sh_order))) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
+  if (sh_order > 3 && (precision != PRTGS_PREC_FP32 || n_glossy > 0)) return PRTGS_ERR_UNSUPPORTED;
   if (n == 0 || k == 0) return PRTGS_OK;
   if (!T || !albedo || !L || !colors) return PRTGS_ERR_INVALID_ARG;
   if (n_glossy > 0 && (!glossy_ids || !M || !means || !cam_pos)) return PRTGS_ERR_INVALID_ARG;

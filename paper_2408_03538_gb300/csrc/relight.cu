@@ -93,6 +93,30 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_glossy(int64_t n, i
   }
 }
 
+// Orders 4-6 (25-49 coefficients): one thread per Gaussian, the transfer row and the lights read
+// through the cache instead of held in registers.
+__global__ void __launch_bounds__(kRelightThreads) k_relight_any(int64_t n, int C, int tch, const float* __restrict__ T,
+                                                                 const float* __restrict__ albedo,
+                                                                 const float* __restrict__ L, int k,
+                                                                 float* __restrict__ colors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+  for (int l = 0; l < k; ++l) {
+    float* out = colors + ((int64_t)l * n + i) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* t = T + (i * tch + (tch > 1 ? c : 0)) * C;
+      const float* Ll = L + ((int64_t)l * 3 + c) * C;
+      float d = 0.f;
+      for (int m = 0; m < C; ++m) d = fmaf(__ldg(t + m), __ldg(Ll + m), d);
+      out[c] = r[c] * d;
+    }
+  }
+}
+
 size_t relight_workspace(int64_t, int32_t, int32_t, int32_t) { return 0; }
 
 template <int C>
@@ -123,6 +147,12 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
       case 1: launch_relight_c<4>(n, T, t_channels, albedo, L, k, colors, stream); break;
       case 2: launch_relight_c<9>(n, T, t_channels, albedo, L, k, colors, stream); break;
       case 3: launch_relight_c<16>(n, T, t_channels, albedo, L, k, colors, stream); break;
+      case 4:
+      case 5:
+      case 6:
+        k_relight_any<<<(unsigned)((n + kRelightThreads - 1) / kRelightThreads), kRelightThreads, 0, stream>>>(
+            n, sh_count(order), t_channels, T, albedo, L, k, colors);
+        break;
       default: return PRTGS_ERR_UNSUPPORTED;
     }
     PRTGS_CHECK_LAUNCH();

@@ -54,6 +54,7 @@ struct TraceArgs {
   const float* dirs;
   int S;
   int sh_order;
+  const float* Ytab;          // [S][C] SH of the directions for orders above 3 (else unused)
   float t_min;
   float filter_t;
   uint32_t flags;
@@ -373,6 +374,48 @@ struct PrefixVis {
   }
 };
 
+// Real SH up to order 6 of the direction set, one thread per direction, in double precision and
+// rounded once: Y_l0 = K_l0 Q_l^0(z), Y_l(+-m) = sqrt2 K_lm Q_l^m(z) {Re, Im}(x + i y)^m, with
+// Q_l^m = P_l^m / sin^m (Condon-Shortley phase) from Q_m^m = (-1)^m (2m-1)!!,
+// Q_{m+1}^m = (2m+1) z Q_m^m, (l-m) Q_l^m = (2l-1) z Q_{l-1}^m - (l+m-1) Q_{l-2}^m, and
+// K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), index l*l+l+m as for orders <= 3.
+__global__ void k_sh_table(int S, int order, const float* __restrict__ dirs, float* __restrict__ Y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const double x = dirs[3 * s], y = dirs[3 * s + 1], z = dirs[3 * s + 2];
+  const int C = (order + 1) * (order + 1);
+  double re = 1.0, im = 0.0;  // (x + i y)^m
+  double qmm = 1.0;           // Q_m^m
+  for (int m = 0; m <= order; ++m) {
+    if (m > 0) {
+      const double r2 = re * x - im * y, i2 = re * y + im * x;
+      re = r2;
+      im = i2;
+      qmm *= -(2.0 * m - 1.0);
+    }
+    double q2 = 0.0, q1 = qmm;  // Q_{l-2}^m, Q_{l-1}^m walking up in l
+    for (int l = m; l <= order; ++l) {
+      double q;
+      if (l == m) q = qmm;
+      else if (l == m + 1) q = (2.0 * m + 1.0) * z * qmm;
+      else q = ((2.0 * l - 1.0) * z * q1 - (double)(l + m - 1) * q2) / (double)(l - m);
+      if (l > m) {
+        q2 = q1;
+        q1 = q;
+      }
+      double ratio = 1.0;  // (l-m)! / (l+m)!
+      for (int j = l - m + 1; j <= l + m; ++j) ratio /= (double)j;
+      const double K = sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
+      if (m == 0) {
+        Y[(int64_t)s * C + l * l + l] = (float)(K * q);
+      } else {
+        Y[(int64_t)s * C + l * l + l + m] = (float)(1.4142135623730951 * K * q * re);
+        Y[(int64_t)s * C + l * l + l - m] = (float)(1.4142135623730951 * K * q * im);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ float ray_cos(float nx, float ny, float nz, const float* d) {
   return fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));
 }
@@ -463,6 +506,19 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
       vis[s] = V;
     }
     __syncwarp();
+    if (C > kMaxC) {
+      // orders above 3: one lane per coefficient, compensated over the directions, the SH from
+      // the table
+      for (int k = lane; k < C; k += 32) {
+        CompSum acc;
+        for (int s = 0; s < a.S; ++s) {
+          const float c = ray_cos(q3.y, q3.z, q3.w, sdir + 3 * s);
+          if (!(c > 0.0f)) continue;
+          acc.add(vis[s] * c * wq * __ldg(a.Ytab + (int64_t)s * C + k));
+        }
+        a.P[(int64_t)gid * C + k] = acc.value();
+      }
+    } else {
     // SH projection of V (n.w)^+ with a compensated sum per lane, then across the warp
     float ps[kMaxC], pc[kMaxC];
 #pragma unroll
@@ -493,6 +549,7 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
       }
     }
     if (lane < C) a.P[(int64_t)gid * C + lane] = mine;
+    }
     if (a.stats) {
       unsigned long long c0 = warp_sum_u64(rs.nodes), c1 = warp_sum_u64(rs.search_nodes),
                          c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits), c4 = warp_sum_u64(rs.rounds);
@@ -1199,6 +1256,7 @@ static int index_buffer_of(const prtgs_transfer_params* p) {
 
 size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p) {
   size_t b = 2 * align_up(sizeof(unsigned int));
+  if (sh_count(p->sh_order) > kMaxC) b += align_up(sizeof(float) * (size_t)p->n_dirs * sh_count(p->sh_order));
   if (p->flags & PRTGS_BOUNCE) {
     const size_t rays = (size_t)trace_batch(n, p->n_dirs) * p->n_dirs;
     b += align_up(queue_rec_bytes(index_buffer_of(p)) * rays) + 3 * align_up(sizeof(uint32_t) * rays) +
@@ -1272,6 +1330,7 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   void* rscan_ws = bounce ? c.take<char>(scan_workspace((int64_t)batch_rays)) : nullptr;
   RoundRec* more = bounce ? c.take<RoundRec>(batch_rays) : nullptr;
   unsigned int* more_count = bounce ? c.take<unsigned int>(1) : nullptr;
+  float* ytab = C > kMaxC ? c.take<float>((size_t)S * C) : nullptr;
   float* tb[2] = {nullptr, nullptr};  // ping-pong bounce buffers [n,3,C] for n_bounces > 1
   if (bounce && n_bounces_of(p) > 1) tb[0] = c.take<float>((size_t)n * 3 * C);
   if (bounce && n_bounces_of(p) > 2) tb[1] = c.take<float>((size_t)n * 3 * C);
@@ -1301,6 +1360,11 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.dirs = p->dirs;
   a.S = S;
   a.sh_order = p->sh_order;
+  a.Ytab = ytab;
+  if (ytab) {
+    k_sh_table<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(S, p->sh_order, p->dirs, ytab);
+    PRTGS_CHECK_LAUNCH();
+  }
   a.t_min = p->t_min;
   a.filter_t = p->same_surface_t;
   a.flags = p->flags;

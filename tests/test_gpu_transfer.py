@@ -416,3 +416,40 @@ def test_multi_bounce_full_size_is_polynomial_in_albedo():
     err = (D[0.25] - pred).norm() / D[0.25].norm()
     assert float(err) < 1e-5, float(err)
     assert float(b.norm()) > 1e-3 * float(a.norm())  # the second bounce is there
+
+
+# ---- SH orders 4-6 (25-49 coefficients): shadowed transfer and FP32 relight -------------------
+@pytest.mark.parametrize("order", [4, 6])
+def test_high_order_transfer_and_relight_match_oracle(order):
+    """Orders above 3 project through a per-call SH table (one lane per coefficient); P against
+    the oracle (norm-wise 1e-4 + allowance), and the FP32 relight of seeded scalar and RGB
+    transfers at that order against the oracle."""
+    sc = S.isotropic_scene(700, 60 + order)
+    dirs = S.direction_set(96, 7)
+    out = _transfer_gpu(sc, dirs, order)
+    ref = oracle.transfer(sc, dirs, order, np.arange(sc.n))
+    _check_norm(out["P"], ref["P"], ref["allow_P"], 1e-3 * oracle.unoccluded_norm(order))
+    C = (order + 1) ** 2
+    rng = np.random.default_rng(order)
+    Lsh = rng.standard_normal((5, 3, C)).astype(np.float32)
+    for Tin in (rng.standard_normal((sc.n, C)).astype(np.float32),
+                rng.standard_normal((sc.n, 3, C)).astype(np.float32)):
+        col = api.relight(torch.from_numpy(Tin).cuda(), _gt(sc).albedo, torch.from_numpy(Lsh).cuda(),
+                          order).cpu().numpy()
+        cref = oracle.relight(Tin, sc.albedo, Lsh)
+        err = oracle.norm_err(col.transpose(1, 0, 2), cref.transpose(1, 0, 2), 1e-3)
+        assert err.max() < 1e-5
+
+
+def test_high_order_rejects_what_it_does_not_cover():
+    sc = S.isotropic_scene(50, 3)
+    g = _gt(sc)
+    bvh = api.build_bvh(g)
+    d = torch.from_numpy(S.direction_set(32, 1)).cuda()
+    with pytest.raises(Exception):
+        api.precompute_transfer(g, bvh, d, 6, bounce=True)
+    with pytest.raises(Exception):
+        api.relight(torch.zeros((50, 49), device="cuda"), g.albedo, torch.zeros((1, 3, 49), device="cuda"), 6,
+                    precision=1)
+    with pytest.raises(Exception):
+        api.precompute_transfer(g, bvh, d, 7)

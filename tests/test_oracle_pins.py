@@ -84,7 +84,7 @@ def test_direction_set_is_unit_and_equal_area():
     assert np.all(np.abs(np.sort(k) - (np.arange(4096) + 0.5)) <= 0.5 + 1e-3)
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 6])
 def test_unoccluded_transfer_is_clamped_cosine(oracle_mod, order):
     """An unoccluded splat's transfer is A_l Y_lm(n) (Ramamoorthi & Hanrahan 2001)."""
     rng = np.random.default_rng(order)
