@@ -134,8 +134,8 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
 /*
  * Transfer precompute parameters (Sec. 4.4-4.5).
  *   sh_order        1..3 (C = (order+1)^2 coefficients); 4..6 (25-49 coefficients, the SH of the
- *                   direction set tabulated per call) for the shadowed transfer without
- *                   PRTGS_BOUNCE or PRTGS_GLOSSY (else PRTGS_ERR_UNSUPPORTED)
+ *                   direction set tabulated per call) without PRTGS_GLOSSY (else
+ *                   PRTGS_ERR_UNSUPPORTED)
  *   n_dirs, dirs    S shared world-space directions [S,3] (device); weight 4 pi / S each
  *   t_min           a ray stops once its transmittance falls below t_min (bounded error
  *                   t_min per ray); 0 disables early exit. Suggested 2^-30.

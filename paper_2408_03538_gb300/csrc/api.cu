@@ -118,7 +118,7 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
   if (rc) return rc;
   if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
   if ((rc = check_order_high(p->sh_order))) return rc;
-  if (p->sh_order > 3 && (p->flags & (PRTGS_BOUNCE | PRTGS_GLOSSY))) return PRTGS_ERR_UNSUPPORTED;
+  if (p->sh_order > 3 && (p->flags & PRTGS_GLOSSY)) return PRTGS_ERR_UNSUPPORTED;
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
   if (p->n_bounces < 0 || p->n_bounces > 64) return PRTGS_ERR_INVALID_ARG;

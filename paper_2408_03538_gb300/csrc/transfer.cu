@@ -1050,59 +1050,63 @@ __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
-  const int k = lane & 15, half = lane >> 4;
+  const int half = lane >> 4;
   const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
   const float wq = 4.0f * kPi / (float)S;
-  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-  for (int base = 0; base < S; base += 32) {
-    int s = base + lane;
-    int jl = s < S ? idx[i * S + s] : -1;
-    if (jl >= n) {
-      set_status(status, PRTGS_STATUS_BAD_INDEX);
-      jl = -1;
-    }
-    float cl = 0.f;
-    if (jl >= 0) cl = fmaxf(fmaf(nx, dirs[3 * s], fmaf(ny, dirs[3 * s + 1], nz * dirs[3 * s + 2])), 0.f);
+  // coefficients in chunks of 16 (one chunk up to order 3, up to four for order 6)
+  for (int kb = 0; kb < C; kb += 16) {
+    const int k = kb + (lane & 15);
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+    for (int base = 0; base < S; base += 32) {
+      int s = base + lane;
+      int jl = s < S ? idx[i * S + s] : -1;
+      if (jl >= n) {
+        set_status(status, PRTGS_STATUS_BAD_INDEX);
+        jl = -1;
+      }
+      float cl = 0.f;
+      if (jl >= 0) cl = fmaxf(fmaf(nx, dirs[3 * s], fmaf(ny, dirs[3 * s + 1], nz * dirs[3 * s + 2])), 0.f);
 #pragma unroll 4
-    for (int q = 0; q < 16; ++q) {
-      int src = 2 * q + half;
-      int j = __shfl_sync(0xffffffffu, jl, src);
-      float c = __shfl_sync(0xffffffffu, cl, src);
-      if (j < 0) continue;
-      const float coef = wq * c * (1.0f / kPi);
-      if (FROM_P) {
-        const float cp = coef * (k < C ? __ldg(P + (int64_t)j * C + k) : 0.f);
-        acc0 = fmaf(cp, __ldg(albedo + 3 * j), acc0);
-        acc1 = fmaf(cp, __ldg(albedo + 3 * j + 1), acc1);
-        acc2 = fmaf(cp, __ldg(albedo + 3 * j + 2), acc2);
-      } else if (k < C) {
-        const float* tj = Tprev + (int64_t)j * 3 * C + k;
-        acc0 = fmaf(coef * __ldg(albedo + 3 * j), __ldg(tj), acc0);
-        acc1 = fmaf(coef * __ldg(albedo + 3 * j + 1), __ldg(tj + C), acc1);
-        acc2 = fmaf(coef * __ldg(albedo + 3 * j + 2), __ldg(tj + 2 * C), acc2);
+      for (int q = 0; q < 16; ++q) {
+        int src = 2 * q + half;
+        int j = __shfl_sync(0xffffffffu, jl, src);
+        float c = __shfl_sync(0xffffffffu, cl, src);
+        if (j < 0) continue;
+        const float coef = wq * c * (1.0f / kPi);
+        if (FROM_P) {
+          const float cp = coef * (k < C ? __ldg(P + (int64_t)j * C + k) : 0.f);
+          acc0 = fmaf(cp, __ldg(albedo + 3 * j), acc0);
+          acc1 = fmaf(cp, __ldg(albedo + 3 * j + 1), acc1);
+          acc2 = fmaf(cp, __ldg(albedo + 3 * j + 2), acc2);
+        } else if (k < C) {
+          const float* tj = Tprev + (int64_t)j * 3 * C + k;
+          acc0 = fmaf(coef * __ldg(albedo + 3 * j), __ldg(tj), acc0);
+          acc1 = fmaf(coef * __ldg(albedo + 3 * j + 1), __ldg(tj + C), acc1);
+          acc2 = fmaf(coef * __ldg(albedo + 3 * j + 2), __ldg(tj + 2 * C), acc2);
+        }
       }
     }
-  }
-  acc0 += __shfl_xor_sync(0xffffffffu, acc0, 16);
-  acc1 += __shfl_xor_sync(0xffffffffu, acc1, 16);
-  acc2 += __shfl_xor_sync(0xffffffffu, acc2, 16);
-  if (half == 0 && k < C) {
-    float* t = T + i * 3 * C + k;
-    if (FROM_P) {
-      const float p = P[i * C + k];
-      t[0] = p + acc0;
-      t[C] = p + acc1;
-      t[2 * C] = p + acc2;
-    } else {
-      t[0] += acc0;
-      t[C] += acc1;
-      t[2 * C] += acc2;
-    }
-    if (Tcur) {
-      float* u = Tcur + i * 3 * C + k;
-      u[0] = acc0;
-      u[C] = acc1;
-      u[2 * C] = acc2;
+    acc0 += __shfl_xor_sync(0xffffffffu, acc0, 16);
+    acc1 += __shfl_xor_sync(0xffffffffu, acc1, 16);
+    acc2 += __shfl_xor_sync(0xffffffffu, acc2, 16);
+    if (half == 0 && k < C) {
+      float* t = T + i * 3 * C + k;
+      if (FROM_P) {
+        const float p = P[i * C + k];
+        t[0] = p + acc0;
+        t[C] = p + acc1;
+        t[2 * C] = p + acc2;
+      } else {
+        t[0] += acc0;
+        t[C] += acc1;
+        t[2 * C] += acc2;
+      }
+      if (Tcur) {
+        float* u = Tcur + i * 3 * C + k;
+        u[0] = acc0;
+        u[C] = acc1;
+        u[2 * C] = acc2;
+      }
     }
   }
 }

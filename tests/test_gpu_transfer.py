@@ -447,9 +447,27 @@ def test_high_order_rejects_what_it_does_not_cover():
     bvh = api.build_bvh(g)
     d = torch.from_numpy(S.direction_set(32, 1)).cuda()
     with pytest.raises(Exception):
-        api.precompute_transfer(g, bvh, d, 6, bounce=True)
+        api.precompute_transfer(g, bvh, d, 6, glossy=True)
     with pytest.raises(Exception):
         api.relight(torch.zeros((50, 49), device="cuda"), g.albedo, torch.zeros((1, 3, 49), device="cuda"), 6,
                     precision=1)
     with pytest.raises(Exception):
         api.precompute_transfer(g, bvh, d, 7)
+
+
+@pytest.mark.parametrize("nb", [1, 3])
+def test_high_order_bounce_matches_oracle(nb):
+    """Order 6 (49 coefficients) with the one- and three-bounce self-transfer against the
+    oracle (every receiver of a crowded scene)."""
+    sc = _crowded(300, 23)
+    dirs = S.direction_set(64, 9)
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    T = api.precompute_transfer(g, bvh, torch.from_numpy(dirs).cuda(), 6, bounce=True, n_bounces=nb,
+                                status=st)["T"].cpu().numpy()
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    tr = oracle.transfer(sc, dirs, 6, np.arange(sc.n), bounce=True)
+    Tref, allow = oracle.multi_bounce(sc, dirs, 6, tr, nb)
+    _check_norm(T, Tref, allow.max(axis=1), 1e-3 * oracle.unoccluded_norm(6))
