@@ -403,7 +403,7 @@ def run_kernels_small():
     render forward + backward of the 100k surface scene, and the transfer backward of the 20k
     scene; then every other kernel of the library once (shadow-only walk, glossy matrices,
     relight with RGB transfer and glossy rows, batched relight, loss, relight backward,
-    three-bounce self-transfer, pixel-space relight)."""
+    three-bounce self-transfer, pixel-space relight, depth/normal maps, SH order 6)."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -457,6 +457,10 @@ def run_kernels_small():
     for prec in (0, 1):
         api.render_relit(gg, outg["T"], L8, cam, 3, bg=bg, precision=prec, glossy_ids=gids, M=outg["M"],
                          max_pairs=4_000_000)
+    # depth and normal maps; SH order 6 transfer and relight
+    api.render_geometry(gg, cam, max_pairs=4_000_000)
+    P6 = api.precompute_transfer(gg, api.build_bvh(gg), dirs, 6)["P"]
+    api.relight(P6, gg.albedo, torch.randn((2, 3, 49), device="cuda", generator=gen), 6)
     torch.cuda.synchronize()
     print(json.dumps({"case": "kernels-small", "idx_max": int(out["idx"].max()),
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
