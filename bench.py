@@ -320,7 +320,8 @@ def run_ours(args):
         oracle.build()
         n_recv = calibrate_oracle(sc, dirs, order, 12.0)
         dt, rays, tr = oracle_sample(sc, dirs, order, n_recv, 999)
-        hits_per_ray = float(tr["hits"].sum() / max(1, ((tr["flags"] & 1) != 0).sum()))
+        # hits a ray takes before its transmittance falls below t_min (the algorithmic work)
+        hits_per_ray = float(tr["hits_live"].sum() / max(1, ((tr["flags"] & 1) != 0).sum()))
         cpu = {"value": rays / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{n_recv} seeded receivers x {S_} directions of {WORKLOAD} (shadow + index matrix, "
                          f"brute force over all {sc.n} Gaussians), {dt:.1f} s"}

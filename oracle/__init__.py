@@ -62,7 +62,7 @@ def _load():
         P = ctypes.c_void_p
         lib.oracle_sh.argtypes = [ctypes.c_int, ctypes.c_int64, P, P]
         lib.oracle_trace.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P, P]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, P, P, P]
         lib.oracle_morton_lbvh.argtypes = [ctypes.c_int64, P, ctypes.c_int, P, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -112,11 +112,11 @@ def trace(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = Fal
                        _f32(scene.normals))
     out = dict(P=np.zeros((R, C)), V=np.zeros((R, S)), idx=np.full((R, S), -1, np.int32),
                cand=np.full((R, S, 4), -1, np.int32), flags=np.zeros((R, S), np.int32), dV=np.zeros((R, S)),
-               hits=np.zeros(R))
+               hits=np.zeros(R), hits_live=np.zeros(R))
     rc = lib.oracle_trace(m.shape[0], _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(nrm), S, _ptr(dirs), order,
                           (1 if shadow else 0) | (2 if bounce else 0), float(filter_t), float(t_min), R, _ptr(recv),
                           _ptr(out["P"]), _ptr(out["V"]), _ptr(out["idx"]), _ptr(out["cand"]), _ptr(out["flags"]),
-                          _ptr(out["dV"]), _ptr(out["hits"]))
+                          _ptr(out["dV"]), _ptr(out["hits"]), _ptr(out["hits_live"]))
     if rc != 0:
         raise RuntimeError(f"oracle_trace failed: {rc}")
     return out
@@ -149,7 +149,7 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
     traced = (tr["flags"] & RF_TRACED) != 0
     allow_P = (w * c * ynorm[None, :] * (tr["dV"] + np.where(traced, t_min, 0.0))).sum(axis=1)
     res = dict(P=tr["P"], allow_P=allow_P, V=tr["V"], dV=tr["dV"], idx=tr["idx"], flags=tr["flags"],
-               hits=tr["hits"], traced=traced.sum(axis=1))
+               hits=tr["hits"], hits_live=tr["hits_live"], traced=traced.sum(axis=1))
     if not bounce:
         return res
     # receivers whose P is needed: every index-matrix entry, plus the alternatives of flagged rays

@@ -188,11 +188,14 @@ static int hit_cmp(const void* pa, const void* pb) {
  *   ray_flags[n_recv, S] RF_* bits
  *   dV[n_recv, S]        bound on |V_gpu - V| from ambiguous occluders (no early exit here)
  *   hits[n_recv]         number of (ray, occluder) intersections over the receiver's traced rays
+ *   hits_live[n_recv]    the same, counting each ray's hits in t order only until its
+ *                        transmittance first falls below t_min (that hit included): the hits a
+ *                        walk with the visibility cut-off must take (nullable)
  */
 int oracle_trace(int64_t n, const float* means, const float* scales, const float* quats, const float* opacity,
                  const float* normals, int S, const float* dirs, int order, int flags, double filter_t,
                  double t_min, int64_t n_recv, const int64_t* recv, double* P, double* V, int32_t* idx, int32_t* cand,
-                 int32_t* ray_flags, double* dV, double* hits) {
+                 int32_t* ray_flags, double* dV, double* hits, double* hits_live) {
   if (order < 0 || order > ORACLE_MAX_ORDER) return -3;
   const int C = (order + 1) * (order + 1);
   const double w = 4.0 * M_PI / (double)S;
@@ -212,7 +215,7 @@ int oracle_trace(int64_t n, const float* means, const float* scales, const float
     if (!hl) { err = -5; continue; }
     double Pacc[ORACLE_MAX_C];
     for (int k = 0; k < C; ++k) Pacc[k] = 0;
-    double hit_total = 0;
+    double hit_total = 0, live_total = 0;
     const OG* gi = &g[i];
     for (int s = 0; s < S; ++s) {
       double d[3] = {dirs[3 * s], dirs[3 * s + 1], dirs[3 * s + 2]};
@@ -265,6 +268,16 @@ int oracle_trace(int64_t n, const float* means, const float* scales, const float
       }
       V[rs] = vis;
       for (int k = 0; k < C; ++k) Pacc[k] += w * vis * c * Ys[(size_t)s * C + k];
+      if (hits_live && nh > 0) {
+        qsort(hl, (size_t)nh, sizeof(Hit), hit_cmp);
+        double tl = 1.0;
+        for (int q = 0; q < nh; ++q) {
+          if (hl[q].ambiguous == 2) continue;
+          live_total += 1.0;
+          tl *= 1.0 - hl[q].alpha;
+          if (tl < t_min) break;
+        }
+      }
 
       if ((flags & 2) && nh > 0) {
         qsort(hl, (size_t)nh, sizeof(Hit), hit_cmp);
@@ -317,6 +330,7 @@ int oracle_trace(int64_t n, const float* means, const float* scales, const float
     }
     for (int k = 0; k < C; ++k) P[(size_t)r * C + k] = Pacc[k];
     if (hits) hits[r] = hit_total;
+    if (hits_live) hits_live[r] = live_total;
     free(hl);
   }
   free(g);
