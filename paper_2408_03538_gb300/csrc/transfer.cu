@@ -302,7 +302,7 @@ struct QueueRec {
   int self;
   int s;
   float t_hor;
-  int pad;
+  float amax;  // largest alpha_j max(-d.n_j, 0) of the ray's front-facing hits within the horizon
   FrontBuf<KB> fb;
 };
 
@@ -323,10 +323,10 @@ struct ShadowFrontVis {
   float T;
   float t_seen;
   float t_hor;
+  float amax;
   FrontBuf<KB> fb;
-  __device__ float t_hi() const {
-    return T < a.t_min ? fminf(slack_hi(t_hor), slack_hi(fb.t_full())) : FLT_MAX;
-  }
+  // pruned to the horizon only, so that amax covers every front-facing hit within it
+  __device__ float t_hi() const { return T < a.t_min ? slack_hi(t_hor) : FLT_MAX; }
   __device__ bool stop() const { return false; }
   __device__ void leaf(int pos) {
     if (pos == self) return;
@@ -341,7 +341,10 @@ struct ShadowFrontVis {
     } else if (t > t_hor) {
       return;
     }
-    if (m > 0.f) fb.insert(t, pos, al, m);
+    if (m > 0.f) {
+      fb.insert(t, pos, al, m);
+      amax = fmaxf(amax, al * m);
+    }
   }
 };
 
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
       float V = 1.0f;
       if (a.flags & PRTGS_SHADOW) {
         if (BOUNCE) {
-          ShadowFrontVis<KB> sv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX};
+          ShadowFrontVis<KB> sv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, 0.0f};
           sv.fb.clear();
           traverse(a, r, root, 0.0f, sv, rs, rs.nodes);
           V = sv.T;
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(kTraceThreads, BOUNCE ? kBounceMinBlocks : kSh
             q->self = self;
             q->s = s;
             q->t_hor = sv.t_hor;
-            q->pad = 0;
+            q->amax = sv.amax;
             q->fb = sv.fb;
             a.pending[slot] = 1;
           }
@@ -581,6 +584,7 @@ struct RoundRec {
   float lt_base;
   int best;
   float lw_best;
+  float lamax;  // log of the largest alpha m among the ray's front-facing hits (W_j <= amax T_j)
 };
 
 // First index-matrix round of the listed rays (one thread per ray): the prefix walk for the
@@ -634,15 +638,16 @@ __global__ void __launch_bounds__(128, kPrefixMinBlocks) k_prefix(TraceArgs a, c
     }
     bool settled = nc < KB;
     float lt_next = 0.f;
+    const float lamax = logf(rec.amax);  // every later candidate has W_j <= amax T_j
     if (!settled) {
       lt_next = pb.lt[KB - 1] + log1pf(-rec.fb.ba[KB - 1]);
-      settled = lt_next <= lw_best || lt_next < lmin;
+      settled = lt_next + lamax <= lw_best || lt_next < lmin;
     }
     if (settled) {
       a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
     } else {
       const unsigned m = atomicAdd(more_count, 1u);
-      more[m] = RoundRec{self, s, rec.t_hor, fb.bt[KB - 1], fb.bp[KB - 1], lt_next, best, lw_best};
+      more[m] = RoundRec{self, s, rec.t_hor, fb.bt[KB - 1], fb.bp[KB - 1], lt_next, best, lw_best, lamax};
       ++n_more;
     }
   }
@@ -686,7 +691,7 @@ struct AllHitsVis {
 
 template <int KR>
 __device__ int index_search_all(const TraceArgs& a, const Ray& r, int root, int self, RayStats& st, float t_hor,
-                                float t_last, int p_last, float lt, int best, float lw_best) {
+                                float t_last, int p_last, float lt, int best, float lw_best, float lamax) {
   const float lfilter = logf(a.filter_t);
   const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
   for (int64_t round = 0;; ++round) {
@@ -694,7 +699,7 @@ __device__ int index_search_all(const TraceArgs& a, const Ray& r, int root, int 
       set_status(a.status, PRTGS_STATUS_BAD_INDEX);
       break;
     }
-    if (lt < lmin || lt <= lw_best) break;  // nothing past this point can be a better candidate
+    if (lt < lmin || lt + lamax <= lw_best) break;  // later W_j <= amax T_j: none can do better
     ++st.rounds;
     AllHitsVis<KR> v{a, r, self, st, t_last, p_last, t_hor};
     v.fb.clear();
@@ -704,7 +709,7 @@ __device__ int index_search_all(const TraceArgs& a, const Ray& r, int root, int 
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
       if (k < nh && !decided) {
-        if (lt < lmin || lt <= lw_best) {
+        if (lt < lmin || lt + lamax <= lw_best) {
           decided = true;
         } else {
           if (v.fb.bm[k] > 0.f && lt <= lfilter) {
@@ -745,7 +750,7 @@ __global__ void __launch_bounds__(128, kRoundsMinBlocks) k_rounds(TraceArgs a, c
     Ray r;
     make_ray(r, q0.x, q0.y, q0.z, __ldg(a.dirs + 3 * s), __ldg(a.dirs + 3 * s + 1), __ldg(a.dirs + 3 * s + 2));
     const int best = index_search_all<kRoundHits>(a, r, root, self, rs, rec.t_hor, rec.t_last, rec.p_last,
-                                                  rec.lt_base, rec.best, rec.lw_best);
+                                                  rec.lt_base, rec.best, rec.lw_best, rec.lamax);
     a.idx[(int64_t)gid * a.S + s] = best >= 0 ? a.order[best] : -1;
   }
   if (a.stats) {
