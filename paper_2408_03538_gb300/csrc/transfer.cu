@@ -277,7 +277,9 @@ struct FrontBuf {
     }
   }
   __device__ float t_full() const { return bt[KB - 1]; }
-  __device__ void insert(float t, int p, float al, float m) {
+  // Returns alpha * m of the entry that falls out (the new one if it is past the last slot;
+  // 0 while the buffer is not full).
+  __device__ float insert(float t, int p, float al, float m) {
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
       if (key_less(t, p, bt[k], bp[k])) {
@@ -287,6 +289,7 @@ struct FrontBuf {
         float mm = bm[k]; bm[k] = m; m = mm;
       }
     }
+    return al * m;
   }
   __device__ int count() const {
     int nc = 0;
@@ -302,7 +305,7 @@ struct QueueRec {
   int self;
   int s;
   float t_hor;
-  float amax;  // largest alpha_j max(-d.n_j, 0) of the ray's front-facing hits within the horizon
+  float amax;  // largest alpha_j max(-d.n_j, 0) of the front-facing hits past the KB in fb
   FrontBuf<KB> fb;
 };
 
@@ -312,8 +315,9 @@ __device__ __forceinline__ float slack_hi(float t) { return t == FLT_MAX ? FLT_M
 // any order, as ShadowVis) and keeps the KB nearest front-facing hits. At the cut-off it
 // records the horizon: the largest t* met so far; every hit past it has a prefix
 // transmittance below t_min, so it is no index-matrix candidate. The same walk then goes on,
-// pruned to the horizon (and to the KB-th candidate), so that the buffer ends up holding the
-// KB nearest front-facing hits of the whole ray within the horizon.
+// pruned to the horizon, so that the buffer ends up holding the KB nearest front-facing hits
+// of the whole ray within the horizon and amax bounds alpha m of every one past them: a later
+// candidate j has W_j <= amax T_j, which ends the search once the prefix drops below the best.
 template <int KB>
 struct ShadowFrontVis {
   const TraceArgs& a;
@@ -325,7 +329,8 @@ struct ShadowFrontVis {
   float t_hor;
   float amax;
   FrontBuf<KB> fb;
-  // pruned to the horizon only, so that amax covers every front-facing hit within it
+  // pruned to the horizon only, so that amax covers every front-facing hit within it that
+  // is not among the KB nearest (the candidates of the later rounds)
   __device__ float t_hi() const { return T < a.t_min ? slack_hi(t_hor) : FLT_MAX; }
   __device__ bool stop() const { return false; }
   __device__ void leaf(int pos) {
@@ -341,10 +346,7 @@ struct ShadowFrontVis {
     } else if (t > t_hor) {
       return;
     }
-    if (m > 0.f) {
-      fb.insert(t, pos, al, m);
-      amax = fmaxf(amax, al * m);
-    }
+    if (m > 0.f) amax = fmaxf(amax, fb.insert(t, pos, al, m));
   }
 };
 
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(128, kPrefixMinBlocks) k_prefix(TraceArgs a, c
     }
     bool settled = nc < KB;
     float lt_next = 0.f;
-    const float lamax = logf(rec.amax);  // every later candidate has W_j <= amax T_j
+    const float lamax = logf(rec.amax);  // every candidate past the KB has W_j <= amax T_j
     if (!settled) {
       lt_next = pb.lt[KB - 1] + log1pf(-rec.fb.ba[KB - 1]);
       settled = lt_next + lamax <= lw_best || lt_next < lmin;
