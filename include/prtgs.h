@@ -168,7 +168,7 @@ typedef struct prtgs_transfer_params {
 size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);
 
 /*
- * Per-Gaussian radiance transfer (Eq. 29, Eq. 33, Eq. 40).
+ * Per-Gaussian radiance transfer (Eq. 29, Eq. 33-35, Eq. 40).
  *  P[n,C]        out: P_i = sum_s (4 pi/S) V_is max(0, n_i.w_s) Y(w_s), with
  *                V_is = prod over the other Gaussians j hit by the ray from mu_i along w_s
  *                of (1 - opacity_j exp(-D_ij^2/2)); a hit is t* > 0 and D^2 <= 9, with t*
@@ -176,14 +176,17 @@ size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_tr
  *                (Eq. 27 read as the Gaussian's maximum along the ray). Albedo and 1/pi are
  *                applied at relight time.
  *  T[n,3,C]      out (PRTGS_BOUNCE, else unused): T_i = P_i + sum_s (4 pi/S) max(0, n_i.w_s)
- *                (albedo_j/pi) P_j, j = idx[i,s] (Eq. 33, one bounce).
+ *                (albedo_j/pi) P_j, j = idx[i,s] (Eq. 33, one bounce); with p->n_bounces > 1
+ *                the further bounces of Eq. 34-35 are added (see prtgs_transfer_params).
  *  idx[n,S]      out (required with PRTGS_BOUNCE, else unused): index matrix of Sec. 4.4:
  *                the hit with the largest W_j = alpha_j prod_{before j}(1-alpha) max(0,-w.n_j)
  *                (Eq. 26), -1 when no eligible hit has W > 0 or n_i.w_s <= 0.
  *  M[n_glossy,C,C] out (PRTGS_GLOSSY): glossy transfer matrices (Eq. 40), in increasing
  *                Gaussian order of the glossy splats:
  *                M[a,b] = sum_s sum_o (4 pi/S)^2 Y_a(w_s) k(w_s,w_o) max(0,n.w_s) V_s Y_b(w_o),
- *                k = (1-metallic) + pi D F G / (4 (n.w_s)(n.w_o)), zero for n.w_o <= 0.
+ *                k = (1-metallic) + pi D F G / (4 (n.w_s)(n.w_o)), zero for n.w_o <= 0, with
+ *                the unit normal n/|n| in D, F, G (GGX with alpha = roughness^2, Schlick with
+ *                F0 = 0.04, Smith-Schlick with k = alpha/2).
  *  status        device int32 word for PRTGS_STATUS_* bits (may be NULL).
  * A BVH built from the same Gaussian arrays must be passed.
  */
