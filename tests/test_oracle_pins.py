@@ -606,3 +606,48 @@ def test_multi_bounce_converges_to_the_resolvent(oracle_mod):
                     W[i, idx[i, s_]] += w * cosw[i, s_] * sc.albedo[idx[i, s_], ch] / math.pi
         assert np.max(np.abs(np.linalg.eigvals(W))) < 0.7
         np.testing.assert_allclose(T[:, ch, :], np.linalg.solve(np.eye(N) - W, P), rtol=1e-10, atol=1e-10)
+
+
+def test_live_hits_stop_at_the_visibility_cut_off(oracle_mod):
+    """A ray straight up through a column of m identical occluders hit at their centres
+    (alpha = opacity each) takes min(m, q) hits before its transmittance falls below t_min,
+    q the first count with (1 - alpha)^q < t_min; all m hits are counted otherwise."""
+    m, op = 40, 0.6
+    means = [[0, 0, 0]] + [[0, 0, 1.0 + k] for k in range(m)]
+    sc = _sc(means, np.full((m + 1, 3), 0.05), [0.5] + [op] * m, np.tile([0, 0, 1.0], (m + 1, 1)))
+    dirs = np.array([[0, 0, 1.0]], np.float32)
+    for t_min, expect in ((2.0 ** -30, int(np.ceil(np.log(2.0 ** -30) / np.log(1 - op)))), (0.0, m)):
+        tr = oracle_mod.trace(sc, dirs, 1, [0], t_min=t_min)
+        assert tr["hits"][0] == m
+        assert tr["hits_live"][0] == min(m, expect), (t_min, tr["hits_live"][0])
+    assert int(np.ceil(np.log(2.0 ** -30) / np.log(1 - op))) < m  # the cut-off is inside the column
+
+
+def test_multi_bounce_allowance_covers_switching_a_flagged_ray(oracle_mod):
+    """For a ray flagged rounding-ambiguous, taking any of its other candidates changes the
+    n-bounce T by no more than the carried allowance."""
+    rng = np.random.default_rng(11)
+    N, Sd, C = 12, 8, 4
+    dirs = S.direction_set(Sd, 3)
+    normals = rng.standard_normal((N, 3))
+    normals /= np.linalg.norm(normals, axis=1, keepdims=True)
+    sc = _TwoSplats(normals, rng.uniform(0.1, 0.9, (N, 3)))
+    idx = rng.integers(-2, N, (N, Sd))
+    idx[idx < 0] = -1
+    flags = np.zeros((N, Sd), np.int32)
+    cand = -np.ones((N, Sd, 4), np.int64)
+    amb = [(0, 1), (3, 2), (5, 0)]
+    for i, s_ in amb:
+        flags[i, s_] = oracle_mod.RF_AMBIG_ARGMAX
+        cand[i, s_, :3] = rng.integers(0, N, 3)
+    P = rng.standard_normal((N, C))
+    tr = dict(P=P, allow_P=np.zeros(N), idx=idx, flags=flags, cand=cand)
+    for nb in (1, 3):
+        T, allow = oracle_mod.multi_bounce(sc, dirs, 1, tr, nb)
+        for i, s_ in amb:
+            for alt in list(cand[i, s_, :3]) + [-1]:
+                idx2 = idx.copy()
+                idx2[i, s_] = alt
+                T2, _ = oracle_mod.multi_bounce(sc, dirs, 1, dict(tr, idx=idx2, flags=np.zeros_like(flags)), nb)
+                # a single switch moves receiver i directly and, through later bounces, others
+                assert np.all(np.linalg.norm(T2 - T, axis=2)[i] <= allow[i] + 1e-12), (nb, i, alt)
