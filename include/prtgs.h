@@ -17,10 +17,13 @@
  *    (arguments, shapes, workspace size, CUDA launch errors). Errors detected on the device
  *    (non-finite inputs, traversal stack overflow, buffer capacity) are OR-ed as bit flags
  *    into a caller-provided int32 device status word, read after synchronisation with
- *    prtgs_read_status(). No kernel traps, asserts or waits without a bound.
+ *    prtgs_read_status(). No kernel traps, asserts or waits without a bound: the one device
+ *    wait, for the tensor cores' completion in the tcgen05 relight paths, gives up after a
+ *    bounded number of polls and then writes NaN to that tile's outputs instead of results.
  *
  * Notation follows the paper: N Gaussians, S sphere directions, C = (order+1)^2 real SH
- * coefficients (order <= 3, so C <= 16), k lights, H x W image.
+ * coefficients (order <= 3, so C <= 16, for every path; orders 4-6, C <= 49, where a call says
+ * so), k lights, H x W image.
  */
 #ifndef PRTGS_H
 #define PRTGS_H
