@@ -101,7 +101,6 @@ def test_unoccluded_transfer_is_clamped_cosine(oracle_mod, order):
 
 
 def test_clamped_cosine_constants():
-    A = [S for S in (0,)]  # noqa: F841 (placeholder for flake)
     import oracle
 
     assert oracle.clamped_cosine_A(0) == pytest.approx(math.pi)
