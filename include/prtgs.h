@@ -150,10 +150,14 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *                   T^k_i = sum_s w (n_i.w_s)^+ (rho_j/pi) T^{k-1}_j over the index matrix, T^0 = P;
  *                   0 or 1 = one bounce (Eq. 33), at most 64; more than one needs 3nC floats of
  *                   workspace per extra buffer (two at most)
- *   stats           optional device uint64[8] that the call ADDS its work counters to:
+ *   walk            tuning: 0 = warp packets (default: the rays that 32 receivers adjacent in
+ *                   Morton order cast along one direction walk the BVH together), 1 = one ray
+ *                   per lane (the plain per-ray walk); both give the same results
+ *   stats           optional device uint64[10] that the call ADDS its work counters to:
  *                   BVH node visits of the visibility walks, node visits of the index-matrix
  *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays, rays
- *                   queued for the first index-matrix round, rays that needed later rounds
+ *                   queued for the first index-matrix round, rays that needed later rounds,
+ *                   warp-packet walks, leaves a packet evaluated for at least one of its rays
  *                   (NULL = not gathered)
  */
 typedef struct prtgs_transfer_params {
@@ -166,6 +170,7 @@ typedef struct prtgs_transfer_params {
   int32_t index_buffer;
   unsigned long long* stats;
   int32_t n_bounces;
+  int32_t walk;
 } prtgs_transfer_params;
 
 size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);

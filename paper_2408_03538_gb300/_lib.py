@@ -36,7 +36,7 @@ class BVH(ctypes.Structure):
 class TransferParams(ctypes.Structure):
     _fields_ = [("sh_order", c_int32), ("n_dirs", c_int32), ("dirs", c_void_p), ("t_min", c_float),
                 ("same_surface_t", c_float), ("flags", c_uint32), ("index_buffer", c_int32), ("stats", c_void_p),
-                ("n_bounces", c_int32)]
+                ("n_bounces", c_int32), ("walk", c_int32)]
 
 
 class Camera(ctypes.Structure):

@@ -133,10 +133,12 @@ def build_bvh(g: GaussianTensors, scene_offsets: torch.Tensor | None = None, sta
 def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int, shadow: bool = True,
                         bounce: bool = False, glossy: bool = False, t_min: float = DEFAULT_T_MIN,
                         same_surface_t: float = 1.0, status: Status | None = None, out: dict | None = None,
-                        stats: torch.Tensor | None = None, index_buffer: int = 0, n_bounces: int = 1):
+                        stats: torch.Tensor | None = None, index_buffer: int = 0, n_bounces: int = 1,
+                        walk: int = 0):
     """Transfer vectors P [n,C], and with ``bounce`` T [n,3,C] (``n_bounces`` self-transfer
     bounces over the index matrix) and idx [n,S]; with ``glossy`` the C x C matrices
-    M [n_glossy,C,C] of the glossy splats (in increasing index order)."""
+    M [n_glossy,C,C] of the glossy splats (in increasing index order). ``walk``: 0 = warp
+    packets of parallel rays (default), 1 = one ray per lane; the results are the same."""
     lib = L.load()
     dev = g.means.device
     S = int(dirs.shape[0])
@@ -152,7 +154,7 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
     if glossy:
         M = torch.empty((max(n_glossy, 1), C, C), dtype=torch.float32, device=dev)
     p = L.TransferParams(order, S, _ptr(dirs), float(t_min), float(same_surface_t), flags, int(index_buffer),
-                         _ptr(stats), int(n_bounces))
+                         _ptr(stats), int(n_bounces), int(walk))
     ws, nb = _ws(lib.prtgs_transfer_workspace_size(g.n, n_glossy, ctypes.byref(p)), dev)
     gs = g.struct()
     L.check(lib.prtgs_precompute_transfer(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(P), _ptr(T),

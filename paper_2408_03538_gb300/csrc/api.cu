@@ -122,6 +122,7 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
   if (p->n_bounces < 0 || p->n_bounces > 64) return PRTGS_ERR_INVALID_ARG;
+  if (p->walk < 0 || p->walk > 1) return PRTGS_ERR_INVALID_ARG;
   if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
   if (g->n == 0) return PRTGS_OK;
   if (!P || !g->normals) return PRTGS_ERR_INVALID_ARG;

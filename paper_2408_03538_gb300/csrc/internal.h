@@ -30,6 +30,10 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
                         float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
                         cudaStream_t stream);
 
+struct TraceArgs;
+// packet.cu
+int launch_packet(const TraceArgs& a, float* V, bool bounce, int sms, cudaStream_t stream);
+
 size_t transfer_backward_workspace(int64_t n, const prtgs_transfer_params* p);
 int precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
                                  const float* dP, float* d_means, float* d_scales, float* d_quats, float* d_opacity,

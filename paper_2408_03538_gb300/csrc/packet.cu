@@ -1,0 +1,599 @@
+// Warp-packet traversal of the transfer rays (Sec. 4.4-4.5).
+//
+// Every receiver traces the same S world-space directions, so the rays that 32 receivers
+// adjacent in Morton order cast along one direction are parallel and start from a small patch
+// of the scene. One warp takes such a packet: the lanes walk the LBVH together, testing up to
+// 32 nodes per step against the packet's beam (the rectangle the packet's origins span in the
+// plane orthogonal to the direction, and the depth range along it that the lanes still need),
+// and collect the leaves the beam meets in a shared-memory chunk. Each leaf of a chunk is then
+// tested by every lane whose own ray can meet its box, with the same per-ray hit test and the
+// same visitors as the per-ray walks in transfer.cu, so every hit decision, product and
+// index-matrix rule is that of a single ray; only the traversal is shared.
+//
+//  k_packet<B>    visibility V_is of every (receiver, direction) of a receiver batch into
+//                 V[s][i] (Eq. 4 along a ray, Eq. 27 read as the Gaussian's maximum); with B
+//                 (bounce) also the index matrix of Sec. 4.4: the visibility walk finds the
+//                 horizon and the nearest front-facing hit, then search rounds walk the hits
+//                 from there in key order until the argmax of W_j (Eq. 26) is settled.
+//  k_project      P_i = sum_s (4 pi / S) V_is max(0, n_i.w_s) Y(w_s) (Eq. 29 with Eq. 9),
+//                 one lane per receiver, compensated sums; also copies V of glossy receivers.
+#include "trace.cuh"
+
+namespace prtgs {
+
+constexpr int kPacketWarps = 4;
+constexpr int kPacketThreads = 32 * kPacketWarps;
+constexpr int kPStack = 384;     // node stack of a warp (ints)
+#ifndef PRTGS_PACKET_ROUND_HITS
+#define PRTGS_PACKET_ROUND_HITS 16
+#endif
+constexpr int kPacketRoundHits = PRTGS_PACKET_ROUND_HITS;  // hits per index-matrix search round
+#ifndef PRTGS_PACKET_LEAVES
+#define PRTGS_PACKET_LEAVES 128
+#endif
+#ifndef PRTGS_PACKET_MIN_BLOCKS
+#define PRTGS_PACKET_MIN_BLOCKS 1
+#endif
+constexpr int kPLeaves = PRTGS_PACKET_LEAVES;  // leaf chunk of a warp (> 64)
+// wide pops (32 nodes) only while the stack keeps room for their pushes plus a full one-node-
+// at-a-time descent of the deepest possible tree (64 levels)
+constexpr int kPHeadroom = 64 + 64 + 4;
+constexpr int kPacketDirs = 16;  // directions per work item (fewer for small batches)
+
+struct PacketSmem {
+  int stack[kPStack];
+  float4 la[kPLeaves];     // leaf box lo xyz, sorted position
+  float4 lb[kPLeaves];     // leaf box hi xyz, unused
+  float4 stage[32][5];     // a group of leaves, staged: q0, q1, q2, (a22, A d), (1/|A d|^2, sqrt, m, pos)
+};
+// Bounce mode, per warp after the PacketSmem array: the search round's nearest hits of each lane,
+// hits[k][lane] = (t*, position, alpha, m).
+using RoundHits = float4[kPacketRoundHits][32];
+
+// Orthonormal frame (e1, e2, w) around a unit direction w (Duff et al. 2017, "Building an
+// orthonormal basis, revisited": the branchless form).
+struct Frame {
+  float e1x, e1y, e1z, e2x, e2y, e2z, wx, wy, wz;
+};
+
+__device__ __forceinline__ Frame make_frame(float x, float y, float z) {
+  const float sgn = copysignf(1.0f, z);
+  const float a = -1.0f / (sgn + z);
+  const float b = x * y * a;
+  Frame f;
+  f.e1x = 1.0f + sgn * x * x * a;
+  f.e1y = sgn * b;
+  f.e1z = -sgn * x;
+  f.e2x = b;
+  f.e2y = sgn + y * y * a;
+  f.e2z = -y;
+  f.wx = x;
+  f.wy = y;
+  f.wz = z;
+  return f;
+}
+
+// The packet's beam: the projected origins' rectangle and the depth range along w that the
+// lanes still need.
+struct Beam {
+  float xlo, xhi, ylo, yhi, zlo, zhi;
+};
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__device__ __forceinline__ Beam make_beam(bool need, float xl, float yl, float zlo, float zhi) {
+  Beam b;
+  b.xlo = warp_min(need ? xl : FLT_MAX);
+  b.xhi = warp_max(need ? xl : -FLT_MAX);
+  b.ylo = warp_min(need ? yl : FLT_MAX);
+  b.yhi = warp_max(need ? yl : -FLT_MAX);
+  b.zlo = warp_min(need ? zlo : FLT_MAX);
+  b.zhi = warp_max(need ? zhi : -FLT_MAX);
+  return b;
+}
+
+// Projection of a box [lo, hi] on the frame: centre and half-width along e1, e2 and w, widened
+// by a margin above the FP32 error of these sums and of a ray's drift off its projected origin
+// (|w.e1| of a few ulp times the distance travelled). Any point of the box -- in particular the
+// closest approach of a ray that hits a Gaussian inside it -- projects inside these intervals.
+__device__ __forceinline__ void project_box(const Frame& f, float lx, float ly, float lz, float hx, float hy,
+                                            float hz, float4& A, float2& Z) {
+  const float cx = 0.5f * (lx + hx), cy = 0.5f * (ly + hy), cz = 0.5f * (lz + hz);
+  const float hxx = 0.5f * (hx - lx), hyy = 0.5f * (hy - ly), hzz = 0.5f * (hz - lz);
+  const float px = f.e1x * cx + f.e1y * cy + f.e1z * cz;
+  const float py = f.e2x * cx + f.e2y * cy + f.e2z * cz;
+  const float pz = f.wx * cx + f.wy * cy + f.wz * cz;
+  const float rx = fabsf(f.e1x) * hxx + fabsf(f.e1y) * hyy + fabsf(f.e1z) * hzz;
+  const float ry = fabsf(f.e2x) * hxx + fabsf(f.e2y) * hyy + fabsf(f.e2z) * hzz;
+  const float rz = fabsf(f.wx) * hxx + fabsf(f.wy) * hyy + fabsf(f.wz) * hzz;
+  const float m = 3e-5f * (1.0f + fabsf(cx) + fabsf(cy) + fabsf(cz) + hxx + hyy + hzz);
+  A = make_float4(px, py, rx + m, ry + m);
+  Z = make_float2(pz - rz - m, pz + rz + m);
+}
+
+__device__ __forceinline__ bool beam_meets(const Beam& b, const float4& A, const float2& Z) {
+  return A.x + A.z >= b.xlo && A.x - A.z <= b.xhi && A.y + A.w >= b.ylo && A.y - A.w <= b.yhi && Z.y >= b.zlo &&
+         Z.x <= b.zhi;
+}
+
+// One packet walk. Lane state: `active` (this lane's ray takes part), its projected origin
+// (xl, yl) and depth zl, the lower bound t_lo of the hits it wants (0: all hits ahead) and its
+// visitor, whose t_hi() bounds the hits it still wants and stop() ends its ray. The leaves of a
+// chunk are staged 32 at a time (one record load and one set of direction terms per lane), then
+// each lane whose ray meets a leaf's box (the slab test of the per-ray walk) evaluates the hit and
+// hands it to vis.hit(), in chunk order.
+template <class Vis>
+__device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, int self, int root, bool active,
+                            float xl, float yl, float zl, float t_lo, Vis& vis, PacketSmem& sm, RayStats& st,
+                            unsigned& node_count) {
+  const int lane = threadIdx.x & 31;
+  const float prune_lo = t_lo > 0.f ? t_lo * (1.0f - 1e-5f) - 1e-6f : -FLT_MAX;
+  const unsigned above = lane == 31 ? 0u : (0xffffffffu << (lane + 1));  // lanes > lane
+  const unsigned below = (1u << lane) - 1u;                                // lanes < lane
+  const float zlo_l = t_lo > 0.f ? zl + (t_lo * (1.0f - 1e-5f) - 1e-6f) : zl;
+  bool need = active && !vis.stop();
+  if (!__any_sync(0xffffffffu, need) || root == INT32_MIN) return;
+  if (root < 0) {  // a one-Gaussian scene
+    if (need) vis.leaf(~root);
+    return;
+  }
+  float th = vis.t_hi();
+  Beam bm = make_beam(need, xl, yl, zlo_l, th == FLT_MAX ? FLT_MAX : zl + th);
+  int sp = 1, nl = 0;
+  if (lane == 0) sm.stack[0] = root;
+  __syncwarp();
+  const int64_t max_steps = 4 * a.n + 64;
+  for (int64_t step = 0;; ++step) {
+    if (step > max_steps) {
+      set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+      break;
+    }
+    if (sp > 0) {
+      const int npop = sp + kPHeadroom <= kPStack ? min(32, sp) : 1;
+      int node = -1;
+      if (lane < npop) node = sm.stack[sp - 1 - lane];
+      sp -= npop;
+      if (lane == 0) node_count += npop;
+      bool push0 = false, push1 = false, leaf0 = false, leaf1 = false;
+      int c0 = 0, c1 = 0;
+      float4 A0, A1;
+      float2 Z0, Z1;
+      float4 bx0, bx1;  // child boxes: lo xyz + hi x
+      float2 by0, by1;  //              hi y, hi z
+      bool near0 = true;
+      if (node >= 0) {
+        float4 n0, n1, n2;
+        load_node(a.nodes, node, n0, n1, n2, c0, c1);
+        bx0 = n0;
+        by0 = make_float2(n1.x, n1.y);
+        bx1 = make_float4(n1.z, n1.w, n2.x, n2.y);
+        by1 = make_float2(n2.z, n2.w);
+        project_box(f, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, A0, Z0);
+        project_box(f, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, A1, Z1);
+        const bool h0 = beam_meets(bm, A0, Z0) && child_ok(c0, a.n, a.status);
+        const bool h1 = beam_meets(bm, A1, Z1) && child_ok(c1, a.n, a.status);
+        push0 = h0 && c0 >= 0;
+        push1 = h1 && c1 >= 0;
+        leaf0 = h0 && c0 < 0;
+        leaf1 = h1 && c1 < 0;
+        near0 = Z0.x + Z0.y <= Z1.x + Z1.y;  // nearer box centre along w
+      }
+      // pushes: far child first, near child on top; lane 0's pushes end on top of the stack
+      const int np = (int)push0 + (int)push1;
+      const unsigned b1 = __ballot_sync(0xffffffffu, np >= 1), b2 = __ballot_sync(0xffffffffu, np == 2);
+      int pos = sp + __popc(b1 & above) + __popc(b2 & above);
+      if (pos + np > kPStack) {  // only a malformed tree gets here: report, drop the pushes
+        set_status(a.status, PRTGS_STATUS_STACK_OVERFLOW);
+      } else if (np == 2) {
+        sm.stack[pos] = near0 ? c1 : c0;
+        sm.stack[pos + 1] = near0 ? c0 : c1;
+      } else if (np == 1) {
+        sm.stack[pos] = push0 ? c0 : c1;
+      }
+      sp = min(sp + __popc(b1) + __popc(b2), kPStack);
+      // leaves: appended to the chunk (their boxes; each lane tests its own ray against them)
+      const int nlf = (int)leaf0 + (int)leaf1;
+      const unsigned l1 = __ballot_sync(0xffffffffu, nlf >= 1), l2 = __ballot_sync(0xffffffffu, nlf == 2);
+      int lp = nl + __popc(l1 & below) + __popc(l2 & below);
+      if (leaf0) {
+        sm.la[lp] = make_float4(bx0.x, bx0.y, bx0.z, __int_as_float(~c0));
+        sm.lb[lp] = make_float4(bx0.w, by0.x, by0.y, 0.f);
+        ++lp;
+      }
+      if (leaf1) {
+        sm.la[lp] = make_float4(bx1.x, bx1.y, bx1.z, __int_as_float(~c1));
+        sm.lb[lp] = make_float4(bx1.w, by1.x, by1.y, 0.f);
+      }
+      nl += __popc(l1) + __popc(l2);
+      __syncwarp();
+    }
+    if (nl > kPLeaves - 64 || (sp == 0 && nl > 0)) {
+      for (int g = 0; g < nl; g += 32) {
+        // stage: lane j loads the record of leaf g + j and its direction terms
+        if (g + lane < nl) {
+          const int pos = __float_as_int(sm.la[g + lane].w);
+          const float4 q0 = __ldg(a.recs + 4 * pos), q1 = __ldg(a.recs + 4 * pos + 1),
+                       q2 = __ldg(a.recs + 4 * pos + 2), q3 = __ldg(a.recs + 4 * pos + 3);
+          const DirTerms dt = dir_terms(q1, q2, q3, f.wx, f.wy, f.wz);
+          sm.stage[lane][0] = q0;
+          sm.stage[lane][1] = q1;
+          sm.stage[lane][2] = q2;
+          sm.stage[lane][3] = make_float4(q3.x, dt.dax, dt.day, dt.daz);
+          sm.stage[lane][4] = make_float4(dt.rdd, dt.srdd, dt.m, __int_as_float(pos));
+        }
+        __syncwarp();
+        const int cnt = min(32, nl - g);
+        for (int j = 0; j < cnt; ++j) {
+          const float4 lo = sm.la[g + j];
+          const float4 hi = sm.lb[g + j];
+          const int pos = __float_as_int(lo.w);
+          th = vis.t_hi();
+          float tn, tf;
+          const bool cover = need && pos != self && slab(r, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, tn, tf) &&
+                             tf >= prune_lo && tn <= th;
+          if (!__any_sync(0xffffffffu, cover)) continue;
+          if (lane == 0) ++st.entries;
+          if (cover) {
+            ++st.leaves;
+            const float4 q0 = sm.stage[j][0], q1 = sm.stage[j][1], q2 = sm.stage[j][2], q3 = sm.stage[j][3],
+                         q4 = sm.stage[j][4];
+            DirTerms dt;
+            dt.dax = q3.y;
+            dt.day = q3.z;
+            dt.daz = q3.w;
+            dt.rdd = q4.x;
+            dt.srdd = q4.y;
+            dt.m = q4.z;
+            float t, al;
+            if (hit_eval(q0, q1, q2, q3.x, dt, r, t, al)) {
+              ++st.hits;
+              vis.hit(pos, t, al, dt.m);
+              need = !vis.stop();
+            }
+          }
+        }
+        __syncwarp();
+      }
+      nl = 0;
+      if (!__any_sync(0xffffffffu, need)) break;
+      th = vis.t_hi();
+      bm = make_beam(need, xl, yl, zlo_l, th == FLT_MAX ? FLT_MAX : zl + th);
+      __syncwarp();
+    }
+    if (sp == 0 && nl == 0) break;
+  }
+  __syncwarp();
+}
+
+// Visibility walk of the bounce mode. Until T < t_min it multiplies every hit into T (in any
+// order, as ShadowVis), records the largest alpha m of the front-facing hits and, at the cut-off,
+// the horizon: the largest t* met so far (a hit past it has prefix transmittance below t_min and
+// is no index-matrix candidate). It keeps the nearest front-facing hit (by key). After the cut-off
+// the walk goes on pruned to the nearer of the horizon and that hit, so that it ends as the
+// nearest front-facing hit of the whole ray within the horizon: the first index-matrix candidate.
+struct BounceVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float T;
+  float t_seen;
+  float t_hor;
+  float tf;  // nearest front-facing hit: t*, position
+  int pf;
+  float amax;  // largest alpha m of the front-facing hits multiplied into T
+  __device__ float t_hi() const { return T < a.t_min ? fminf(slack_hi(t_hor), slack_hi(tf)) : FLT_MAX; }
+  __device__ bool stop() const { return false; }
+  __device__ void hit(int pos, float t, float al, float m) {
+    if (!(T < a.t_min)) {
+      T *= 1.0f - al;
+      t_seen = fmaxf(t_seen, t);
+      if (T < a.t_min) t_hor = t_seen;
+      if (m > 0.f) amax = fmaxf(amax, al * m);
+    } else if (t > t_hor) {
+      return;
+    }
+    if (m > 0.f && key_less(t, pos, tf, pf)) {
+      tf = t;
+      pf = pos;
+    }
+  }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    hit(pos, t, al, m);
+  }
+};
+
+// One search round of the index matrix: the KR nearest hits of any kind with key past the last
+// one processed (and t* within the horizon), kept sorted by key in the lane's column of a shared-
+// memory buffer, for processing in key order. In the first round (no hit processed yet) the hits
+// in front of the first candidate (key below (tf, pf)) are not kept but summed into lbase = log of
+// the prefix transmittance in front of that candidate.
+template <int KR>
+struct SearchVis {
+  const TraceArgs& a;
+  const Ray& r;
+  int self;
+  RayStats& st;
+  float t_last;
+  int p_last;
+  float t_hor;
+  float tf;
+  int pf;
+  float lbase;
+  float4 (*buf)[32];  // buf[k][lane]
+  int lane;
+  int count;
+  float t_max;  // key of the last kept hit once the buffer is full
+  int p_max;
+  __device__ float t_hi() const { return fminf(count == KR ? slack_hi(t_max) : FLT_MAX, slack_hi(t_hor)); }
+  __device__ bool stop() const { return false; }
+  __device__ void hit(int pos, float t, float al, float m) {
+    if (!key_less(t_last, p_last, t, pos)) return;
+    if (key_less(t, pos, tf, pf)) {
+      lbase += log1pf(-al);
+      return;
+    }
+    if (count == KR && !key_less(t, pos, t_max, p_max)) return;
+    // sorted insertion: shift the larger keys up by one (the last falls out when full)
+    int k = count < KR ? count : KR - 1;
+    while (k > 0) {
+      const float4 e = buf[k - 1][lane];
+      if (!key_less(t, pos, e.x, __float_as_int(e.y))) break;
+      buf[k][lane] = e;
+      --k;
+    }
+    buf[k][lane] = make_float4(t, __int_as_float(pos), al, m);
+    if (count < KR) ++count;
+    if (count == KR) {
+      const float4 e = buf[KR - 1][lane];
+      t_max = e.x;
+      p_max = __float_as_int(e.y);
+    }
+  }
+  __device__ void leaf(int pos) {
+    if (pos == self) return;
+    ++st.leaves;
+    float t, al, m;
+    if (!gauss_hit(a.recs, pos, r, t, al, m)) return;
+    ++st.hits;
+    hit(pos, t, al, m);
+  }
+};
+
+// Visibility (and with BOUNCE the index matrix) of the rays of receiver batch [r0, r1):
+// V[s * batch + (i - r0)] (0 where n.w <= 0), idx[gid * S + s].
+#ifndef PRTGS_PACKET_BOUNCE_MIN_BLOCKS
+#define PRTGS_PACKET_BOUNCE_MIN_BLOCKS 3
+#endif
+template <bool BOUNCE>
+__global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_MIN_BLOCKS : PRTGS_PACKET_MIN_BLOCKS)
+    k_packet(TraceArgs a, float* __restrict__ V, int dpi) {
+  extern __shared__ float4 psmem4[];
+  float* sdir = reinterpret_cast<float*>(psmem4);  // [S*3]
+  PacketSmem* wsm = reinterpret_cast<PacketSmem*>(sdir + ((3 * a.S + 3) & ~3));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  PacketSmem& sm = wsm[warp];
+  RoundHits& hbuf = reinterpret_cast<RoundHits*>(wsm + kPacketWarps)[warp];  // bounce mode only
+  __shared__ unsigned int s_item[kPacketWarps];
+  for (int i = threadIdx.x; i < 3 * a.S; i += blockDim.x) sdir[i] = a.dirs[i];
+  __syncthreads();
+  const int64_t batch = a.r1 - a.r0;
+  const int64_t n_packets = (batch + 31) / 32;
+  const int dblocks = (a.S + dpi - 1) / dpi;  // dpi directions per work item
+  RayStats rs{0u, 0u, 0u, 0u, 0u, 0u};
+  unsigned traced = 0, walks = 0;
+  for (;;) {
+    if (lane == 0) s_item[warp] = atomicAdd(a.work, 1u);
+    __syncwarp();
+    const unsigned item = s_item[warp];
+    __syncwarp();
+    if ((int64_t)item >= n_packets * dblocks) break;
+    const int64_t p = item / dblocks;
+    const int s0 = (int)(item % dblocks) * dpi;
+    const int64_t self64 = a.r0 + 32 * p + lane;
+    const bool valid = self64 < a.r1;
+    const int self = valid ? (int)self64 : (int)a.r0;
+    const float4 q0 = __ldg(a.recs + 4 * self);
+    const float4 q3 = __ldg(a.recs + 4 * self + 3);
+    int root = INT32_MIN;
+    if (valid) {
+      const int gid = a.order[self];
+      root = a.roots[find_scene(a.offsets, a.n_scenes, gid)];
+      if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
+    }
+    const int s1 = min(a.S, s0 + dpi);
+    for (int s = s0; s < s1; ++s) {
+      const float* d = sdir + 3 * s;
+      const float c = ray_cos(q3.y, q3.z, q3.w, d);
+      const bool up = valid && c > 0.0f;
+      float vis = up ? 1.0f : 0.0f;
+      int best = -1;  // index-matrix entry (sorted position of the chosen hit)
+      if ((a.flags & PRTGS_SHADOW) && __any_sync(0xffffffffu, up)) {
+        const Frame f = make_frame(d[0], d[1], d[2]);
+        const float xl = f.e1x * q0.x + f.e1y * q0.y + f.e1z * q0.z;
+        const float yl = f.e2x * q0.x + f.e2y * q0.y + f.e2z * q0.z;
+        const float zl = f.wx * q0.x + f.wy * q0.y + f.wz * q0.z;
+        Ray r;
+        make_ray(r, q0.x, q0.y, q0.z, d[0], d[1], d[2]);
+        traced += up ? 1u : 0u;
+        // lanes of different scenes walk their own subtrees, one group at a time
+        unsigned todo = __ballot_sync(0xffffffffu, up);
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int groot = __shfl_sync(0xffffffffu, root, leader);
+          const unsigned grp = __ballot_sync(0xffffffffu, up && root == groot) & todo;
+          const bool mine = (grp >> lane) & 1u;
+          if (lane == 0) ++walks;
+          if (!BOUNCE) {
+            ShadowVis sv{a, r, self, rs, 1.0f};
+            packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
+            if (mine) vis = sv.T;
+          } else {
+            BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f};
+            packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
+            if (mine) vis = bv.T;
+            // index matrix (Sec. 4.4): argmax of W_j = alpha_j T_j m_j over the hits in key order,
+            // T_j the prefix transmittance; candidates need T_j >= t_min and T_j <= filter_t.
+            // Every later candidate has W_j <= amax T_j (amax covers every front-facing hit when
+            // no cut-off happened, else the trivial bound 1).
+            const float lfilter = logf(a.filter_t);
+            const float lmin = a.t_min > 0.f ? logf(a.t_min) : -FLT_MAX;
+            const float lamax = bv.T < a.t_min ? 0.0f : logf(bv.amax);
+            bool searching = mine && bv.tf != FLT_MAX;
+            float t_last = -FLT_MAX, lt = 0.0f, lw_best = -FLT_MAX;
+            int p_last = INT32_MIN;
+            for (int64_t round = 0; __any_sync(0xffffffffu, searching); ++round) {
+              if (round > a.n / kPacketRoundHits + 1) {
+                if (searching) set_status(a.status, PRTGS_STATUS_BAD_INDEX);
+                break;
+              }
+              SearchVis<kPacketRoundHits> sv{a,     r,      self, rs,      t_last, p_last, bv.t_hor, bv.tf,
+                                             bv.pf, 0.0f,   hbuf,   lane, 0,     FLT_MAX, INT32_MAX};
+              if (searching) ++rs.rounds;
+              packet_walk(a, f, r, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
+                          rs.search_nodes);
+              if (searching) {
+                if (round == 0) lt = sv.lbase;
+                const int nh = sv.count;
+                bool decided = false;
+                for (int k = 0; k < nh && !decided; ++k) {
+                  if (lt < lmin || lt + lamax <= lw_best) {
+                    decided = true;
+                  } else {
+                    const float4 e = hbuf[k][lane];  // t*, position, alpha, m
+                    if (e.w > 0.f && lt <= lfilter) {
+                      const float lw = logf(e.z * e.w) + lt;
+                      if (lw > lw_best) {
+                        lw_best = lw;
+                        best = __float_as_int(e.y);
+                      }
+                    }
+                    lt += log1pf(-e.z);
+                  }
+                }
+                if (decided || nh < kPacketRoundHits || lt < lmin || lt + lamax <= lw_best) {
+                  searching = false;
+                } else {
+                  t_last = sv.t_max;
+                  p_last = sv.p_max;
+                }
+              }
+            }
+          }
+          todo &= ~grp;
+        }
+      }
+      if (valid) {
+        V[(int64_t)s * batch + (self64 - a.r0)] = vis;
+        if (BOUNCE) a.idx[(int64_t)a.order[self] * a.S + s] = best >= 0 ? a.order[best] : -1;
+      }
+    }
+  }
+  if (a.stats) {
+    unsigned long long c0 = warp_sum_u64(rs.nodes), c1 = warp_sum_u64(rs.search_nodes),
+                       c2 = warp_sum_u64(rs.leaves), c3 = warp_sum_u64(rs.hits), c4 = warp_sum_u64(rs.rounds),
+                       c5 = warp_sum_u64(traced), c8 = warp_sum_u64(walks), c9 = warp_sum_u64(rs.entries);
+    if (lane == 0) {
+      atomicAdd(a.stats + 0, c0);
+      atomicAdd(a.stats + 1, c1);
+      atomicAdd(a.stats + 4, c4);
+      atomicAdd(a.stats + 2, c2);
+      atomicAdd(a.stats + 3, c3);
+      atomicAdd(a.stats + 5, c5);
+      atomicAdd(a.stats + 8, c8);
+      atomicAdd(a.stats + 9, c9);
+    }
+  }
+}
+
+// P of the receivers of batch [r0, r1) from V[s][i]: one lane per receiver, a compensated sum
+// over the directions per coefficient (orders <= 3 from the Cartesian SH, above from the table).
+__global__ void __launch_bounds__(128) k_project(TraceArgs a, const float* __restrict__ V) {
+  extern __shared__ float psdir[];  // [S*3]
+  for (int i = threadIdx.x; i < 3 * a.S; i += blockDim.x) psdir[i] = a.dirs[i];
+  __syncthreads();
+  const int64_t batch = a.r1 - a.r0;
+  const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= batch) return;
+  const int self = (int)(a.r0 + li);
+  const float4 q3 = __ldg(a.recs + 4 * self + 3);
+  const int gid = a.order[self];
+  const int C = sh_count(a.sh_order);
+  const float wq = 4.0f * kPi / (float)a.S;
+  for (int kb = 0; kb < C; kb += kMaxC) {
+    CompSum acc[kMaxC];
+    for (int s = 0; s < a.S; ++s) {
+      const float* d = psdir + 3 * s;
+      const float c = ray_cos(q3.y, q3.z, q3.w, d);
+      if (!(c > 0.0f)) continue;
+      const float v = V[(int64_t)s * batch + li] * c * wq;
+      if (C <= kMaxC) {
+        float Y[kMaxC];
+        sh_eval_dyn(a.sh_order, d[0], d[1], d[2], Y);
+#pragma unroll
+        for (int k = 0; k < kMaxC; ++k)
+          if (k < C) acc[k].add(v * Y[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kMaxC; ++k)
+          if (kb + k < C) acc[k].add(v * __ldg(a.Ytab + (int64_t)s * C + kb + k));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxC; ++k)
+      if (kb + k < C) a.P[(int64_t)gid * C + kb + k] = acc[k].value();
+  }
+  if (a.Vg) {
+    const int slot = a.glossy_slot[gid];
+    if (slot >= 0)
+      for (int s = 0; s < a.S; ++s) a.Vg[(int64_t)slot * a.S + s] = V[(int64_t)s * batch + li];
+  }
+}
+
+static size_t packet_smem(int S, bool bounce) {
+  return sizeof(float) * ((3 * S + 3) & ~3) + sizeof(PacketSmem) * kPacketWarps +
+         (bounce ? sizeof(RoundHits) * kPacketWarps : 0);
+}
+
+template <bool BOUNCE>
+static int launch_packet_t(const TraceArgs& a, float* V, int sms, cudaStream_t stream) {
+  const size_t smem = packet_smem(a.S, BOUNCE);
+  cudaFuncSetAttribute(k_packet<BOUNCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_packet<BOUNCE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_packet<BOUNCE>, kPacketThreads, smem);
+  const int warps = sms * (per_sm > 0 ? per_sm : 1) * kPacketWarps;
+  // directions per work item: kPacketDirs, fewer when that would leave too few items per warp
+  const int64_t n_packets = (a.r1 - a.r0 + 31) / 32;
+  int dpi = kPacketDirs;
+  while (dpi > 1 && n_packets * ((a.S + dpi - 1) / dpi) < 8 * (int64_t)warps) dpi >>= 1;
+  cudaMemsetAsync(a.work, 0, sizeof(unsigned int), stream);
+  k_packet<BOUNCE><<<sms * (per_sm > 0 ? per_sm : 1), kPacketThreads, smem, stream>>>(a, V, dpi);
+  PRTGS_CHECK_LAUNCH();
+  const int64_t batch = a.r1 - a.r0;
+  k_project<<<(unsigned)((batch + 127) / 128), 128, sizeof(float) * 3 * a.S, stream>>>(a, V);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
+// Visibility, P (and with bounce the index matrix) of receiver batch [a.r0, a.r1) by packets;
+// V is scratch of S * batch floats.
+int launch_packet(const TraceArgs& a, float* V, bool bounce, int sms, cudaStream_t stream) {
+  return bounce ? launch_packet_t<true>(a, V, sms, stream) : launch_packet_t<false>(a, V, sms, stream);
+}
+
+}  // namespace prtgs
