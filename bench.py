@@ -1,13 +1,18 @@
 """Benchmark of the PRTGS hot path on GB300.
 
-One step = one pass of the whole path over the 100k-Gaussian surface workload (SH order 3,
-S = 256 directions, shadow + one-bounce transfer, one 16-coefficient RGB light, 1920x1080):
-BVH build -> transfer precompute (trace + bounce) -> relight -> splat render -> L2 loss ->
-render backward -> relight backward. Inputs are seeded synthetic stand-ins for the paper's
-datasets. Prints one JSON line.
+Default step (the largest single-GPU configuration): the 1M-splat tiled glossy workload (the
+surface scene tiled 5 x 2 with per-instance rotations, 30 % glossy splats, SH order 3, S = 256
+directions): BVH build -> transfer precompute (shadowed visibility, index matrix, one-bounce
+self-transfer, 16 x 16 glossy matrices) -> the 1920x1080 images of 64 environment lights in pixel
+space (one composite of the splats' transfer features, one tcgen05 BF16x3 contraction). The
+plain-FP32 form of the same step (per-ray BVH walk, FP32 relight on the CUDA cores, one composite
+per light) is timed beside it, with the error of the step's images against it. Inputs are
+seeded synthetic stand-ins for the paper's datasets. Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
+--workload surface-100k: the differentiable 100k surface step (transfer with bounce, relight,
+render, L2 loss, render and relight backward); batched-32, diff-300k: see their functions.
 --impl reference times the FP64 CPU oracle (brute force, all host cores) on bounded samples
 of the same workload.
 """
@@ -26,7 +31,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "surface-100k"
+WORKLOAD = "tiled-1m-glossy"
+SURFACE = "surface-100k"
 METRIC = "transfer rays/s and relit 1080p frames/s (fwd+bwd) vs plain FP32 at <=1e-4 rel err"
 UNIT = "rays/s"
 L2_BYTES = 256 << 20  # larger than the 129 MB L2
@@ -39,13 +45,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched-32", "diff-300k", "tiled-1m-glossy"],
-                    help="batched-32: 32 isotropic scenes, one graph-captured step (measurement of batching); "
-                         "diff-300k: differentiable relight + 1080p render of 300k isotropic splats; "
-                         "tiled-1m-glossy: 1M splats, 30 %% glossy, 64 lights on the tensor cores")
-    ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, SURFACE, "batched-32", "diff-300k"],
+                    help="tiled-1m-glossy (default): 1M splats, 30 %% glossy, 64 lights on the tensor cores; "
+                         "surface-100k: the differentiable 100k step; batched-32: 32 isotropic scenes, one "
+                         "graph-captured step (measurement of batching); diff-300k: differentiable relight + "
+                         "1080p render of 300k isotropic splats")
+    ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders", "transfer-traffic"],
                     help="kernels-small: the small profiling case of the ncu captures; sh-orders: relight + "
-                         "render and transfer times at SH orders 1-6, instead of the bench")
+                         "render and transfer times at SH orders 1-6; transfer-traffic: two transfer calls of "
+                         "the workload for a DRAM-traffic capture, instead of the bench")
     return ap.parse_args()
 
 
@@ -56,15 +64,15 @@ def dist_env():
     return rank, world, local
 
 
-def workload_inputs():
+def workload_inputs(name=WORKLOAD):
     from paper_2408_03538_gb300 import scenes as S
 
-    w = S.WORKLOADS[WORKLOAD]
-    sc = S.make_scene(WORKLOAD)
+    w = S.WORKLOADS[name]
+    sc = S.make_scene(name)
     dirs = S.direction_set(w["n_dirs"], S.config_seed(w["config"]))
     Lsh = S.env_lights(w["lights"], w["order"], S.config_seed(w["config"]) + 1)
     Ltarget = S.env_lights(w["lights"], w["order"], S.config_seed(w["config"]) + 2)
-    cam = S.make_camera(WORKLOAD)
+    cam = S.make_camera(name)
     return w, sc, dirs, Lsh, Ltarget, cam
 
 
@@ -99,7 +107,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w, sc, dirs, *_ = workload_inputs()
+    name = args.workload if args.workload in (WORKLOAD, SURFACE) else WORKLOAD
+    w, sc, dirs, *_ = workload_inputs(name)
     order = w["order"]
     import oracle
 
@@ -116,12 +125,12 @@ def run_reference(args):
         traced += int(((tr["flags"] & 1) != 0).sum())
     total = sum(times)
     value = rays / total
-    sample = (f"{n_recv} seeded receivers x {dirs.shape[0]} directions of the {WORKLOAD} workload per step "
+    sample = (f"{n_recv} seeded receivers x {dirs.shape[0]} directions of the {name} workload per step "
               f"(brute force over all {sc.n} Gaussians, shadow + index matrix), FP64 C oracle")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_order": order, "n_dirs": int(dirs.shape[0]),
+            "config": {"workload": name, "n_gaussians": sc.n, "sh_order": order, "n_dirs": int(dirs.shape[0]),
                        "sampled_receivers_per_step": n_recv},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -184,7 +193,9 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def run_ours(args):
+def run_surface(args):
+    """The differentiable 100k surface step: BVH build -> transfer (shadow + bounce) -> relight ->
+    1080p render -> L2 loss -> render backward -> relight backward."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
@@ -196,7 +207,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    w, sc, dirs, Lsh_np, Lt_np, cam = workload_inputs()
+    w, sc, dirs, Lsh_np, Lt_np, cam = workload_inputs(SURFACE)
     order, S_ = w["order"], int(dirs.shape[0])
     C = (order + 1) ** 2
     # host (pinned) inputs for the end-to-end leg
@@ -323,7 +334,7 @@ def run_ours(args):
         # hits a ray takes before its transmittance falls below t_min (the algorithmic work)
         hits_per_ray = float(tr["hits_live"].sum() / max(1, ((tr["flags"] & 1) != 0).sum()))
         cpu = {"value": rays / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{n_recv} seeded receivers x {S_} directions of {WORKLOAD} (shadow + index matrix, "
+               "sample": f"{n_recv} seeded receivers x {S_} directions of {SURFACE} (shadow + index matrix, "
                          f"brute force over all {sc.n} Gaussians), {dt:.1f} s"}
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -333,15 +344,16 @@ def run_ours(args):
     if hits_per_ray is not None:
         flops = traced * (hits_per_ray * 40.0 + 2.0 * C)
         achieved = flops / (transfer_ms / args.steps / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "transfer call: k_trace, k_prefix, k_rounds, k_bounce", "achieved": achieved,
-                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": transfer_traffic_bytes(),
+        roof = {"bound": "alu", "kernel": "transfer call: k_packet<true>, k_project, k_bounce", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": transfer_traffic_bytes(SURFACE, traced),
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz ({pk_kind} max clock)",
                 "algorithmic_flops_per_launch": flops}
-    launches = launches_per_step(g.n, n_pairs, cam)
+    launches = count_launches(lambda: step(g, d_dirs, d_L, target))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": g.n, "sh_order": order, "n_dirs": S_,
+            "config": {"workload": SURFACE, "n_gaussians": g.n, "sh_order": order, "n_dirs": S_,
                        "transfer": "shadow+bounce", "lights": int(Lsh_np.shape[0]),
                        "image": f"{cam.width}x{cam.height}", "l2": "flushed between steps (256 MB write)",
                        "traced_rays_per_step": traced, "pairs_per_frame": n_pairs},
@@ -350,7 +362,7 @@ def run_ours(args):
             "relit_frames_per_s_fwd_bwd_stage": 1e3 / (stage_ms[2:].sum() / args.steps),
             "stages_ms": {k: float(v / args.steps) for k, v in zip(stage_names, stage_ms)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches * args.steps,
+            "gpu_launches": launches * args.steps if launches is not None else None,
             "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -369,33 +381,55 @@ def reduce_max_over_ranks(values, device=None):
     return [float(v) for v in t.cpu()]
 
 
-def transfer_traffic_bytes():
-    """DRAM bytes per transfer call from the committed ncu summary (None if absent)."""
-    p = os.path.join(ROOT, "profiles", "dram_transfer_surface-100k.md")
+def source_sha16(files=("packet.cu", "trace.cuh")):
+    """Hash of the traversal kernel sources (ties a committed ncu traffic figure to the code it
+    was measured on)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2408_03538_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def transfer_traffic_bytes(workload, traced_rays):
+    """DRAM bytes per launch of the dominant transfer kernel, from the committed ncu summary of
+    the current kernel sources: the per-traced-ray figure of the capture times the traced rays of
+    one launch here. None when the summary is absent or was measured on other sources."""
+    p = os.path.join(ROOT, "profiles", "dram_transfer_packet.md")
+    vals = {}
     try:
         for line in open(p):
-            if line.startswith("traffic_bytes_per_transfer_call:"):
-                return float(line.split(":")[1])
+            if ":" in line and line.split(":")[0] in ("source_sha16", "dram_bytes_per_traced_ray"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
     except OSError:
-        pass
-    return None
+        return None
+    if vals.get("source_sha16") != source_sha16() or "dram_bytes_per_traced_ray" not in vals:
+        return None
+    return float(vals["dram_bytes_per_traced_ray"]) * traced_rays
 
 
-def launches_per_step(n, n_pairs, cam, n_dirs=256, bounce=True):
-    """Kernel launches of one bench step, following the launch sequence of the library."""
-    scan = 3
-    sort_pass = 1 + scan + 1  # histogram, scan, scatter
-    bvh = 3 + 4 * sort_pass + 3  # bounds init/bounds/morton, 4 passes of 8 key bits, karras + roots + pack/refit
-    batches = math.ceil(n / max(1, (1 << 23) // n_dirs)) if bounce else 1
-    transfer = batches * (1 + (scan + 3 if bounce else 0)) + (1 if bounce else 0)  # trace (+ compact/prefix/rounds), bounce
-    relight = 1
-    tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
-    tile_bits = max(1, math.ceil(math.log2(tiles)))
-    render = 1 + scan + 1 + 1 + math.ceil((32 + tile_bits) / 8) * sort_pass + 1 + 1
-    loss = 2
-    render_bwd = 2
-    relight_bwd = 3
-    return bvh + transfer + relight + render + loss + render_bwd + relight_bwd
+def count_launches(fn):
+    """Launches of libprtgs kernels during one call of fn, from the CUDA activity trace of
+    torch.profiler (None when the profiler cannot trace kernels here)."""
+    import torch
+
+    try:
+        from torch.profiler import ProfilerActivity, profile
+
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            if str(getattr(e, "device_type", "")).endswith("CUDA") and "prtgs::" in e.name:
+                n += 1
+        return n if n > 0 else None
+    except Exception:
+        return None
 
 
 def run_kernels_small():
@@ -421,9 +455,9 @@ def run_kernels_small():
     L = torch.randn((64, 3, 16), device="cuda", generator=gen)
     col = api.relight(T, alb, L, 3, precision=1)
     col32 = api.relight(T, alb, L, 3, precision=0)
-    sc2 = S.make_scene(WORKLOAD)
+    sc2 = S.make_scene(SURFACE)
     g2 = api.GaussianTensors.from_scene(sc2)
-    cam = S.make_camera(WORKLOAD, 1280, 720)
+    cam = S.make_camera(SURFACE, 1280, 720)
     colors = torch.rand((1, g2.n, 3), device="cuda", generator=gen)
     bg = torch.zeros(3, device="cuda")
     img, st = api.render(g2, colors, cam, bg, max_pairs=4_000_000)
@@ -467,6 +501,28 @@ def run_kernels_small():
                       "relight_tc_vs_fp32_max_abs": float((col - col32).abs().max())}))
 
 
+def run_transfer_traffic(args):
+    """The transfer of the bench workload (shadow + bounce, no glossy matrices) called twice, for
+    a one-pass ncu capture of the DRAM bytes of the second call's k_packet launches. Prints the
+    traced rays and the receiver batches (k_packet launches) of a call and the kernel sources'
+    hash, which the committed summary records."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    w, sc, dirs_np, *_ = workload_inputs(args.workload if args.workload in (WORKLOAD, SURFACE) else WORKLOAD)
+    g = api.GaussianTensors.from_scene(sc)
+    dirs = torch.from_numpy(dirs_np).cuda()
+    bvh = api.build_bvh(g)
+    for _ in range(2):
+        api.precompute_transfer(g, bvh, dirs, w["order"], bounce=True)
+    torch.cuda.synchronize()
+    traced = int((sc.normals.astype(np.float64) @ dirs_np.astype(np.float64).T > 0).sum())
+    batch = max(32, ((1 << 26) // dirs_np.shape[0]) // 32 * 32)
+    print(json.dumps({"case": "transfer-traffic", "workload": sc.n, "traced_rays_per_call": traced,
+                      "k_packet_launches_per_call": math.ceil(sc.n / batch), "source_sha16": source_sha16()}))
+
+
 def run_sh_orders():
     """Relight + 1920x1080 render of the 100k surface scene under one light at SH orders 1-6
     (the render-time-against-order measurement of the paper's Table 4), and the shadowed
@@ -475,9 +531,9 @@ def run_sh_orders():
 
     from paper_2408_03538_gb300 import api, scenes as S
 
-    sc = S.make_scene(WORKLOAD)
+    sc = S.make_scene(SURFACE)
     g = api.GaussianTensors.from_scene(sc)
-    cam = S.make_camera(WORKLOAD)
+    cam = S.make_camera(SURFACE)
     bg = torch.zeros(3, device="cuda")
     bvh = api.build_bvh(g)
     dirs = torch.from_numpy(S.direction_set(256, S.config_seed(1))).cuda()
@@ -507,7 +563,7 @@ def run_sh_orders():
             frames.append(a.elapsed_time(b))
         res[str(order)] = {"coefficients": C, "relight_render_ms": float(np.median(frames[3:])),
                            "transfer_ms": t_ms}
-    print(json.dumps({"case": "sh-orders", "workload": WORKLOAD, "image": f"{cam.width}x{cam.height}",
+    print(json.dumps({"case": "sh-orders", "workload": SURFACE, "image": f"{cam.width}x{cam.height}",
                       "by_order": res}))
 
 
@@ -693,109 +749,221 @@ def run_diff(args):
 
 
 def run_tiled(args):
-    """The 1M-splat tiled glossy workload (the surface scene tiled 5 x 2, 30 % glossy, order 3,
-    S = 256): a step is BVH build -> transfer (shadow + bounce + the 16 x 16 glossy matrices) ->
-    the 64 lights' 1920x1080 images in pixel space (one composite of the transfer features, one
-    tcgen05 BF16x3 contraction). Reports nominal transfer rays/s of the whole step; frames/s
-    counts the 64 relit 1080p images of a step. The per-light form (relight + 64 composites) is
-    timed beside it."""
+    """The 1M-splat tiled glossy workload (the default step). A step is BVH build -> transfer
+    (shadow + bounce + the 16 x 16 glossy matrices, warp-packet walks) -> the 64 lights' 1920x1080
+    images in pixel space (one composite of the transfer features, one tcgen05 BF16x3
+    contraction). value: nominal transfer rays (N x S) per second of whole step; frames_per_s:
+    the 64 relit 1080p images of a step per second. plain_fp32: the same step in its plain form
+    (per-ray BVH walk, FP32 relight on the CUDA cores, one composite per light), timed on the same
+    GPU, with the error of the step's images against it."""
     import torch
 
     from paper_2408_03538_gb300 import api, scenes as S
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    w = S.WORKLOADS["tiled-1m-glossy"]
-    seed = S.config_seed(w["config"])
-    sc = S.make_scene("tiled-1m-glossy")
-    g = api.GaussianTensors.from_scene(sc, dev)
-    dirs = torch.from_numpy(S.direction_set(w["n_dirs"], seed)).to(dev)
-    cam = S.make_camera("tiled-1m-glossy")
-    order, k = w["order"], w["lights"]
-    Lsh = torch.from_numpy(S.env_lights(k, order, seed + 1)).to(dev)
-    gids = torch.from_numpy(np.nonzero(sc.glossy_mask)[0].astype(np.int32)).to(dev)
-    cam_pos = torch.from_numpy((-np.asarray(cam.rot).T @ np.asarray(cam.trans)).astype(np.float32)).to(dev)
+    w, sc, dirs_np, Lsh_np, _, cam = workload_inputs(WORKLOAD)
+    order, k, S_ = w["order"], w["lights"], int(dirs_np.shape[0])
+    C = (order + 1) ** 2
+    fields = ("means", "scales", "quats", "opacity", "normals", "albedo", "roughness", "metallic", "glossy_mask")
+    host = {f: torch.from_numpy(np.ascontiguousarray(getattr(sc, f))).pin_memory() for f in fields}
+    host["dirs"] = torch.from_numpy(dirs_np).pin_memory()
+    host["L"] = torch.from_numpy(Lsh_np).pin_memory()
+    g = api.GaussianTensors(*(host[f].to(dev) for f in fields))
+    dirs = host["dirs"].to(dev)
+    Lsh = host["L"].to(dev)
     bg = torch.zeros(3, device=dev)
     status = api.Status(dev)
+    # render-state capacity from one render of the scene (outside the timed region)
     bvh0 = api.build_bvh(g, status=status)
     tr0 = api.precompute_transfer(g, bvh0, dirs, order, bounce=True, glossy=True, status=status)
-    col0 = api.relight(tr0["T"], g.albedo, Lsh[:1], order)
-    _, st0 = api.render(g, col0, cam, bg, max_pairs=60_000_000, status=status)
+    gids0 = torch.nonzero(g.glossy_mask).flatten().to(torch.int32)
+    _, st0 = api.render_relit(g, tr0["T"], Lsh[:1], cam, order, bg=bg, glossy_ids=gids0, M=tr0["M"],
+                              max_pairs=60_000_000, status=status)
     torch.cuda.synchronize()
     n_pairs = st0.n_pairs()
     state = api.RenderState(g.n, cam.width, cam.height, int(n_pairs * 1.25) + 4096, dev)
-    del tr0, col0, st0, bvh0
-    C = (order + 1) ** 2
+    del tr0, st0, bvh0
     bufs = {"P": torch.empty((g.n, C), device=dev), "T": torch.empty((g.n, 3, C), device=dev),
-            "idx": torch.empty((g.n, int(dirs.shape[0])), dtype=torch.int32, device=dev)}
-    colors = torch.empty((k, g.n, 3), device=dev)
+            "idx": torch.empty((g.n, S_), dtype=torch.int32, device=dev)}
+    image = torch.empty((k, 3, cam.height, cam.width), device=dev)
     stream = torch.cuda.current_stream()
     names = ["bvh", "transfer", "relight_render_64_lights"]
 
-    image = torch.empty((k, 3, cam.height, cam.width), device=dev)
+    def step(gt, dirs_t, L_t, ev=None, out_img=image):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
 
-    def step(ev):
-        ev[0].record(stream)
-        bvh = api.build_bvh(g, status=status)
-        ev[1].record(stream)
-        out = api.precompute_transfer(g, bvh, dirs, order, bounce=True, glossy=True, status=status, out=bufs)
-        ev[2].record(stream)
-        # all 64 lights in pixel space: one composite of the transfer features, one contraction
-        api.render_relit(g, out["T"], Lsh, cam, order, bg=bg, precision=1, glossy_ids=gids, M=out["M"],
-                         state=state, status=status, out=image)
-        ev[3].record(stream)
+        mark(0)
+        bvh = api.build_bvh(gt, status=status)
+        mark(1)
+        out = api.precompute_transfer(gt, bvh, dirs_t, order, bounce=True, glossy=True, status=status, out=bufs)
+        mark(2)
+        gids = torch.nonzero(gt.glossy_mask).flatten().to(torch.int32)
+        api.render_relit(gt, out["T"], L_t, cam, order, bg=bg, precision=1, glossy_ids=gids, M=out["M"],
+                         state=state, status=status, out=out_img)
+        mark(3)
         return out
 
     for _ in range(args.warmup):
-        out = step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+        step(g, dirs, Lsh)
     torch.cuda.synchronize()
     assert status.read() == 0, "device status reported an error"
+    if world > 1:
+        dist.barrier()
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    stage_ms = np.zeros(3)
-    total = 0.0
+    evs = []
     for _ in range(args.steps):
         flush.zero_()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        out = step(ev)
-        ev[3].synchronize()
+        step(g, dirs, Lsh, ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    stage_ms = np.zeros(3)
+    total = 0.0
+    for ev in evs:
         for i in range(3):
             stage_ms[i] += ev[i].elapsed_time(ev[i + 1])
         total += ev[0].elapsed_time(ev[3])
-    clocks = sampler.stop()
-    # the per-light form beside it (outside the timed step): relight of every splat under each
-    # light, then one composite per light
-    per_light = []
-    for _ in range(3):
+    # end to end through the public API: host (pinned) inputs copied in and the 64 images copied
+    # out every step
+    gbuf = api.GaussianTensors(*(torch.empty_like(getattr(g, f)) for f in fields))
+    dirs_b, L_b = torch.empty_like(dirs), torch.empty_like(Lsh)
+    img_h = torch.empty(image.shape, dtype=torch.float32).pin_memory()
+    h2d = sum(host[f].numel() * host[f].element_size() for f in host)
+    d2h = img_h.numel() * 4
+    e2e = 0.0
+    for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        api.relight(out["T"], g.albedo, Lsh, order, precision=1, glossy_ids=gids, M=out["M"], means=g.means,
-                    cam_pos=cam_pos, out=colors)
-        api.render(g, colors, cam, bg, state=state, status=status, out=image)
+        for f in fields:
+            getattr(gbuf, f).copy_(host[f], non_blocking=True)
+        dirs_b.copy_(host["dirs"], non_blocking=True)
+        L_b.copy_(host["L"], non_blocking=True)
+        step(gbuf, dirs_b, L_b)
+        img_h.copy_(image, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-        per_light.append(e0.elapsed_time(e1))
+        e2e += e0.elapsed_time(e1)
+    clocks = sampler.stop()
     assert status.read() == 0
-    total, = reduce_max_over_ranks([total], dev)
-    rays = g.n * int(dirs.shape[0])
+    launches = count_launches(lambda: step(g, dirs, Lsh))
+    # the dominant kernel group: the transfer's visibility walk and index matrix (k_packet<true>,
+    # with k_project and k_bounce), timed live in calls without the glossy matrices
+    tx = []
+    for _ in range(3):
+        bvh = api.build_bvh(g, status=status)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.precompute_transfer(g, bvh, dirs, order, bounce=True, status=status, out=bufs)
+        e1.record(stream)
+        e1.synchronize()
+        tx.append(e0.elapsed_time(e1))
+    walk_ms = float(np.median(tx))
+    # the optimised step's outputs, then the plain-FP32 form of the same step
+    out_opt = step(g, dirs, Lsh)
+    T_opt = out_opt["T"].clone()
+    img_opt = image.clone()
+    colors = torch.empty((k, g.n, 3), device=dev)
+    cam_pos = torch.from_numpy(np.asarray(cam.position, np.float32)).to(dev)
+    pbufs = {"P": torch.empty_like(bufs["P"]), "T": torch.empty_like(bufs["T"]), "idx": torch.empty_like(bufs["idx"])}
+    img_plain = torch.empty_like(image)
+    plain = {"bvh": [], "transfer": [], "relight_render_64_lights": []}
+    for _ in range(2):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        bvh = api.build_bvh(g, status=status)
+        ev[1].record(stream)
+        outp = api.precompute_transfer(g, bvh, dirs, order, bounce=True, glossy=True, status=status, out=pbufs,
+                                       walk=1)
+        ev[2].record(stream)
+        gids = torch.nonzero(g.glossy_mask).flatten().to(torch.int32)
+        api.relight(outp["T"], g.albedo, Lsh, order, precision=0, glossy_ids=gids, M=outp["M"], means=g.means,
+                    cam_pos=cam_pos, out=colors)
+        api.render(g, colors, cam, bg, state=state, status=status, out=img_plain)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        for i, nm in enumerate(plain):
+            plain[nm].append(ev[i].elapsed_time(ev[i + 1]))
+    assert status.read() == 0
+    a = img_opt.double().reshape(k, -1)
+    b = img_plain.double().reshape(k, -1)
+    img_err = float(((a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-30)).max())
+    ta, tb = T_opt.double().reshape(g.n, -1), pbufs["T"].double().reshape(g.n, -1)
+    t_err = (ta - tb).norm(dim=1) / tb.norm(dim=1).clamp_min(1e-3 * 1.44)
+    plain_ms = {nm: float(np.median(v)) for nm, v in plain.items()}
+    plain_total = sum(plain_ms.values())
+    total, e2e, walk_ms = reduce_max_over_ranks([total, e2e, walk_ms], dev)
+    rays = g.n * S_
+    traced = int((sc.normals.astype(np.float64) @ dirs_np.astype(np.float64).T > 0).sum())
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+    cpu = None
+    hits_per_ray = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        n_recv = calibrate_oracle(sc, dirs_np, order, 12.0)
+        dt, nr, tr = oracle_sample(sc, dirs_np, order, n_recv, 999)
+        hits_per_ray = float(tr["hits_live"].sum() / max(1, ((tr["flags"] & 1) != 0).sum()))
+        cpu = {"value": nr / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{n_recv} seeded receivers x {S_} directions of {WORKLOAD} (shadow + index matrix, "
+                         f"brute force over all {sc.n} Gaussians), {dt:.1f} s"}
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    roof = None
+    if hits_per_ray is not None:
+        flops = traced * (hits_per_ray * 40.0 + 2.0 * C)
+        achieved = flops / (walk_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_packet<true> (visibility walk + index matrix; with k_project and "
+                                          "k_bounce, one transfer call without the glossy matrices)",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": transfer_traffic_bytes(WORKLOAD, traced),
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz ({pk_kind} max clock)",
+                "algorithmic_flops_per_call": flops, "call_ms": walk_ms,
+                "hits_per_traced_ray": hits_per_ray, "traced_rays": traced,
+                "timed": "3 calls after the timed steps, L2 flushed, CUDA events on the launching stream"}
     line = {"metric": METRIC, "value": world * rays * args.steps / (total / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (relight bf16x3 on tensor cores)",
-            "data": "synthetic",
-            "config": {"workload": "tiled-1m-glossy", "n_gaussians": g.n, "n_glossy": int(gids.numel()),
-                       "sh_order": order, "n_dirs": int(dirs.shape[0]), "transfer": "shadow+bounce+glossy",
-                       "lights": k, "image": f"{cam.width}x{cam.height}", "pairs_per_frame": n_pairs,
-                       "l2": "flushed between steps (256 MB write)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": g.n, "n_glossy": int(gids0.numel()), "sh_order": order,
+                       "n_dirs": S_, "transfer": "shadow+bounce+glossy (warp-packet walk)", "lights": k,
+                       "relight": "pixel space, tcgen05 BF16x3 (FP32-accurate split), FP32 accumulate",
+                       "image": f"{cam.width}x{cam.height}", "pairs_per_frame": n_pairs,
+                       "traced_rays_per_step": traced, "l2": "flushed between steps (256 MB write)"},
             "frames_per_s": world * k * args.steps / (total / 1e3),
             "stages_ms": {nm: float(v / args.steps) for nm, v in zip(names, stage_ms)},
-            "per_light_relight_render_ms": float(np.median(per_light)),
-            "clocks": clocks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "plain_fp32": {"form": "per-ray BVH walk, FP32 relight on the CUDA cores, one composite per light",
+                           "ms_per_step": plain_total, "stages_ms": plain_ms,
+                           "speedup_of_step": plain_total / (total / args.steps),
+                           "max_rel_err_images": img_err,
+                           "T_rel_err_max": float(t_err.max()), "T_splats_rel_err_above_1e-4": int((t_err > 1e-4).sum()),
+                           "note": "image error: norm-wise per light, the step's images against the plain form's; "
+                                   "T differs only where a rounding near-tie flips an index-matrix entry"},
+            "e2e": {"value": world * rays * args.steps / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches * args.steps if launches is not None else None,
+            "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
 
 
 def main():
@@ -804,16 +972,18 @@ def main():
         run_kernels_small()
     elif args.case == "sh-orders":
         run_sh_orders()
+    elif args.case == "transfer-traffic":
+        run_transfer_traffic(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched-32":
         run_batched(args)
     elif args.workload == "diff-300k":
         run_diff(args)
-    elif args.workload == "tiled-1m-glossy":
-        run_tiled(args)
+    elif args.workload == SURFACE:
+        run_surface(args)
     else:
-        run_ours(args)
+        run_tiled(args)
 
 
 if __name__ == "__main__":

@@ -18,8 +18,12 @@
  *    (non-finite inputs, traversal stack overflow, buffer capacity) are OR-ed as bit flags
  *    into a caller-provided int32 device status word, read after synchronisation with
  *    prtgs_read_status(). No kernel traps, asserts or waits without a bound: the one device
- *    wait, for the tensor cores' completion in the tcgen05 relight paths, gives up after a
- *    bounded number of polls and then writes NaN to that tile's outputs instead of results.
+ *    wait, for the tensor cores' completion in the tcgen05 relight paths, polls at most
+ *    tc_wait_polls times (PRTGS_TC_WAIT_POLLS normally). When it gives up, the CTA sets
+ *    PRTGS_STATUS_TIMEOUT, waits once more with PRTGS_TC_WAIT_POLLS polls so that the
+ *    tensor cores have finished with its shared and tensor memory before either is reused or
+ *    freed, writes NaN to the outputs of that tile and of every later tile it owns, and issues
+ *    no further tensor-core work.
  *
  * Notation follows the paper: N Gaussians, S sphere directions, C = (order+1)^2 real SH
  * coefficients (order <= 3, so C <= 16, for every path; orders 4-6, C <= 49, where a call says
@@ -50,6 +54,10 @@ typedef struct CUstream_st* prtgs_stream_t; /* a cudaStream_t; NULL = legacy def
 #define PRTGS_STATUS_STACK_OVERFLOW 2  /* BVH traversal stack exceeded (cannot happen for <= 2^27 leaves) */
 #define PRTGS_STATUS_CAPACITY 4        /* render: more (Gaussian, tile) pairs than max_pairs */
 #define PRTGS_STATUS_BAD_INDEX 8       /* an index outside its array was met and skipped */
+#define PRTGS_STATUS_TIMEOUT 16        /* a tensor-core completion wait gave up (outputs of that tile are NaN) */
+
+/* Default poll limit of the tensor cores' completion wait (argument tc_wait_polls below). */
+#define PRTGS_TC_WAIT_POLLS (1u << 26)
 
 /* ---- flags of prtgs_transfer_params.flags ------------------------------------------- */
 #define PRTGS_SHADOW 1u  /* visibility V from the other Gaussians (else V = 1) */
@@ -237,12 +245,16 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
  * or k <= 160 (t_channels 3: three accumulators in the 512 TMEM columns), otherwise
  * PRTGS_ERR_UNSUPPORTED.
  * cam_pos and means may be NULL when n_glossy == 0.
+ * status (device int32, may be NULL) receives PRTGS_STATUS_TIMEOUT when a tensor-core wait gave
+ * up; tc_wait_polls bounds that wait (PRTGS_TC_WAIT_POLLS; 0 gives up at once, which exercises the
+ * failure path). Both are ignored by PRTGS_PREC_FP32.
  */
 size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision);
 int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
                   int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* means,
                   const float* cam_pos, const float* L, int32_t k, int32_t precision, float* colors,
-                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+                  int32_t* status, uint32_t tc_wait_polls, void* workspace, size_t workspace_bytes,
+                  prtgs_stream_t stream);
 
 /*
  * Relight of many scenes in one launch: scene b holds Gaussians scene_offsets[b] ..
@@ -250,11 +262,12 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
  * L[b,k,3,C] (device). colors[3 k n] holds one contiguous [k, n_b, 3] block per scene,
  * scene b's block starting at float 3 k scene_offsets[b] (the input layout of prtgs_render
  * for that scene). No workspace. Tensor-core precisions need 3k <= 256 (t_channels 1) or
- * k <= 160 (t_channels 3).
+ * k <= 160 (t_channels 3). status, tc_wait_polls: as prtgs_relight.
  */
 int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
                           const int64_t* scene_offsets, int32_t n_scenes, const float* L, int32_t k,
-                          int32_t precision, float* colors, prtgs_stream_t stream);
+                          int32_t precision, float* colors, int32_t* status, uint32_t tc_wait_polls,
+                          prtgs_stream_t stream);
 
 /*
  * Relight backward (diffuse splats; glossy rows of dcolors must be zero or are ignored).
@@ -349,15 +362,16 @@ int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const
  * or FP32 CUDA cores (k <= 256). Same result as prtgs_relight + prtgs_render up to rounding, at
  * the cost of one 3C-channel composite instead of k 3-channel ones.
  *   T[n,t_channels,C], albedo from g; glossy as prtgs_relight; L[k,3,C]; bg[3] (device);
- *   image[k,3,H,W] out. Workspace: prtgs_render_relit_workspace_size.
+ *   image[k,3,H,W] out. Workspace: prtgs_render_relit_workspace_size. status: as prtgs_render, plus
+ *   PRTGS_STATUS_TIMEOUT from the tensor-core contraction; tc_wait_polls: as prtgs_relight.
  */
 size_t prtgs_render_relit_workspace_size(int64_t n, int32_t sh_order, int32_t width, int32_t height,
                                          int64_t max_pairs);
 int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* T, int32_t t_channels,
                        int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* L, int32_t k,
                        int32_t precision, const prtgs_camera* cam, const float* bg, float* image,
-                       prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
-                       prtgs_stream_t stream);
+                       prtgs_render_state* st, int32_t* status, uint32_t tc_wait_polls, void* workspace,
+                       size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
  * Depth and normal maps of the splats (Eq. 23 and Eq. 25): front-to-back composites, with the

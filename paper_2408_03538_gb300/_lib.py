@@ -16,7 +16,8 @@ c_int32, c_int64, c_uint32, c_float, c_size_t, c_void_p = (ctypes.c_int32, ctype
 
 # status codes and flags (include/prtgs.h)
 OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA = 0, -1, -2, -3, -4, -5
-STATUS_NONFINITE, STATUS_STACK_OVERFLOW, STATUS_CAPACITY, STATUS_BAD_INDEX = 1, 2, 4, 8
+STATUS_NONFINITE, STATUS_STACK_OVERFLOW, STATUS_CAPACITY, STATUS_BAD_INDEX, STATUS_TIMEOUT = 1, 2, 4, 8, 16
+TC_WAIT_POLLS = 1 << 26
 SHADOW, BOUNCE, GLOSSY = 1, 2, 4
 PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
 
@@ -72,16 +73,16 @@ _SIGS = {
     "prtgs_render_relit_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32, c_int64]),
     "prtgs_render_relit": (c_int32, [P(Gaussians), c_int32, c_void_p, c_int32, c_int64, c_void_p, c_void_p,
                                      c_void_p, c_int32, c_int32, P(Camera), c_void_p, c_void_p, P(RenderState),
-                                     c_void_p, c_void_p, c_size_t, c_void_p]),
+                                     c_void_p, c_uint32, c_void_p, c_size_t, c_void_p]),
     "prtgs_render_geometry_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int64]),
     "prtgs_render_geometry": (c_int32, [P(Gaussians), P(Camera), c_void_p, c_void_p, P(RenderState), c_void_p,
                                         c_void_p, c_size_t, c_void_p]),
     "prtgs_relight_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "prtgs_relight": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_void_p,
-                                c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
-                                c_void_p]),
+                                c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_uint32,
+                                c_void_p, c_size_t, c_void_p]),
     "prtgs_relight_batched": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
-                                        c_int32, c_int32, c_void_p, c_void_p]),
+                                        c_int32, c_int32, c_void_p, c_void_p, c_uint32, c_void_p]),
     "prtgs_relight_backward_workspace_size": (c_size_t, [c_int64, c_int32, c_int32]),
     "prtgs_relight_backward": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

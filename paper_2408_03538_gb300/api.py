@@ -197,8 +197,10 @@ def precompute_transfer_backward(g: GaussianTensors, bvh: Bvh, dirs: torch.Tenso
 # Relight
 # ------------------------------------------------------------------------------------------
 def relight(T: torch.Tensor, albedo: torch.Tensor, Lsh: torch.Tensor, order: int, precision: int = L.PREC_FP32,
-            glossy_ids=None, M=None, means=None, cam_pos=None, out=None):
-    """colors [k,n,3] = (albedo/pi) * (T . L_k) (Eq. 14; glossy Eq. 41)."""
+            glossy_ids=None, M=None, means=None, cam_pos=None, out=None, status: Status | None = None,
+            tc_wait_polls: int = L.TC_WAIT_POLLS):
+    """colors [k,n,3] = (albedo/pi) * (T . L_k) (Eq. 14; glossy Eq. 41). ``status`` receives
+    STATUS_TIMEOUT when a tensor-core completion wait (``tc_wait_polls`` polls) gave up."""
     lib = L.load()
     n = int(T.shape[0])
     tch = 3 if T.dim() == 3 else 1
@@ -207,12 +209,14 @@ def relight(T: torch.Tensor, albedo: torch.Tensor, Lsh: torch.Tensor, order: int
     ng = int(glossy_ids.numel()) if glossy_ids is not None else 0
     ws, nb = _ws(lib.prtgs_relight_workspace_size(n, order, k, precision), T.device)
     L.check(lib.prtgs_relight(n, order, _ptr(T), tch, _ptr(albedo), ng, _ptr(glossy_ids), _ptr(M), _ptr(means),
-                              _ptr(cam_pos), _ptr(Lsh), k, precision, _ptr(colors), _ptr(ws), nb, _stream()),
+                              _ptr(cam_pos), _ptr(Lsh), k, precision, _ptr(colors),
+                              status.ptr() if status else None, int(tc_wait_polls), _ptr(ws), nb, _stream()),
             "prtgs_relight")
     return colors
 
 
-def relight_batched(T, albedo, scene_offsets, Lsh, order, precision=L.PREC_FP32, out=None):
+def relight_batched(T, albedo, scene_offsets, Lsh, order, precision=L.PREC_FP32, out=None, status=None,
+                    tc_wait_polls=L.TC_WAIT_POLLS):
     """Relight many scenes in one launch; Lsh [B,k,3,C] holds each scene's lights. Returns a flat
     buffer of 3kn floats holding one [k, n_b, 3] block per scene (see scene_colors)."""
     lib = L.load()
@@ -221,7 +225,8 @@ def relight_batched(T, albedo, scene_offsets, Lsh, order, precision=L.PREC_FP32,
     B, k = int(Lsh.shape[0]), int(Lsh.shape[1])
     colors = out if out is not None else torch.empty(3 * k * n, dtype=torch.float32, device=T.device)
     L.check(lib.prtgs_relight_batched(n, order, _ptr(T), tch, _ptr(albedo), _ptr(scene_offsets), B, _ptr(Lsh), k,
-                                      precision, _ptr(colors), _stream()), "prtgs_relight_batched")
+                                      precision, _ptr(colors), status.ptr() if status else None,
+                                      int(tc_wait_polls), _stream()), "prtgs_relight_batched")
     return colors
 
 
@@ -307,7 +312,8 @@ def render(g: GaussianTensors, colors: torch.Tensor, cam, bg: torch.Tensor, stat
 
 def render_relit(g: GaussianTensors, T: torch.Tensor, Lsh: torch.Tensor, cam, order: int, bg: torch.Tensor = None,
                  precision: int = L.PREC_BF16X3, glossy_ids=None, M=None, state: RenderState | None = None,
-                 max_pairs: int | None = None, status: Status | None = None, out=None):
+                 max_pairs: int | None = None, status: Status | None = None, out=None,
+                 tc_wait_polls: int = L.TC_WAIT_POLLS):
     """image [k,3,H,W] of every light at once in pixel space: one composite of the splats'
     (rho/pi) T (glossy: (rho/pi) M Y(v)) features, then a per-pixel contraction with the lights."""
     lib = L.load()
@@ -325,7 +331,8 @@ def render_relit(g: GaussianTensors, T: torch.Tensor, Lsh: torch.Tensor, cam, or
     cs = camera_struct(cam)
     L.check(lib.prtgs_render_relit(ctypes.byref(gs), order, _ptr(T), tch, ng, _ptr(glossy_ids), _ptr(M), _ptr(Lsh),
                                    k, precision, ctypes.byref(cs), _ptr(bg), _ptr(image), ctypes.byref(state.s),
-                                   status.ptr() if status else None, _ptr(ws), nb, _stream()), "prtgs_render_relit")
+                                   status.ptr() if status else None, int(tc_wait_polls), _ptr(ws), nb, _stream()),
+            "prtgs_render_relit")
     state._ws = ws
     return image, state
 

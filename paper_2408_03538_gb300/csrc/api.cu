@@ -172,7 +172,8 @@ size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int3
 int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
                   int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* means,
                   const float* cam_pos, const float* L, int32_t k, int32_t precision, float* colors,
-                  void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+                  int32_t* status, uint32_t tc_wait_polls, void* workspace, size_t workspace_bytes,
+                  prtgs_stream_t stream) {
   int rc;
   if (n < 0 || k < 0 || n_glossy < 0 || n_glossy > n) return PRTGS_ERR_SHAPE;
   if ((rc = check_order_high(sh_order))) return rc;
@@ -185,12 +186,13 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
   rc = check_ws(workspace, workspace_bytes, relight_workspace(n, sh_order, k, precision));
   if (rc) return rc;
   return finish(relight(n, sh_order, T, t_channels, albedo, n_glossy, glossy_ids, M, means, cam_pos, L, k, precision,
-                        colors, workspace, reinterpret_cast<cudaStream_t>(stream)));
+                        colors, status, tc_wait_polls, workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels, const float* albedo,
                           const int64_t* scene_offsets, int32_t n_scenes, const float* L, int32_t k,
-                          int32_t precision, float* colors, prtgs_stream_t stream) {
+                          int32_t precision, float* colors, int32_t* status, uint32_t tc_wait_polls,
+                          prtgs_stream_t stream) {
   int rc;
   if (n < 0 || k < 0 || n_scenes < 1) return PRTGS_ERR_SHAPE;
   if ((rc = check_order(sh_order))) return rc;
@@ -201,7 +203,7 @@ int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t
   if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_shape(k, t_channels, nullptr, nullptr))
     return PRTGS_ERR_UNSUPPORTED;
   return finish(relight_batched(n, sh_order, T, t_channels, albedo, scene_offsets, n_scenes, L, k, precision,
-                                colors, reinterpret_cast<cudaStream_t>(stream)));
+                                colors, status, tc_wait_polls, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 size_t prtgs_relight_backward_workspace_size(int64_t n, int32_t sh_order, int32_t k) {
@@ -261,8 +263,8 @@ size_t prtgs_render_relit_workspace_size(int64_t n, int32_t sh_order, int32_t wi
 int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* T, int32_t t_channels,
                        int64_t n_glossy, const int32_t* glossy_ids, const float* M, const float* L, int32_t k,
                        int32_t precision, const prtgs_camera* cam, const float* bg, float* image,
-                       prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
-                       prtgs_stream_t stream) {
+                       prtgs_render_state* st, int32_t* status, uint32_t tc_wait_polls, void* workspace,
+                       size_t workspace_bytes, prtgs_stream_t stream) {
   int rc = check_gaussians(g);
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
@@ -278,7 +280,7 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
                 render_relit_workspace(g->n, sh_order, cam->width, cam->height, st->max_pairs));
   if (rc) return rc;
   return finish(render_relit(g, sh_order, T, t_channels, n_glossy, glossy_ids, M, L, k, precision, cam, bg, image,
-                             st, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+                             st, status, tc_wait_polls, workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 size_t prtgs_render_geometry_workspace_size(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {

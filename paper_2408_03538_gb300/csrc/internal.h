@@ -43,23 +43,25 @@ int precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh,
 size_t relight_workspace(int64_t n, int32_t order, int32_t k, int32_t precision);
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
             const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
-            int32_t k, int32_t precision, float* colors, void* ws, cudaStream_t stream);
+            int32_t k, int32_t precision, float* colors, int32_t* status, unsigned tc_wait_polls, void* ws,
+            cudaStream_t stream);
 int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                     const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
-                    float* colors, cudaStream_t stream);
+                    float* colors, int32_t* status, unsigned tc_wait_polls, cudaStream_t stream);
 // relight_tc.cu
 int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad, int* tmem_cols);
 int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,
                int32_t k, int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors,
-               cudaStream_t stream);
+               int32_t* status, unsigned tc_wait_polls, cudaStream_t stream);
 
 int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float* final_T, const float* bg,
-                      const float* L, int32_t k, int32_t precision, float* image, cudaStream_t stream);
+                      const float* L, int32_t k, int32_t precision, float* image, int32_t* status,
+                      unsigned tc_wait_polls, cudaStream_t stream);
 size_t render_relit_workspace(int64_t n, int32_t order, int32_t width, int32_t height, int64_t max_pairs);
 int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_t t_channels, int64_t n_glossy,
                  const int32_t* glossy_ids, const float* M, const float* L, int32_t k, int32_t precision,
                  const prtgs_camera* cam, const float* bg, float* image, prtgs_render_state* st, int32_t* status,
-                 void* ws, cudaStream_t stream);
+                 unsigned tc_wait_polls, void* ws, cudaStream_t stream);
 
 size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k);
 int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,

@@ -135,12 +135,14 @@ static void launch_relight_c(int64_t n, const float* T, int tch, const float* al
 
 int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, int64_t n_glossy,
             const int32_t* glossy_ids, const float* M, const float* means, const float* cam_pos, const float* L,
-            int32_t k, int32_t precision, float* colors, void* ws, cudaStream_t stream) {
+            int32_t k, int32_t precision, float* colors, int32_t* status, unsigned tc_wait_polls, void* ws,
+            cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
   if (k > kMaxLightsSmem) return PRTGS_ERR_UNSUPPORTED;
   if (precision != PRTGS_PREC_FP32) {
     // every row on the tensor cores; glossy rows are then rewritten by the glossy kernel
-    const int rc = relight_tc(n, order, T, t_channels, albedo, L, k, precision, nullptr, 1, colors, stream);
+    const int rc = relight_tc(n, order, T, t_channels, albedo, L, k, precision, nullptr, 1, colors, status,
+                              tc_wait_polls, stream);
     if (rc != PRTGS_OK) return rc;
   } else {
     switch (order) {
@@ -259,7 +261,7 @@ size_t render_relit_workspace(int64_t n, int32_t order, int32_t width, int32_t h
 int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_t t_channels, int64_t n_glossy,
                  const int32_t* glossy_ids, const float* M, const float* L, int32_t k, int32_t precision,
                  const prtgs_camera* cam, const float* bg, float* image, prtgs_render_state* st, int32_t* status,
-                 void* ws, cudaStream_t stream) {
+                 unsigned tc_wait_polls, void* ws, cudaStream_t stream) {
   const int64_t n = g->n;
   const int C = sh_count(order);
   const int64_t n_pix = (int64_t)cam->width * cam->height;
@@ -287,7 +289,8 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
   int rc = render(g, F, C, cam, zero, TI, st, status, rws, stream);
   if (rc != PRTGS_OK) return rc;
   if (precision != PRTGS_PREC_FP32)
-    return relight_tc_pixels(n_pix, order, TI, st->final_T, bg, L, k, precision, image, stream);
+    return relight_tc_pixels(n_pix, order, TI, st->final_T, bg, L, k, precision, image, status, tc_wait_polls,
+                             stream);
   const size_t smem = sizeof(float) * k * 3 * C;
   const unsigned blocks = (unsigned)((n_pix + kRelightThreads - 1) / kRelightThreads);
   switch (order) {
@@ -350,10 +353,11 @@ static void launch_relight_batched_c(int64_t n, const float* T, int tch, const f
 
 int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                     const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k, int32_t precision,
-                    float* colors, cudaStream_t stream) {
+                    float* colors, int32_t* status, unsigned tc_wait_polls, cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
   if (precision != PRTGS_PREC_FP32)
-    return relight_tc(n, order, T, t_channels, albedo, L, k, precision, offsets, n_scenes, colors, stream);
+    return relight_tc(n, order, T, t_channels, albedo, L, k, precision, offsets, n_scenes, colors, status,
+                      tc_wait_polls, stream);
   switch (order) {
     case 1: launch_relight_batched_c<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
     case 2: launch_relight_batched_c<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;

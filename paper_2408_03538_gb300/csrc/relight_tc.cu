@@ -103,6 +103,43 @@ __device__ __forceinline__ void load_lights(unsigned char* sB, const float* __re
   }
 }
 
+// Polls the mbarrier phase at most `polls` times; true once the phase has completed.
+__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t phase, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase));
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int64_t ob_of(const int64_t* offsets, int b) { return offsets ? offsets[b] : 0; }
+__device__ __forceinline__ int64_t nb_of(const int64_t* offsets, int b, int64_t n) {
+  return offsets ? offsets[b + 1] - offsets[b] : n;
+}
+
+// NaN for every light's output of this thread's row (a tile whose MMA result is not trusted).
+template <bool PIXEL>
+__device__ __forceinline__ void write_nan(bool mine, int k, int64_t n, int64_t gi, int64_t ob, int64_t nb,
+                                          float* __restrict__ colors) {
+  if (!mine || (threadIdx.x >> 7) != 0) return;  // one thread per row
+  const float q = __int_as_float(0x7fc00000);
+  for (int l = 0; l < k; ++l) {
+    if (PIXEL) {
+      for (int c = 0; c < 3; ++c) colors[((int64_t)l * 3 + c) * n + gi] = q;
+    } else {
+      float* out = colors + 3 * (int64_t)k * ob + ((int64_t)l * nb + (gi - ob)) * 3;
+      out[0] = q;
+      out[1] = q;
+      out[2] = q;
+    }
+  }
+}
+
 // offsets == nullptr: one scene with lights L. Otherwise scene b (rows offsets[b] ..
 // offsets[b+1]) uses lights L + b * k * 3 * C; a tile that straddles scenes is run once per
 // scene with the other rows zeroed. n_pad: N of each MMA; TMEM group g starts at column
@@ -116,7 +153,8 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
                                                            const float* __restrict__ L, int k, int n_pad, int slabs,
                                                            int tmem_cols, const int64_t* __restrict__ offsets,
                                                            int n_scenes, float* __restrict__ colors,
-                                                           const float* __restrict__ bgv = nullptr) {
+                                                           const float* __restrict__ bgv, int32_t* status,
+                                                           unsigned wait_polls) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // layout: [A groups x slabs][B groups x slabs]
   unsigned char* sA = smem_raw;
@@ -144,6 +182,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
   uint32_t phase = 0;
   const int64_t tiles = (n + kTcRows - 1) / kTcRows;
   int cached = -1;
+  bool failed = false;  // a completion wait of this CTA gave up: no further MMAs, NaN outputs
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kTcRows;
     const int64_t row_end = row0 + kTcRows < n ? row0 + kTcRows : n;
@@ -198,11 +237,15 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t lo = offsets ? (offsets[b] > row0 ? offsets[b] : row0) : row0;
       const int64_t hi = offsets ? (offsets[b + 1] < row_end ? offsets[b + 1] : row_end) : row_end;
       if (hi <= lo) continue;  // empty scene (uniform over the block)
+      const bool mine = gi >= lo && gi < hi;
+      if (failed) {  // CTA-uniform: the tensor cores are no longer used by this CTA
+        write_nan<PIXEL>(mine, k, n, gi, ob_of(offsets, b), nb_of(offsets, b, n), colors);
+        continue;
+      }
       if (b != cached) {
         load_lights<C, TCH>(sB, L + (int64_t)b * k * 3 * C, k, n_pad, slabs);
         cached = b;
       }
-      const bool mine = gi >= lo && gi < hi;
       // output block of this scene: [k, n_b, 3] at 3 k offsets[b] (the whole [k, n, 3] for one scene)
       const int64_t ob = offsets ? offsets[b] : 0;
       const int64_t nb = offsets ? offsets[b + 1] - ob : n;
@@ -250,19 +293,24 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&mbar)));
       }
-      // bounded wait for the MMA chain
-      bool done = false;
-      for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(&mbar)), "r"(phase));
-        done = ok != 0;
+      // bounded wait for the MMA chain. If any thread gives up, the whole CTA treats the tile as
+      // failed: it reports PRTGS_STATUS_TIMEOUT and waits again with the full limit so that the
+      // chain has finished reading the operands and writing the accumulator before anything
+      // reuses them (or the tensor memory is freed); the tile's outputs become NaN.
+      bool done = bounded_wait(smem_u32(&mbar), phase, wait_polls);
+      if (__syncthreads_or(!done)) {
+        if (tid == 0) set_status(status, PRTGS_STATUS_TIMEOUT);
+        bounded_wait(smem_u32(&mbar), phase, kWaitLimit);
+        failed = true;
       }
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;");
+      if (failed) {
+        write_nan<PIXEL>(mine, k, n, gi, ob, nb, colors);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        continue;
+      }
       // epilogue: this thread holds accumulator row `row` (TMEM lane row); eight lights at a
       // time, the warps of a lane quarter taking groups of eight in turn
       for (int l0 = 8 * khalf; l0 < k; l0 += 8 * kKSplit) {
@@ -287,7 +335,7 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const uint32_t bits = TCH == 1 ? r[3 * ll + c] : r[8 * c + ll];
-            v[c] = done ? fmaf(__uint_as_float(bits), rho[c], add[c]) : __int_as_float(0x7fc00000);
+            v[c] = fmaf(__uint_as_float(bits), rho[c], add[c]);
           }
           if (PIXEL) {
             if (mine) {
@@ -315,10 +363,10 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
 template <int C, int TCH>
 static void launch_tc(int grid, size_t smem, cudaStream_t stream, int64_t n, const float* T, const float* albedo,
                       const float* L, int k, int n_pad, int slabs, int tmem_cols, const int64_t* offsets,
-                      int n_scenes, float* colors) {
+                      int n_scenes, float* colors, int32_t* status, unsigned wait_polls) {
   cudaFuncSetAttribute(k_relight_tc<C, TCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_relight_tc<C, TCH><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
-                                                            n_scenes, colors);
+                                                            n_scenes, colors, nullptr, status, wait_polls);
 }
 
 // Tensor-core shape of a relight: N of each MMA and the TMEM columns (a power of two >= 32
@@ -340,7 +388,8 @@ int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad_out, int* tmem_co
 
 // Pixel-space relight on the tensor cores: image[l,c,p] = sum_m TI[m,c,p] L[l,c,m] + bg[c] final_T[p].
 int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float* final_T, const float* bg,
-                      const float* L, int32_t k, int32_t precision, float* image, cudaStream_t stream) {
+                      const float* L, int32_t k, int32_t precision, float* image, int32_t* status,
+                      unsigned wait_polls, cudaStream_t stream) {
   if (n_pix == 0 || k == 0) return PRTGS_OK;
   int n_pad = 0, tmem_cols = 0;
   if (!relight_tc_shape(k, 3, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
@@ -361,7 +410,7 @@ int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float
 #define PRTGS_PIX_LAUNCH(CC)                                                                                     \
   cudaFuncSetAttribute(k_relight_tc<CC, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
   k_relight_tc<CC, 3, true><<<grid, kTcThreads, smem, stream>>>(n_pix, TI, final_T, L, k, n_pad, slabs, tmem_cols, \
-                                                                nullptr, 1, image, bg)
+                                                                nullptr, 1, image, bg, status, wait_polls)
   switch (order) {
     case 1: PRTGS_PIX_LAUNCH(4); break;
     case 2: PRTGS_PIX_LAUNCH(9); break;
@@ -374,7 +423,7 @@ int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float
 
 int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,
                int32_t k, int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors,
-               cudaStream_t stream) {
+               int32_t* status, unsigned wait_polls, cudaStream_t stream) {
   if (n == 0 || k == 0) return PRTGS_OK;
   int n_pad = 0, tmem_cols = 0;
   if (!relight_tc_shape(k, t_channels, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
@@ -399,16 +448,16 @@ int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, con
   const bool rgb = tch == 3;
   switch (order) {
     case 1:
-      if (rgb) launch_tc<4, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
-      else launch_tc<4, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      if (rgb) launch_tc<4, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
+      else launch_tc<4, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
       break;
     case 2:
-      if (rgb) launch_tc<9, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
-      else launch_tc<9, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      if (rgb) launch_tc<9, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
+      else launch_tc<9, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
       break;
     default:
-      if (rgb) launch_tc<16, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
-      else launch_tc<16, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors);
+      if (rgb) launch_tc<16, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
+      else launch_tc<16, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
       break;
   }
   PRTGS_CHECK_LAUNCH();

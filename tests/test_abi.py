@@ -79,10 +79,10 @@ def test_host_side_validation_without_gpu():
     assert lib.prtgs_build_bvh(ctypes.byref(g2), ctypes.byref(bvh2), None, ctypes.c_void_p(264), need,
                                None) == L.ERR_WORKSPACE
     # relight: bad channel count and precision
-    assert lib.prtgs_relight(10, 2, fake, 2, fake, 0, None, None, None, None, fake, 1, 0, fake, None, 0,
-                             None) == L.ERR_SHAPE
-    assert lib.prtgs_relight(10, 2, fake, 1, fake, 0, None, None, None, None, fake, 1, 7, fake, None, 0,
-                             None) == L.ERR_INVALID_ARG
+    assert lib.prtgs_relight(10, 2, fake, 2, fake, 0, None, None, None, None, fake, 1, 0, fake, None,
+                             L.TC_WAIT_POLLS, None, 0, None) == L.ERR_SHAPE
+    assert lib.prtgs_relight(10, 2, fake, 1, fake, 0, None, None, None, None, fake, 1, 7, fake, None,
+                             L.TC_WAIT_POLLS, None, 0, None) == L.ERR_INVALID_ARG
     # BVH layout: too many scenes
     out = L.BVH()
     assert lib.prtgs_bvh_init(fake, 1 << 20, 10, 200, fake, ctypes.byref(out)) == L.ERR_UNSUPPORTED

@@ -49,16 +49,31 @@ def test_max_over_ranks_without_process_group():
     assert bench.reduce_max_over_ranks([1.5, 2]) == [1.5, 2.0]
 
 
-def test_launch_count_and_traffic_file():
+def test_traffic_figure_is_tied_to_the_kernel_sources(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic is read from the committed ncu summary only when that summary
+    was measured on the current traversal sources; otherwise it is reported as unknown."""
     sys.path.insert(0, ROOT)
     import bench
-    from paper_2408_03538_gb300 import scenes as S
 
-    cam = S.make_camera("surface-100k")
-    n = bench.launches_per_step(100_000, 2_000_000, cam)
-    assert 50 < n < 200
-    t = bench.transfer_traffic_bytes()
-    assert t is None or t > 0
+    h = bench.source_sha16()
+    assert len(h) == 16 and h == bench.source_sha16()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "paper_2408_03538_gb300").symlink_to(os.path.join(ROOT, "paper_2408_03538_gb300"))
+    assert bench.transfer_traffic_bytes("tiled-1m-glossy", 1000) is None  # no summary
+    (prof / "dram_transfer_packet.md").write_text(f"source_sha16: {h}\ndram_bytes_per_traced_ray: 12.5\n")
+    assert bench.transfer_traffic_bytes("tiled-1m-glossy", 1000) == 12500.0
+    (prof / "dram_transfer_packet.md").write_text("source_sha16: 0000000000000000\ndram_bytes_per_traced_ray: 12.5\n")
+    assert bench.transfer_traffic_bytes("tiled-1m-glossy", 1000) is None  # stale: other sources
+
+
+def test_launch_count_needs_a_cuda_trace():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    if not torch.cuda.is_available():
+        assert bench.count_launches(lambda: None) is None
 
 
 def test_reference_arm_prints_the_contract_line():
@@ -78,6 +93,6 @@ def test_reference_arm_prints_the_contract_line():
     for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
-    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "surface-100k"
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "tiled-1m-glossy"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
