@@ -362,7 +362,7 @@ def run_surface(args):
             "relit_frames_per_s_fwd_bwd_stage": 1e3 / (stage_ms[2:].sum() / args.steps),
             "stages_ms": {k: float(v / args.steps) for k, v in zip(stage_names, stage_ms)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches * args.steps if launches is not None else None,
+            "gpu_launches": launches * args.steps,
             "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -412,24 +412,17 @@ def transfer_traffic_bytes(workload, traced_rays):
 
 
 def count_launches(fn):
-    """Launches of libprtgs kernels during one call of fn, from the CUDA activity trace of
-    torch.profiler (None when the profiler cannot trace kernels here)."""
+    """Kernel launches libprtgs issues during one call of fn (the library's own launch counter)."""
     import torch
 
-    try:
-        from torch.profiler import ProfilerActivity, profile
+    from paper_2408_03538_gb300 import _lib as L
 
-        torch.cuda.synchronize()
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        n = 0
-        for e in prof.events():
-            if str(getattr(e, "device_type", "")).endswith("CUDA") and "prtgs::" in e.name:
-                n += 1
-        return n if n > 0 else None
-    except Exception:
-        return None
+    lib = L.load()
+    torch.cuda.synchronize()
+    c0 = lib.prtgs_launch_count()
+    fn()
+    torch.cuda.synchronize()
+    return int(lib.prtgs_launch_count() - c0)
 
 
 def run_kernels_small():
@@ -569,11 +562,14 @@ def run_sh_orders():
 
 def run_batched(args):
     """32 isotropic scenes (Gaussian counts log-uniform in [1e4, 5e5]), order 3, S = 128, shadowed
-    transfer, 8 lights per scene relit, 1280x720 render + L2 loss + backward per scene; the whole
-    step is one CUDA-graph replay. Reports summed transfer rays/s and relit frames/s."""
+    transfer, 8 lights per scene relit with the FP32-accurate BF16x3 split on the tensor cores,
+    1280x720 render + per-scene L2 loss + render and relight backward: one call per stage over
+    every scene, the whole step one CUDA-graph replay. Reports summed transfer rays/s and relit
+    frames/s (fwd+bwd); the same step as one call per scene and stage is timed beside it."""
     import torch
 
-    from paper_2408_03538_gb300 import batched, scenes as S
+    from paper_2408_03538_gb300 import _lib as L
+    from paper_2408_03538_gb300 import api, batched, scenes as S
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -581,9 +577,10 @@ def run_batched(args):
     seed = S.config_seed(w["config"])
     parts = S.batched_scenes(seed)
     lights = np.stack([S.env_lights(w["lights"], w["order"], seed + 100 + b) for b in range(len(parts))])
-    cams = [S.make_camera("batched-32") for _ in parts]
+    cams = [S.look_at_camera((0.05 * (b % 8) - 0.2, -3.5, 1.5), (0.0, 0.0, 0.0), 50.0, 1280, 720)
+            for b in range(len(parts))]
     dirs = S.direction_set(w["n_dirs"], seed)
-    pipe = batched.BatchedPipeline(parts, dirs, w["order"], lights, cams)
+    pipe = batched.BatchedPipeline(parts, dirs, w["order"], lights, cams, precision=L.PREC_BF16X3)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         pipe.step()
@@ -612,25 +609,37 @@ def run_batched(args):
             else:
                 eager_ms += e0.elapsed_time(e1)
     clocks = sampler.stop()
-    # the same transfer work without batching: one BVH build and one transfer call per scene
-    from paper_2408_03538_gb300 import api
-
-    per_scene_ms = 0.0
+    # the same step as one call per scene and stage (no batching)
     gts = [pipe.scene(b) for b in range(pipe.B)]
-    for _ in range(2):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for gb in gts:
-            api.precompute_transfer(gb, api.build_bvh(gb), pipe.dirs, w["order"])
-        e1.record(stream)
-        e1.synchronize()
-        per_scene_ms = e0.elapsed_time(e1)
+    states = []
+    for b, gb in enumerate(gts):
+        col = torch.zeros((w["lights"], gb.n, 3), device="cuda")
+        _, st0 = api.render(gb, col, cams[b], pipe.bg, max_pairs=64 * max(gb.n, 4096))
+        torch.cuda.synchronize()
+        states.append(api.RenderState(gb.n, 1280, 720, int(st0.n_pairs() * 1.25) + 4096))
+        del st0
+    tgt = pipe.targets
+
+    def per_scene_step():
+        for b, gb in enumerate(gts):
+            bvh = api.build_bvh(gb)
+            P = api.precompute_transfer(gb, bvh, pipe.dirs, w["order"], packet_dirs=pipe.packet_dirs)["P"]
+            col = api.relight(P, gb.albedo, pipe.L[b], w["order"], precision=pipe.precision)
+            img, _ = api.render(gb, col, cams[b], pipe.bg, state=states[b])
+            loss, dimg = api.l2_loss(img, tgt[b])
+            dcol = api.render_backward(gb, col, cams[b], pipe.bg, states[b], dimg)[4]
+            api.relight_backward(P, gb.albedo, pipe.L[b], w["order"], dcol)
+
+    per_scene_step()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
     e0.record(stream)
-    api.precompute_transfer(pipe.g, api.build_bvh(pipe.g, pipe.offs_d), pipe.dirs, w["order"])
+    per_scene_step()
     e1.record(stream)
     e1.synchronize()
-    batched_transfer_ms = e0.elapsed_time(e1)
+    per_scene_ms = e0.elapsed_time(e1)
+    launches = count_launches(pipe.step)
     n_total = sum(p.n for p in parts)
     rays = n_total * int(dirs.shape[0])
     frames = len(parts) * w["lights"]
@@ -640,12 +649,12 @@ def run_batched(args):
             "config": {"workload": "batched-32", "scenes": len(parts), "n_gaussians": n_total,
                        "sizes_min_max": [min(p.n for p in parts), max(p.n for p in parts)], "sh_order": w["order"],
                        "n_dirs": int(dirs.shape[0]), "lights_per_scene": w["lights"],
-                       "image": f"{cams[0].width}x{cams[0].height}", "relight_precision": int(pipe.precision),
-                       "l2": "flushed between steps (256 MB write)"},
+                       "image": f"{cams[0].width}x{cams[0].height}", "relight": "tcgen05 BF16x3",
+                       "packet_dirs": int(pipe.packet_dirs), "l2": "flushed between steps (256 MB write)"},
             "frames_per_s": frames * args.steps / (graph_ms / 1e3),
             "eager_ms_per_step": eager_ms / args.steps, "graph_ms_per_step": graph_ms / args.steps,
-            "transfer_batched_ms": batched_transfer_ms, "transfer_per_scene_calls_ms": per_scene_ms,
-            "clocks": clocks}
+            "per_scene_calls_ms_per_step": per_scene_ms,
+            "gpu_launches_per_step": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -959,7 +968,7 @@ def run_tiled(args):
                                    "T differs only where a rounding near-tie flips an index-matrix entry"},
             "e2e": {"value": world * rays * args.steps / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches * args.steps if launches is not None else None,
+            "gpu_launches": launches * args.steps,
             "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -161,6 +161,9 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *   walk            tuning: 0 = warp packets (default: the rays that 32 receivers adjacent in
  *                   Morton order cast along one direction walk the BVH together), 1 = one ray
  *                   per lane (the plain per-ray walk); both give the same results
+ *   packet_dirs     tuning: directions per work item of the packet walk (its work tile:
+ *                   32 receivers x packet_dirs directions), 1..64; 0 = chosen from the problem
+ *                   size (see prtgs_autotune); the results do not depend on it
  *   stats           optional device uint64[10] that the call ADDS its work counters to:
  *                   BVH node visits of the visibility walks, node visits of the index-matrix
  *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays, rays
@@ -179,6 +182,7 @@ typedef struct prtgs_transfer_params {
   unsigned long long* stats;
   int32_t n_bounces;
   int32_t walk;
+  int32_t packet_dirs;
 } prtgs_transfer_params;
 
 size_t prtgs_transfer_workspace_size(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);
@@ -332,7 +336,9 @@ typedef struct prtgs_render_state {
   uint32_t* ranges;    /* [tiles, 2] start, end of each tile's run of pairs */
   float* final_T;      /* [H,W] */
   int32_t* n_contrib;  /* [H,W] one past the last contributing pair of each pixel's tile list */
+  /* (batched states: ranges [n_scenes * tiles, 2], final_T and n_contrib [n_scenes, H, W]) */
   uint32_t* n_pairs;   /* [1] number of pairs produced */
+  int32_t n_scenes;    /* scenes whose tiles, final_T and n_contrib the state holds (1 unless batched) */
 } prtgs_render_state;
 
 size_t prtgs_render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
@@ -404,12 +410,132 @@ size_t prtgs_l2_loss_workspace_size(int64_t count);
 int prtgs_l2_loss(const float* image, const float* target, int64_t count, float* loss, float* dimage,
                   void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
 
+/*
+ * Batched scenes (many scenes of uneven size in one launch per stage; Sec. 5's scenes relit
+ * together). Scene b holds Gaussians scene_offsets[b] .. scene_offsets[b+1] (device int64
+ * [n_scenes+1], n_scenes <= 128) and has its own camera cams[b] (HOST array [n_scenes]; every
+ * camera has the same width and height); the cameras are passed by value to the kernels, so
+ * these calls copy nothing to the device and can be captured in a CUDA graph.
+ *   colors   the layout of prtgs_relight_batched: scene b's [k, n_b, 3] block at 3 k offsets[b]
+ *   images   [n_scenes, k, 3, H, W]
+ *   st       a state laid out by prtgs_render_state_init_batched for the same n_scenes; the
+ *            single-scene calls reject it (and the batched calls reject single-scene states)
+ * Tiles are numbered scene-major, so one preprocess, one duplicate, one sort, one range pass
+ * and one composite launch cover every scene; the results equal prtgs_render per scene.
+ */
+size_t prtgs_render_state_bytes_batched(int64_t n, int32_t n_scenes, int32_t width, int32_t height,
+                                        int64_t max_pairs);
+int prtgs_render_state_init_batched(void* buffer, size_t bytes, int64_t n, int32_t n_scenes, int32_t width,
+                                    int32_t height, int64_t max_pairs, prtgs_render_state* out);
+size_t prtgs_render_batched_workspace_size(int64_t n, int32_t n_scenes, int32_t width, int32_t height,
+                                           int64_t max_pairs);
+int prtgs_render_batched(const prtgs_gaussians* g, const int64_t* scene_offsets, int32_t n_scenes,
+                         const float* colors, int32_t k, const prtgs_camera* cams, const float* bg, float* images,
+                         prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                         prtgs_stream_t stream);
+
+/* Backward of prtgs_render_batched: dimages [n_scenes, k, 3, H, W] in; d_colors in the batched
+ * colour layout, the other gradients per Gaussian (overwritten). As prtgs_render_backward. */
+size_t prtgs_render_backward_batched_workspace_size(int64_t n, int32_t k);
+int prtgs_render_backward_batched(const prtgs_gaussians* g, const int64_t* scene_offsets, int32_t n_scenes,
+                                  const float* colors, int32_t k, const prtgs_camera* cams, const float* bg,
+                                  const prtgs_render_state* st, const float* dimages, float* d_means, float* d_scales,
+                                  float* d_quats, float* d_opacity, float* d_colors, void* workspace,
+                                  size_t workspace_bytes, prtgs_stream_t stream);
+
+/* Per-scene L2 losses of n_scenes images of `count` elements each (images and targets
+ * [n_scenes, count]): losses[b] = mean over scene b, dimages = 2 (image - target) / count. */
+size_t prtgs_l2_loss_batched_workspace_size(int64_t count, int32_t n_scenes);
+int prtgs_l2_loss_batched(const float* images, const float* targets, int64_t count, int32_t n_scenes, float* losses,
+                          float* dimages, void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/* Relight backward of prtgs_relight_batched (diffuse): dcolors in the batched colour layout,
+ * L[n_scenes, k, 3, C]; d_albedo[n,3], dT[n,t_channels,C] (may be NULL) and dL[n_scenes, k, 3, C]
+ * out (overwritten; dL a deterministic per-scene reduction). */
+size_t prtgs_relight_backward_batched_workspace_size(int64_t n, int32_t n_scenes, int32_t sh_order, int32_t k);
+int prtgs_relight_backward_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels,
+                                   const float* albedo, const int64_t* scene_offsets, int32_t n_scenes, const float* L,
+                                   int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                                   void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * Autotuning of launch variants (the work-tile shapes and paths that give the same results).
+ * prtgs_autotune times each variant of one call on the caller's own inputs (one untimed run, then
+ * `repeats` timed runs, CUDA events on `stream`; the call synchronises the stream and overwrites
+ * the call's outputs), stores the fastest in *best and writes a JSON report to out_json (host,
+ * json_bytes >= 512 suggested; PRTGS_ERR_INVALID_ARG if it does not fit):
+ *   {"kernel": ..., "variant": ..., "shape": {...}, "ms": {"<variant>": <mean ms>, ...}, "best": ...}
+ *   PRTGS_TUNE_TRANSFER   args: prtgs_tune_transfer (the arguments of prtgs_precompute_transfer);
+ *                         variant: packet_dirs in {1, 2, 4, 8, 16, 32}
+ *   PRTGS_TUNE_RELIGHT    args: prtgs_tune_relight (the arguments of prtgs_relight_batched; one
+ *                         scene is scene_offsets {0, n}); variant: precision among the
+ *                         FP32-accurate ones, PRTGS_PREC_FP32 and (when the shape fits the tensor
+ *                         cores) PRTGS_PREC_BF16X3
+ * Errors of the timed call are returned as they are.
+ */
+#define PRTGS_TUNE_TRANSFER 1
+#define PRTGS_TUNE_RELIGHT 2
+
+typedef struct prtgs_tune_transfer {
+  const prtgs_gaussians* g;
+  const prtgs_bvh* bvh;
+  prtgs_transfer_params params;
+  float* P;
+  float* T;
+  int32_t* idx;
+  float* M;
+  int64_t n_glossy;
+  int32_t* status;
+  void* workspace;
+  size_t workspace_bytes;
+} prtgs_tune_transfer;
+
+typedef struct prtgs_tune_relight {
+  int64_t n;
+  int32_t sh_order;
+  int32_t t_channels;
+  const float* T;
+  const float* albedo;
+  const int64_t* scene_offsets;
+  int32_t n_scenes;
+  int32_t k;
+  const float* L;
+  float* colors;
+  int32_t* status;
+} prtgs_tune_relight;
+
+int prtgs_autotune(int32_t kernel_id, const void* args, int32_t repeats, prtgs_stream_t stream, int32_t* best,
+                   char* out_json, size_t json_bytes);
+
+/*
+ * CUDA-graph capture of a sequence of library calls (the batched step replayed with one launch
+ * from the host). Between prtgs_graph_begin(stream) and prtgs_graph_end(stream, &graph), calls
+ * enqueued on `stream` are recorded instead of run; prtgs_graph_launch replays them on a stream,
+ * with the pointers and scalars they were recorded with (so their buffers and workspaces must
+ * stay allocated), and prtgs_graph_destroy frees the graph. Every call that enqueues work can be
+ * recorded, except prtgs_read_status (it synchronises) and the first call of
+ * prtgs_relight_backward_noalloc on a device (it looks up its scratch address). The legacy
+ * default stream (NULL) cannot be captured: PRTGS_ERR_INVALID_ARG. A CUDA error while capturing
+ * or instantiating: PRTGS_ERR_CUDA. Instantiation takes driver resources, no device memory of
+ * the caller.
+ */
+typedef struct prtgs_graph_s* prtgs_graph_t;
+int prtgs_graph_begin(prtgs_stream_t stream);
+int prtgs_graph_end(prtgs_stream_t stream, prtgs_graph_t* graph);
+int prtgs_graph_launch(prtgs_graph_t graph, prtgs_stream_t stream);
+int prtgs_graph_destroy(prtgs_graph_t graph);
+
 /* Read and clear a device status word (synchronises `stream`). Returns the bits or a
  * negative PRTGS_ERR_* code. */
 int prtgs_read_status(int32_t* status, prtgs_stream_t stream);
 
 const char* prtgs_strerror(int code);
 int prtgs_version(void);
+
+/* Kernel launches the library has issued in this process so far (every device and thread; a
+ * CUDA-graph replay relaunches captured kernels without passing through the library, so it
+ * does not count). Host only; for measuring how many kernels a sequence of calls runs. */
+unsigned long long prtgs_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -129,7 +129,7 @@ def _cos_weights(scene, dirs, recv):
 
 
 def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = False, filter_t: float = 1.0,
-             t_min: float = DEFAULT_T_MIN, tol: float = 1e-4):
+             t_min: float = DEFAULT_T_MIN, tol: float = 1e-4, bounce_T: bool = True):
     """Transfer vectors for receivers ``recv``.
 
     Returns P [R,C] (Eq. 29: raw sum_s w V (n.w)^+ Y(w_s), w = 4 pi/S; albedo and 1/pi are
@@ -137,7 +137,8 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
     with j the index-matrix entry of ray s (Eq. 33; the hit splat's own diffuse transfer
     carries its rho_j/pi, so T becomes RGB). ``allow_P``/``allow_T`` bound the change that
     flipping any flagged discrete decision (or stopping a ray at transmittance t_min) can
-    cause, for use as a per-receiver tolerance widening.
+    cause, for use as a per-receiver tolerance widening. ``bounce_T=False`` returns the index
+    matrix of a bounce trace without T (which needs P of every splat the index matrix points to).
     """
     recv = np.asarray(recv, dtype=np.int64).reshape(-1)
     S = np.asarray(dirs).shape[0]
@@ -151,6 +152,9 @@ def transfer(scene, dirs, order: int, recv, shadow: bool = True, bounce: bool = 
     res = dict(P=tr["P"], allow_P=allow_P, V=tr["V"], dV=tr["dV"], idx=tr["idx"], flags=tr["flags"],
                hits=tr["hits"], hits_live=tr["hits_live"], traced=traced.sum(axis=1))
     if not bounce:
+        return res
+    if not bounce_T:
+        res.update(cand=tr["cand"])
         return res
     # receivers whose P is needed: every index-matrix entry, plus the alternatives of flagged rays
     amb = (tr["flags"] & RF_AMBIG_ARGMAX) != 0

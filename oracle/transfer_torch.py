@@ -17,9 +17,27 @@ import torch
 from .render import quat_to_rot
 
 
+def _hit_test(means, Sinv, recv_means, d, j0, j1):
+    """Frozen hit set of the receivers' rays against Gaussians j0..j1: [Ni,Nj,S] booleans
+    (t* > 0 and D^2 <= 9, the closest approach in Sigma^-1)."""
+    u = recv_means[:, None, :] - means[None, j0:j1, :]  # o - mu_j
+    Sd = torch.einsum("jab,sb->jsa", Sinv[j0:j1], d)
+    a = torch.einsum("sa,jsa->js", d, Sd)
+    b = torch.einsum("ija,jsa->ijs", u, Sd)
+    cc = torch.einsum("ija,jab,ijb->ij", u, Sinv[j0:j1], u)
+    t = -b / a[None]
+    D2 = cc[:, :, None] - b * b / a[None]
+    return (t > 0) & (D2 <= 9.0)
+
+
 def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
     """P [len(recv),C] for the receivers ``recv`` (default: all, in index order); every Gaussian
-    is an occluder. dirs [S,3] and Y [S,C] (SH table) are constants."""
+    is an occluder. dirs [S,3] and Y [S,C] (SH table) are constants.
+
+    A Gaussian that no traced ray (n.w > 0) of receiver i hits contributes a factor 1 to each of
+    the visibility products that reach P_i, and nothing to the gradient, so after the (detached)
+    hit test over all Gaussians the differentiable product of receiver i runs over the ones its
+    traced rays hit."""
     d = torch.as_tensor(np.asarray(dirs, np.float64))
     Y = torch.as_tensor(np.asarray(Y, np.float64))
     n = means.shape[0]
@@ -27,20 +45,35 @@ def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
     recv = torch.arange(n) if recv is None else torch.as_tensor(np.asarray(recv), dtype=torch.long)
     R = quat_to_rot(quats)
     Sinv = R @ torch.diag_embed(1.0 / (scales * scales)) @ R.transpose(1, 2)  # [N,3,3]
-    u = means[recv][:, None, :] - means[None, :, :]  # [Ni,Nj,3] = o - mu_j
-    Sd = torch.einsum("jab,sb->jsa", Sinv, d)  # [Nj,S,3]
-    a = torch.einsum("sa,jsa->js", d, Sd)  # [Nj,S]
-    b = torch.einsum("ija,jsa->ijs", u, Sd)  # [Ni,Nj,S]
-    cc = torch.einsum("ija,jab,ijb->ij", u, Sinv, u)  # [Ni,Nj]
-    t = -b / a[None]
-    D2 = cc[:, :, None] - b * b / a[None]
-    hit = ((t > 0) & (D2 <= 9.0)).detach()
-    hit = hit & (recv[:, None] != torch.arange(n)[None, :])[:, :, None]
-    alpha = opacity[None, :, None] * torch.exp(-0.5 * D2)
-    one_m = torch.where(hit, 1.0 - alpha, torch.ones_like(alpha))
-    V = torch.prod(one_m, dim=1)  # [Ni,S]
-    c = normals[recv] @ d.T  # [Ni,S]
-    up = (c > 0).detach()
+    with torch.no_grad():
+        traced = (normals.detach()[recv] @ d.T) > 0  # [Ni,S]: rays with n.w <= 0 contribute nothing
+        chunk = max(1, (1 << 23) // max(1, len(recv) * S))
+        occ_mask = torch.zeros((len(recv), n), dtype=torch.bool)
+        for j0 in range(0, n, chunk):
+            j1 = min(n, j0 + chunk)
+            h = _hit_test(means.detach(), Sinv.detach(), means.detach()[recv], d, j0, j1)
+            occ_mask[:, j0:j1] = (h & traced[:, None, :]).any(dim=2)
+        occ_mask[torch.arange(len(recv)), recv] = False  # the receiver itself is no occluder
     w = 4.0 * math.pi / S
-    contrib = torch.where(up, w * V * c, torch.zeros_like(c))
-    return contrib @ Y
+    rows = []
+    for r, i in enumerate(recv.tolist()):
+        occ = torch.nonzero(occ_mask[r]).flatten()
+        c = normals[i] @ d.T  # [S]
+        up = (c > 0).detach()
+        if occ.numel() == 0:  # nothing hit: V = 1 on every traced ray
+            rows.append(torch.where(up, w * c, torch.zeros_like(c)))
+            continue
+        u = means[i][None, :] - means[occ]  # [No,3] = o - mu_j
+        So = Sinv[occ]
+        Sd = torch.einsum("jab,sb->jsa", So, d)  # [No,S,3]
+        a = torch.einsum("sa,jsa->js", d, Sd)  # [No,S]
+        b = torch.einsum("ja,jsa->js", u, Sd)  # [No,S]
+        cc = torch.einsum("ja,jab,jb->j", u, So, u)  # [No]
+        t = -b / a
+        D2 = cc[:, None] - b * b / a
+        hit = ((t > 0) & (D2 <= 9.0)).detach()
+        alpha = opacity[occ][:, None] * torch.exp(-0.5 * D2)
+        one_m = torch.where(hit, 1.0 - alpha, torch.ones_like(alpha))
+        V = torch.prod(one_m, dim=0)  # [S]
+        rows.append(torch.where(up, w * V * c, torch.zeros_like(c)))
+    return torch.stack(rows) @ Y

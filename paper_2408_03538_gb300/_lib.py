@@ -37,7 +37,22 @@ class BVH(ctypes.Structure):
 class TransferParams(ctypes.Structure):
     _fields_ = [("sh_order", c_int32), ("n_dirs", c_int32), ("dirs", c_void_p), ("t_min", c_float),
                 ("same_surface_t", c_float), ("flags", c_uint32), ("index_buffer", c_int32), ("stats", c_void_p),
-                ("n_bounces", c_int32), ("walk", c_int32)]
+                ("n_bounces", c_int32), ("walk", c_int32), ("packet_dirs", c_int32)]
+
+
+class TuneTransfer(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("bvh", ctypes.c_void_p), ("params", TransferParams), ("P", c_void_p),
+                ("T", c_void_p), ("idx", c_void_p), ("M", c_void_p), ("n_glossy", c_int64), ("status", c_void_p),
+                ("workspace", c_void_p), ("workspace_bytes", c_size_t)]
+
+
+class TuneRelight(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("sh_order", c_int32), ("t_channels", c_int32), ("T", c_void_p),
+                ("albedo", c_void_p), ("scene_offsets", c_void_p), ("n_scenes", c_int32), ("k", c_int32),
+                ("L", c_void_p), ("colors", c_void_p), ("status", c_void_p)]
+
+
+TUNE_TRANSFER, TUNE_RELIGHT = 1, 2
 
 
 class Camera(ctypes.Structure):
@@ -51,12 +66,13 @@ class RenderState(ctypes.Structure):
                 ("tiles_x", c_int32), ("tiles_y", c_int32), ("mean2d", c_void_p), ("conic_op", c_void_p),
                 ("depth", c_void_p), ("radius", c_void_p), ("tiles_touched", c_void_p), ("pair_keys", c_void_p),
                 ("pair_ids", c_void_p), ("ranges", c_void_p), ("final_T", c_void_p), ("n_contrib", c_void_p),
-                ("n_pairs", c_void_p)]
+                ("n_pairs", c_void_p), ("n_scenes", c_int32)]
 
 
 P = ctypes.POINTER
 _SIGS = {
     "prtgs_version": (c_int32, []),
+    "prtgs_launch_count": (ctypes.c_ulonglong, []),
     "prtgs_strerror": (ctypes.c_char_p, [c_int32]),
     "prtgs_read_status": (c_int32, [c_void_p, c_void_p]),
     "prtgs_bvh_bytes": (c_size_t, [c_int64, c_int32]),
@@ -98,6 +114,28 @@ _SIGS = {
     "prtgs_render_backward": (c_int32, [P(Gaussians), c_void_p, c_int32, P(Camera), c_void_p, P(RenderState),
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_size_t, c_void_p]),
+    "prtgs_render_state_bytes_batched": (c_size_t, [c_int64, c_int32, c_int32, c_int32, c_int64]),
+    "prtgs_render_state_init_batched": (c_int32, [c_void_p, c_size_t, c_int64, c_int32, c_int32, c_int32, c_int64,
+                                                  P(RenderState)]),
+    "prtgs_render_batched_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32, c_int64]),
+    "prtgs_render_batched": (c_int32, [P(Gaussians), c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
+                                       c_void_p, P(RenderState), c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_render_backward_batched_workspace_size": (c_size_t, [c_int64, c_int32]),
+    "prtgs_render_backward_batched": (c_int32, [P(Gaussians), c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                                                c_void_p, P(RenderState), c_void_p, c_void_p, c_void_p, c_void_p,
+                                                c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_l2_loss_batched_workspace_size": (c_size_t, [c_int64, c_int32]),
+    "prtgs_l2_loss_batched": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_size_t,
+                                        c_void_p]),
+    "prtgs_relight_backward_batched_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
+    "prtgs_relight_backward_batched": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                                 c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                 c_size_t, c_void_p]),
+    "prtgs_autotune": (c_int32, [c_int32, c_void_p, c_int32, c_void_p, P(c_int32), ctypes.c_char_p, c_size_t]),
+    "prtgs_graph_begin": (c_int32, [c_void_p]),
+    "prtgs_graph_end": (c_int32, [c_void_p, P(c_void_p)]),
+    "prtgs_graph_launch": (c_int32, [c_void_p, c_void_p]),
+    "prtgs_graph_destroy": (c_int32, [c_void_p]),
     "prtgs_l2_loss_workspace_size": (c_size_t, [c_int64]),
     "prtgs_l2_loss": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
 }

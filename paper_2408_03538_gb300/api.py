@@ -134,7 +134,7 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
                         bounce: bool = False, glossy: bool = False, t_min: float = DEFAULT_T_MIN,
                         same_surface_t: float = 1.0, status: Status | None = None, out: dict | None = None,
                         stats: torch.Tensor | None = None, index_buffer: int = 0, n_bounces: int = 1,
-                        walk: int = 0):
+                        walk: int = 0, packet_dirs: int = 0):
     """Transfer vectors P [n,C], and with ``bounce`` T [n,3,C] (``n_bounces`` self-transfer
     bounces over the index matrix) and idx [n,S]; with ``glossy`` the C x C matrices
     M [n_glossy,C,C] of the glossy splats (in increasing index order). ``walk``: 0 = warp
@@ -154,7 +154,7 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
     if glossy:
         M = torch.empty((max(n_glossy, 1), C, C), dtype=torch.float32, device=dev)
     p = L.TransferParams(order, S, _ptr(dirs), float(t_min), float(same_surface_t), flags, int(index_buffer),
-                         _ptr(stats), int(n_bounces), int(walk))
+                         _ptr(stats), int(n_bounces), int(walk), int(packet_dirs))
     ws, nb = _ws(lib.prtgs_transfer_workspace_size(g.n, n_glossy, ctypes.byref(p)), dev)
     gs = g.struct()
     L.check(lib.prtgs_precompute_transfer(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(P), _ptr(T),
@@ -272,14 +272,24 @@ def camera_struct(cam) -> L.Camera:
 
 
 class RenderState:
-    def __init__(self, n, width, height, max_pairs, device="cuda"):
+    """Render state of one scene, or (n_scenes > 1) of the batched render of n_scenes scenes."""
+
+    def __init__(self, n, width, height, max_pairs, device="cuda", n_scenes: int = 1):
         lib = L.load()
         self.n, self.width, self.height, self.max_pairs = n, width, height, int(max_pairs)
-        nbytes = lib.prtgs_render_state_bytes(n, width, height, self.max_pairs)
-        self.buffer = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        self.n_scenes = int(n_scenes)
         self.s = L.RenderState()
-        L.check(lib.prtgs_render_state_init(_ptr(self.buffer), nbytes, n, width, height, self.max_pairs,
-                                            ctypes.byref(self.s)), "prtgs_render_state_init")
+        if self.n_scenes == 1:
+            nbytes = lib.prtgs_render_state_bytes(n, width, height, self.max_pairs)
+            self.buffer = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+            L.check(lib.prtgs_render_state_init(_ptr(self.buffer), nbytes, n, width, height, self.max_pairs,
+                                                ctypes.byref(self.s)), "prtgs_render_state_init")
+        else:
+            nbytes = lib.prtgs_render_state_bytes_batched(n, self.n_scenes, width, height, self.max_pairs)
+            self.buffer = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+            L.check(lib.prtgs_render_state_init_batched(_ptr(self.buffer), nbytes, n, self.n_scenes, width, height,
+                                                        self.max_pairs, ctypes.byref(self.s)),
+                    "prtgs_render_state_init_batched")
 
     def view(self, field, dtype, shape):
         off = getattr(self.s, field) - self.buffer.data_ptr()
@@ -374,6 +384,79 @@ def render_backward(g: GaussianTensors, colors, cam, bg, state: RenderState, dim
                                       _ptr(d_quats), _ptr(d_opacity), _ptr(d_colors), _ptr(ws), nb, _stream()),
             "prtgs_render_backward")
     return d_means, d_scales, d_quats, d_opacity, d_colors
+
+
+def camera_array(cams):
+    """Host array of prtgs_camera structs (the batched calls' per-scene cameras)."""
+    arr = (L.Camera * len(cams))()
+    for b, c in enumerate(cams):
+        arr[b] = camera_struct(c)
+    return arr
+
+
+def render_batched(g: GaussianTensors, scene_offsets: torch.Tensor, colors_flat: torch.Tensor, k: int, cams,
+                   bg: torch.Tensor, state: RenderState, status: Status | None = None, out=None):
+    """images [B,k,3,H,W] of B scenes in one launch per stage (Eq. 3-4); colors_flat in the
+    layout of relight_batched."""
+    lib = L.load()
+    B = len(cams)
+    W, H = int(cams[0].width), int(cams[0].height)
+    images = out if out is not None else torch.empty((B, k, 3, H, W), dtype=torch.float32, device=g.means.device)
+    ws, nb = _ws(lib.prtgs_render_batched_workspace_size(g.n, B, W, H, state.max_pairs), g.means.device)
+    gs = g.struct()
+    ca = camera_array(cams)
+    L.check(lib.prtgs_render_batched(ctypes.byref(gs), _ptr(scene_offsets), B, _ptr(colors_flat), k, ca, _ptr(bg),
+                                     _ptr(images), ctypes.byref(state.s), status.ptr() if status else None, _ptr(ws),
+                                     nb, _stream()), "prtgs_render_batched")
+    state._ws = ws
+    return images
+
+
+def render_backward_batched(g: GaussianTensors, scene_offsets, colors_flat, k, cams, bg, state: RenderState,
+                            dimages):
+    """Gradients of render_batched: d_means, d_scales, d_quats, d_opacity and d_colors (batched
+    colour layout)."""
+    lib = L.load()
+    dev = g.means.device
+    out = [torch.empty_like(g.means), torch.empty_like(g.scales), torch.empty_like(g.quats),
+           torch.empty_like(g.opacity), torch.empty_like(colors_flat)]
+    ws, nb = _ws(lib.prtgs_render_backward_batched_workspace_size(g.n, k), dev)
+    gs = g.struct()
+    ca = camera_array(cams)
+    L.check(lib.prtgs_render_backward_batched(ctypes.byref(gs), _ptr(scene_offsets), len(cams), _ptr(colors_flat), k,
+                                              ca, _ptr(bg), ctypes.byref(state.s), _ptr(dimages.contiguous()),
+                                              *(_ptr(t) for t in out), _ptr(ws), nb, _stream()),
+            "prtgs_render_backward_batched")
+    return tuple(out)
+
+
+def l2_loss_batched(images, targets):
+    """Per-scene L2 losses of images [B, ...] against targets: (losses [B], dimages)."""
+    lib = L.load()
+    B = int(images.shape[0])
+    count = images.numel() // B
+    losses = torch.empty(B, dtype=torch.float32, device=images.device)
+    dimages = torch.empty_like(images)
+    ws, nb = _ws(lib.prtgs_l2_loss_batched_workspace_size(count, B), images.device)
+    L.check(lib.prtgs_l2_loss_batched(_ptr(images), _ptr(targets), count, B, _ptr(losses), _ptr(dimages), _ptr(ws), nb,
+                                      _stream()), "prtgs_l2_loss_batched")
+    return losses, dimages
+
+
+def relight_backward_batched(T, albedo, scene_offsets, Lsh, order, dcolors_flat, need_dT=False):
+    """Backward of relight_batched: (d_albedo [n,3], dT or None, dL [B,k,3,C])."""
+    lib = L.load()
+    n = int(T.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    B, k = int(Lsh.shape[0]), int(Lsh.shape[1])
+    d_albedo = torch.empty_like(albedo)
+    dT = torch.empty_like(T) if need_dT else None
+    dL = torch.empty_like(Lsh)
+    ws, nb = _ws(lib.prtgs_relight_backward_batched_workspace_size(n, B, order, k), T.device)
+    L.check(lib.prtgs_relight_backward_batched(n, order, _ptr(T), tch, _ptr(albedo), _ptr(scene_offsets), B,
+                                               _ptr(Lsh), k, _ptr(dcolors_flat), _ptr(d_albedo), _ptr(dT), _ptr(dL),
+                                               _ptr(ws), nb, _stream()), "prtgs_relight_backward_batched")
+    return d_albedo, dT, dL
 
 
 def l2_loss(image, target):

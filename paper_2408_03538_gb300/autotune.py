@@ -1,14 +1,16 @@
-"""Launch-variant autotuner for libprtgs.
+"""Autotuner cache for libprtgs launch variants.
 
-Each tunable call has a few launch variants that give the same result (within the stated
-tolerances): the index-matrix candidate buffer of the transfer kernel (1/2/4/8 entries per
-search round), the relight path (FP32 CUDA cores or the FP32-accurate 3-term BF16 split on
-the tensor cores). The tuner times every variant on the actual inputs with CUDA events after
-a warm-up run, keeps the fastest, and caches the choice per (device, call, shape bucket) in a
-JSON file so later runs and CUDA-graph captures reuse it without timing.
+The timing itself is the library's: prtgs_autotune (C) runs every launch variant of a call on
+the caller's inputs with CUDA events and returns a JSON report. This module keeps those reports
+in a JSON file keyed by (device, call, shape bucket), so later runs and CUDA-graph captures reuse
+the choice without timing again:
+  * transfer: directions per packet work item (the walk's work tile: 32 receivers x packet_dirs
+    directions), 1..32;
+  * relight: FP32 CUDA cores or the FP32-accurate 3-term BF16 split on the tensor cores.
 """
 from __future__ import annotations
 
+import ctypes
 import json
 import math
 import os
@@ -53,52 +55,72 @@ def _key(call: str, **shape) -> str:
     return dev + "|" + call + "|" + ",".join(f"{k}={v}" for k, v in sorted(shape.items()))
 
 
-def time_variant(fn, repeats: int = 3) -> float:
-    """Mean device time of fn() in ms (after one untimed warm-up call)."""
-    fn()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(repeats):
-        fn()
-    e1.record()
-    e1.synchronize()
-    return e0.elapsed_time(e1) / repeats
+def _run(kernel_id: int, args, repeats: int) -> dict:
+    """prtgs_autotune on the current stream: the JSON report (with "best")."""
+    from . import _lib as L
+    from .api import _stream
+
+    lib = L.load()
+    best = ctypes.c_int32(-1)
+    buf = ctypes.create_string_buffer(4096)
+    L.check(lib.prtgs_autotune(kernel_id, ctypes.byref(args), repeats, _stream(), ctypes.byref(best), buf, 4096),
+            "prtgs_autotune")
+    rep = json.loads(buf.value.decode())
+    assert rep["best"] == best.value
+    return rep
 
 
-def choose(call: str, variants: dict, shape: dict, repeats: int = 3, force: bool = False):
-    """Return the fastest variant key (cached); ``variants`` maps key -> zero-argument callable."""
+def _cached(call: str, shape: dict, measure, force: bool):
     cache = _load()
     key = _key(call, **shape)
-    if not force and key in cache and cache[key]["best"] in {str(v) for v in variants}:
-        best = cache[key]["best"]
-        return next(v for v in variants if str(v) == best)
-    times = {str(v): time_variant(fn, repeats) for v, fn in variants.items()}
-    best = min(times, key=times.get)
-    cache[key] = {"best": best, "ms": times}
+    if not force and key in cache:
+        return cache[key]["best"]
+    rep = measure()
+    cache[key] = rep
     _store(cache)
-    return next(v for v in variants if str(v) == best)
+    return rep["best"]
 
 
-def tune_transfer(g, bvh, dirs, order, bounce: bool, repeats: int = 2, force: bool = False) -> int:
-    """Candidate-buffer size of the index-matrix search (only matters with bounce)."""
+def tune_transfer(g, bvh, dirs, order, bounce: bool, repeats: int = 1, force: bool = False) -> int:
+    """Directions per packet work item of the transfer walk for this shape."""
+    from . import _lib as L
     from . import api
 
-    if not bounce:
-        return 0
-    shape = dict(n=_bucket(g.n), S=int(dirs.shape[0]), order=order)
-    variants = {kb: (lambda kb=kb: api.precompute_transfer(g, bvh, dirs, order, bounce=True, index_buffer=kb))
-                for kb in (2, 4, 8)}
-    return choose("transfer_index_buffer", variants, shape, repeats, force)
+    S = int(dirs.shape[0])
+    C = (order + 1) ** 2
+    flags = L.SHADOW | (L.BOUNCE if bounce else 0)
+    shape = dict(n=_bucket(g.n), S=S, order=order, bounce=int(bounce))
+
+    def measure():
+        dev = g.means.device
+        P = torch.empty((g.n, C), dtype=torch.float32, device=dev)
+        T = torch.empty((g.n, 3, C), dtype=torch.float32, device=dev) if bounce else None
+        idx = torch.empty((g.n, S), dtype=torch.int32, device=dev) if bounce else None
+        p = L.TransferParams(order, S, api._ptr(dirs), float(api.DEFAULT_T_MIN), 1.0, flags, 0, None, 1, 0, 0)
+        lib = L.load()
+        ws, nb = api._ws(lib.prtgs_transfer_workspace_size(g.n, 0, ctypes.byref(p)), dev)
+        gs = g.struct()
+        args = L.TuneTransfer(ctypes.addressof(gs), ctypes.addressof(bvh.s), p, api._ptr(P), api._ptr(T),
+                              api._ptr(idx), None, 0, None, api._ptr(ws), nb)
+        return _run(L.TUNE_TRANSFER, args, repeats)
+
+    return int(_cached("transfer_packet_dirs", shape, measure, force))
 
 
 def tune_relight_batched(T, albedo, offsets, Lsh, order, repeats: int = 5, force: bool = False) -> int:
     """FP32 CUDA-core relight or the FP32-accurate BF16x3 tensor-core relight."""
-    from . import api
     from . import _lib as L
+    from . import api
 
-    variants = {L.PREC_FP32: lambda: api.relight_batched(T, albedo, offsets, Lsh, order, L.PREC_FP32)}
-    if T.dim() == 2 and 3 * Lsh.shape[1] <= 256:
-        variants[L.PREC_BF16X3] = lambda: api.relight_batched(T, albedo, offsets, Lsh, order, L.PREC_BF16X3)
-    shape = dict(n=_bucket(T.shape[0]), k=int(Lsh.shape[1]), order=order, scenes=int(Lsh.shape[0]))
-    return choose("relight_precision", variants, shape, repeats, force)
+    n = int(T.shape[0])
+    tch = 3 if T.dim() == 3 else 1
+    B, k = int(Lsh.shape[0]), int(Lsh.shape[1])
+    shape = dict(n=_bucket(n), k=k, order=order, scenes=B, t_channels=tch)
+
+    def measure():
+        colors = torch.empty(3 * k * n, dtype=torch.float32, device=T.device)
+        args = L.TuneRelight(n, order, tch, api._ptr(T), api._ptr(albedo), api._ptr(offsets), B, k, api._ptr(Lsh),
+                             api._ptr(colors), None)
+        return _run(L.TUNE_RELIGHT, args, repeats)
+
+    return int(_cached("relight_precision", shape, measure, force))

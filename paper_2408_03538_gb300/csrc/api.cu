@@ -6,6 +6,13 @@
 
 using namespace prtgs;
 
+namespace prtgs {
+std::atomic<unsigned long long>& launch_counter() {
+  static std::atomic<unsigned long long> c{0};
+  return c;
+}
+}  // namespace prtgs
+
 namespace {
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
@@ -42,6 +49,8 @@ int finish(int rc) {
 extern "C" {
 
 int prtgs_version(void) { return 10000; }
+
+unsigned long long prtgs_launch_count(void) { return launch_counter().load(std::memory_order_relaxed); }
 
 const char* prtgs_strerror(int code) {
   switch (code) {
@@ -122,7 +131,7 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
   if (p->n_bounces < 0 || p->n_bounces > 64) return PRTGS_ERR_INVALID_ARG;
-  if (p->walk < 0 || p->walk > 1) return PRTGS_ERR_INVALID_ARG;
+  if (p->walk < 0 || p->walk > 1 || p->packet_dirs < 0 || p->packet_dirs > 64) return PRTGS_ERR_INVALID_ARG;
   if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
   if (g->n == 0) return PRTGS_OK;
   if (!P || !g->normals) return PRTGS_ERR_INVALID_ARG;
@@ -269,7 +278,8 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
   if ((rc = check_order(sh_order))) return rc;
-  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (!st || st->n != g->n || st->n_scenes != 1 || st->width != cam->width || st->height != cam->height)
+    return PRTGS_ERR_SHAPE;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (n_glossy < 0 || n_glossy > g->n) return PRTGS_ERR_SHAPE;
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
@@ -294,7 +304,8 @@ int prtgs_render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, flo
   int rc = check_gaussians(g);
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
-  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (!st || st->n != g->n || st->n_scenes != 1 || st->width != cam->width || st->height != cam->height)
+    return PRTGS_ERR_SHAPE;
   if (!depth || !normal || (g->n > 0 && !g->normals)) return PRTGS_ERR_INVALID_ARG;
   rc = check_ws(workspace, workspace_bytes, render_geometry_workspace(g->n, cam->width, cam->height, st->max_pairs));
   if (rc) return rc;
@@ -307,7 +318,8 @@ int prtgs_render(const prtgs_gaussians* g, const float* colors, int32_t k, const
   int rc = check_gaussians(g);
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
-  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (!st || st->n != g->n || st->n_scenes != 1 || st->width != cam->width || st->height != cam->height)
+    return PRTGS_ERR_SHAPE;
   if (k < 1 || !bg || !image || (g->n > 0 && !colors)) return PRTGS_ERR_INVALID_ARG;
   rc = check_ws(workspace, workspace_bytes, render_workspace(g->n, cam->width, cam->height, st->max_pairs));
   if (rc) return rc;
@@ -326,7 +338,8 @@ int prtgs_render_backward(const prtgs_gaussians* g, const float* colors, int32_t
   int rc = check_gaussians(g);
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
-  if (!st || st->n != g->n || st->width != cam->width || st->height != cam->height) return PRTGS_ERR_SHAPE;
+  if (!st || st->n != g->n || st->n_scenes != 1 || st->width != cam->width || st->height != cam->height)
+    return PRTGS_ERR_SHAPE;
   if (k < 1 || !bg || !dimage) return PRTGS_ERR_INVALID_ARG;
   if (g->n == 0) return PRTGS_OK;
   if (!colors || !d_means || !d_scales || !d_quats || !d_opacity || !d_colors) return PRTGS_ERR_INVALID_ARG;
@@ -334,6 +347,162 @@ int prtgs_render_backward(const prtgs_gaussians* g, const float* colors, int32_t
   if (rc) return rc;
   return finish(render_backward(g, colors, k, cam, bg, st, dimage, d_means, d_scales, d_quats, d_opacity, d_colors,
                                 workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---- batched scenes: one launch per stage over every scene ----
+size_t prtgs_render_state_bytes_batched(int64_t n, int32_t n_scenes, int32_t width, int32_t height,
+                                        int64_t max_pairs) {
+  if (n < 0 || n_scenes < 1 || width <= 0 || height <= 0 || max_pairs < 0) return 0;
+  return render_state_bytes_batched(n, n_scenes, width, height, max_pairs);
+}
+
+int prtgs_render_state_init_batched(void* buffer, size_t bytes, int64_t n, int32_t n_scenes, int32_t width,
+                                    int32_t height, int64_t max_pairs, prtgs_render_state* out) {
+  if (!out || n < 0 || n_scenes < 1 || width <= 0 || height <= 0 || max_pairs < 0) return PRTGS_ERR_INVALID_ARG;
+  if (n_scenes > kMaxScenes || max_pairs >= (int64_t(1) << 32)) return PRTGS_ERR_UNSUPPORTED;
+  if (!buffer || !aligned256(buffer) || bytes < render_state_bytes_batched(n, n_scenes, width, height, max_pairs))
+    return PRTGS_ERR_WORKSPACE;
+  return render_state_layout_batched(buffer, n, n_scenes, width, height, max_pairs, out);
+}
+
+static int check_batch(const prtgs_gaussians* g, const int64_t* offsets, int32_t n_scenes, const prtgs_camera* cams,
+                       const prtgs_render_state* st) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (n_scenes < 1 || n_scenes > kMaxScenes) return PRTGS_ERR_UNSUPPORTED;
+  if (!offsets || !cams) return PRTGS_ERR_INVALID_ARG;
+  for (int b = 0; b < n_scenes; ++b) {
+    if ((rc = check_camera(cams + b))) return rc;
+    if (cams[b].width != cams[0].width || cams[b].height != cams[0].height) return PRTGS_ERR_SHAPE;
+  }
+  if (!st || st->n != g->n || st->n_scenes != n_scenes || st->width != cams[0].width ||
+      st->height != cams[0].height)
+    return PRTGS_ERR_SHAPE;
+  if ((int64_t)n_scenes * st->tiles_x * st->tiles_y >= (int64_t(1) << 31)) return PRTGS_ERR_UNSUPPORTED;
+  return PRTGS_OK;
+}
+
+size_t prtgs_render_batched_workspace_size(int64_t n, int32_t n_scenes, int32_t width, int32_t height,
+                                           int64_t max_pairs) {
+  if (n < 0 || n_scenes < 1 || width <= 0 || height <= 0 || max_pairs < 0) return 0;
+  return render_workspace(n, width, height, max_pairs);
+}
+
+int prtgs_render_batched(const prtgs_gaussians* g, const int64_t* scene_offsets, int32_t n_scenes,
+                         const float* colors, int32_t k, const prtgs_camera* cams, const float* bg, float* images,
+                         prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
+                         prtgs_stream_t stream) {
+  int rc = check_batch(g, scene_offsets, n_scenes, cams, st);
+  if (rc) return rc;
+  if (k < 1 || !bg || !images || (g->n > 0 && !colors)) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, render_workspace(g->n, cams[0].width, cams[0].height, st->max_pairs));
+  if (rc) return rc;
+  return finish(render_batched(g, scene_offsets, n_scenes, colors, k, cams, bg, images, st, status, workspace,
+                               reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_render_backward_batched_workspace_size(int64_t n, int32_t k) {
+  if (n < 0 || k < 1) return 0;
+  return render_backward_workspace(n, k);
+}
+
+int prtgs_render_backward_batched(const prtgs_gaussians* g, const int64_t* scene_offsets, int32_t n_scenes,
+                                  const float* colors, int32_t k, const prtgs_camera* cams, const float* bg,
+                                  const prtgs_render_state* st, const float* dimages, float* d_means, float* d_scales,
+                                  float* d_quats, float* d_opacity, float* d_colors, void* workspace,
+                                  size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_batch(g, scene_offsets, n_scenes, cams, st);
+  if (rc) return rc;
+  if (k < 1 || !bg || !dimages) return PRTGS_ERR_INVALID_ARG;
+  if (g->n == 0) return PRTGS_OK;
+  if (!colors || !d_means || !d_scales || !d_quats || !d_opacity || !d_colors) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, render_backward_workspace(g->n, k));
+  if (rc) return rc;
+  return finish(render_backward_batched(g, scene_offsets, n_scenes, colors, k, cams, bg, st, dimages, d_means,
+                                        d_scales, d_quats, d_opacity, d_colors, workspace,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_l2_loss_batched_workspace_size(int64_t count, int32_t n_scenes) {
+  return count > 0 && n_scenes > 0 ? l2_loss_batched_workspace(count, n_scenes) : 0;
+}
+
+int prtgs_l2_loss_batched(const float* images, const float* targets, int64_t count, int32_t n_scenes, float* losses,
+                          float* dimages, void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  if (count <= 0 || n_scenes < 1 || !images || !targets || !losses || !dimages) return PRTGS_ERR_INVALID_ARG;
+  if (n_scenes > 65535) return PRTGS_ERR_UNSUPPORTED;
+  int rc = check_ws(workspace, workspace_bytes, l2_loss_batched_workspace(count, n_scenes));
+  if (rc) return rc;
+  return finish(l2_loss_batched(images, targets, count, n_scenes, losses, dimages, workspace,
+                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_relight_backward_batched_workspace_size(int64_t n, int32_t n_scenes, int32_t sh_order, int32_t k) {
+  if (n < 0 || k < 0 || n_scenes < 1 || check_order(sh_order)) return 0;
+  return relight_backward_batched_workspace(n, n_scenes, sh_order, k);
+}
+
+int prtgs_relight_backward_batched(int64_t n, int32_t sh_order, const float* T, int32_t t_channels,
+                                   const float* albedo, const int64_t* scene_offsets, int32_t n_scenes, const float* L,
+                                   int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
+                                   void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc;
+  if (n < 0 || k < 0 || n_scenes < 1) return PRTGS_ERR_SHAPE;
+  if (n_scenes > 65535) return PRTGS_ERR_UNSUPPORTED;
+  if ((rc = check_order(sh_order))) return rc;
+  if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
+  if (k == 0) return PRTGS_OK;
+  if (!dL || !scene_offsets || (n > 0 && (!T || !albedo || !L || !dcolors || !d_albedo))) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, relight_backward_batched_workspace(n, n_scenes, sh_order, k));
+  if (rc) return rc;
+  return finish(relight_backward_batched(n, sh_order, T, t_channels, albedo, scene_offsets, n_scenes, L, k, dcolors,
+                                         d_albedo, dT, dL, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---- CUDA graph capture of a sequence of calls ----
+int prtgs_graph_begin(prtgs_stream_t stream) {
+  if (!stream) return PRTGS_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+  if (cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return PRTGS_ERR_CUDA;
+  }
+  return PRTGS_OK;
+}
+
+int prtgs_graph_end(prtgs_stream_t stream, prtgs_graph_t* out) {
+  if (!stream || !out) return PRTGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &graph) != cudaSuccess || !graph) {
+    (void)cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return PRTGS_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess || !exec) {
+    (void)cudaGetLastError();
+    return PRTGS_ERR_CUDA;
+  }
+  *out = reinterpret_cast<prtgs_graph_t>(exec);
+  return PRTGS_OK;
+}
+
+int prtgs_graph_launch(prtgs_graph_t graph, prtgs_stream_t stream) {
+  if (!graph) return PRTGS_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(reinterpret_cast<cudaGraphExec_t>(graph), reinterpret_cast<cudaStream_t>(stream)) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return PRTGS_ERR_CUDA;
+  }
+  return PRTGS_OK;
+}
+
+int prtgs_graph_destroy(prtgs_graph_t graph) {
+  if (!graph) return PRTGS_OK;
+  return cudaGraphExecDestroy(reinterpret_cast<cudaGraphExec_t>(graph)) == cudaSuccess ? PRTGS_OK : PRTGS_ERR_CUDA;
 }
 
 size_t prtgs_l2_loss_workspace_size(int64_t count) { return count > 0 ? l2_loss_workspace(count) : 0; }

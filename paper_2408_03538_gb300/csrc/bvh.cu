@@ -282,10 +282,10 @@ int build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* w
   uint32_t* counters = c.take<uint32_t>(ni);
   void* sort_ws = c.take<char>(radix_sort_workspace(n));
 
-  k_bounds_init<<<(6 * nsc + 255) / 256, 256, 0, stream>>>(bounds, nsc);
+  k_bounds_init<<<(6 * nsc + 255) / 256, 256, 0, counted(stream)>>>(bounds, nsc);
   int64_t nb = (n + kBoundsThreads * kBoundsItems - 1) / (kBoundsThreads * kBoundsItems);
-  k_bounds<<<(unsigned)nb, kBoundsThreads, 0, stream>>>(g->means, n, bvh->scene_offsets, nsc, bounds);
-  k_morton<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(g->means, n, bvh->scene_offsets, nsc, bounds, keys_x,
+  k_bounds<<<(unsigned)nb, kBoundsThreads, 0, counted(stream)>>>(g->means, n, bvh->scene_offsets, nsc, bounds);
+  k_morton<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(g->means, n, bvh->scene_offsets, nsc, bounds, keys_x,
                                                            vals_x);
   PRTGS_CHECK_LAUNCH();
   // the low 27 bits (index within the scene) are already in order: sort the code and scene bits
@@ -293,12 +293,12 @@ int build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* w
                             kSceneShift + scene_bits(nsc), sort_ws, stream);
   if (rc != PRTGS_OK) return rc;
   if (n > 1)
-    k_karras<<<(unsigned)((n - 1 + 255) / 256), 256, 0, stream>>>(bvh->keys, n, bvh->scene_offsets, nsc,
+    k_karras<<<(unsigned)((n - 1 + 255) / 256), 256, 0, counted(stream)>>>(bvh->keys, n, bvh->scene_offsets, nsc,
                                                                    bvh->nodes, bvh->leaf_parent, bvh->roots);
-  k_small_scene_roots<<<(nsc + 127) / 128, 128, 0, stream>>>(bvh->scene_offsets, nsc, n, bvh->roots,
+  k_small_scene_roots<<<(nsc + 127) / 128, 128, 0, counted(stream)>>>(bvh->scene_offsets, nsc, n, bvh->roots,
                                                               bvh->leaf_parent);
   cudaMemsetAsync(counters, 0, sizeof(uint32_t) * ni, stream);
-  k_pack_refit<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(g->means, g->scales, g->quats, g->opacity,
+  k_pack_refit<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(g->means, g->scales, g->quats, g->opacity,
                                                                g->normals, n, bvh->order, bvh->records, bvh->nodes,
                                                                bvh->leaf_parent, counters, status);
   PRTGS_CHECK_LAUNCH();

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/prtgs.h"
 
 #define PRTGS_CHECK_LAUNCH()                               \
@@ -15,6 +17,13 @@
   } while (0)
 
 namespace prtgs {
+
+// Kernel launches issued by the library (every launch passes its stream through counted()).
+std::atomic<unsigned long long>& launch_counter();
+inline cudaStream_t counted(cudaStream_t s) {
+  launch_counter().fetch_add(1ull, std::memory_order_relaxed);
+  return s;
+}
 
 constexpr int kMaxC = 16;           // SH coefficients for order <= 3
 constexpr int kStackDepth = 64;     // binary radix tree over 64-bit keys: depth <= 64

@@ -64,12 +64,30 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
                  unsigned tc_wait_polls, void* ws, cudaStream_t stream);
 
 size_t relight_backward_workspace(int64_t n, int32_t order, int32_t k);
+size_t relight_backward_batched_workspace(int64_t n, int32_t n_scenes, int32_t order, int32_t k);
+int relight_backward_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                             const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k,
+                             const float* dcolors, float* d_albedo, float* dT, float* dL, void* ws,
+                             cudaStream_t stream);
 int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
                      const float* L, int32_t k, const float* dcolors, float* d_albedo, float* dT, float* dL,
                      void* ws, cudaStream_t stream);
 
 // render.cu
 size_t render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+size_t render_state_bytes_batched(int64_t n, int32_t B, int32_t width, int32_t height, int64_t max_pairs);
+int render_state_layout_batched(void* buffer, int64_t n, int32_t B, int32_t width, int32_t height,
+                                int64_t max_pairs, prtgs_render_state* out);
+int render_batched(const prtgs_gaussians* g, const int64_t* offsets, int32_t B, const float* colors, int32_t k,
+                   const prtgs_camera* cams, const float* bg, float* images, prtgs_render_state* st, int32_t* status,
+                   void* ws, cudaStream_t stream);
+int render_backward_batched(const prtgs_gaussians* g, const int64_t* offsets, int32_t B, const float* colors,
+                            int32_t k, const prtgs_camera* cams, const float* bg, const prtgs_render_state* st,
+                            const float* dimages, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                            float* d_colors, void* ws, cudaStream_t stream);
+size_t l2_loss_batched_workspace(int64_t count, int32_t n_scenes);
+int l2_loss_batched(const float* images, const float* targets, int64_t count, int32_t n_scenes, float* losses,
+                    float* dimages, void* ws, cudaStream_t stream);
 int render_state_layout(void* buffer, int64_t n, int32_t width, int32_t height, int64_t max_pairs,
                         prtgs_render_state* out);
 size_t render_workspace(int64_t n, int32_t width, int32_t height, int64_t max_pairs);

@@ -579,13 +579,16 @@ static int launch_packet_t(const TraceArgs& a, float* V, int sms, cudaStream_t s
   const int warps = sms * (per_sm > 0 ? per_sm : 1) * kPacketWarps;
   // directions per work item: kPacketDirs, fewer when that would leave too few items per warp
   const int64_t n_packets = (a.r1 - a.r0 + 31) / 32;
-  int dpi = kPacketDirs;
-  while (dpi > 1 && n_packets * ((a.S + dpi - 1) / dpi) < 8 * (int64_t)warps) dpi >>= 1;
+  int dpi = a.packet_dirs;
+  if (dpi <= 0) {
+    dpi = kPacketDirs;
+    while (dpi > 1 && n_packets * ((a.S + dpi - 1) / dpi) < 8 * (int64_t)warps) dpi >>= 1;
+  }
   cudaMemsetAsync(a.work, 0, sizeof(unsigned int), stream);
-  k_packet<BOUNCE><<<sms * (per_sm > 0 ? per_sm : 1), kPacketThreads, smem, stream>>>(a, V, dpi);
+  k_packet<BOUNCE><<<sms * (per_sm > 0 ? per_sm : 1), kPacketThreads, smem, counted(stream)>>>(a, V, dpi);
   PRTGS_CHECK_LAUNCH();
   const int64_t batch = a.r1 - a.r0;
-  k_project<<<(unsigned)((batch + 127) / 128), 128, sizeof(float) * 3 * a.S, stream>>>(a, V);
+  k_project<<<(unsigned)((batch + 127) / 128), 128, sizeof(float) * 3 * a.S, counted(stream)>>>(a, V);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }

@@ -126,10 +126,10 @@ static void launch_relight_c(int64_t n, const float* T, int tch, const float* al
   unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
   if (tch == 3) {
     cudaFuncSetAttribute(k_relight<C, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_relight<C, 3><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
+    k_relight<C, 3><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, colors);
   } else {
     cudaFuncSetAttribute(k_relight<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_relight<C, 1><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, colors);
+    k_relight<C, 1><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, colors);
   }
 }
 
@@ -152,7 +152,7 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
       case 4:
       case 5:
       case 6:
-        k_relight_any<<<(unsigned)((n + kRelightThreads - 1) / kRelightThreads), kRelightThreads, 0, stream>>>(
+        k_relight_any<<<(unsigned)((n + kRelightThreads - 1) / kRelightThreads), kRelightThreads, 0, counted(stream)>>>(
             n, sh_count(order), t_channels, T, albedo, L, k, colors);
         break;
       default: return PRTGS_ERR_UNSUPPORTED;
@@ -164,11 +164,11 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
     size_t smem = sizeof(float) * k * 3 * C;
     unsigned grid = (unsigned)((n_glossy + kRelightThreads - 1) / kRelightThreads);
     switch (order) {
-      case 1: k_relight_glossy<1><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
+      case 1: k_relight_glossy<1><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
                                                                           albedo, L, k, colors); break;
-      case 2: k_relight_glossy<2><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
+      case 2: k_relight_glossy<2><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
                                                                           albedo, L, k, colors); break;
-      default: k_relight_glossy<3><<<grid, kRelightThreads, smem, stream>>>(n, n_glossy, glossy_ids, M, means,
+      default: k_relight_glossy<3><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means,
                                                                            cam_pos, albedo, L, k, colors); break;
     }
     PRTGS_CHECK_LAUNCH();
@@ -273,15 +273,15 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
   cudaMemsetAsync(zero, 0, sizeof(float) * 4, stream);
   if (n > 0) {
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    if (t_channels == 3) k_transfer_features<3><<<blocks, 256, 0, stream>>>(n, C, T, g->albedo, F);
-    else k_transfer_features<1><<<blocks, 256, 0, stream>>>(n, C, T, g->albedo, F);
+    if (t_channels == 3) k_transfer_features<3><<<blocks, 256, 0, counted(stream)>>>(n, C, T, g->albedo, F);
+    else k_transfer_features<1><<<blocks, 256, 0, counted(stream)>>>(n, C, T, g->albedo, F);
     if (n_glossy > 0) {
       const unsigned gb = (unsigned)((n_glossy + 255) / 256);
       const float px = cam->pos[0], py = cam->pos[1], pz = cam->pos[2];
       switch (order) {
-        case 1: k_glossy_features<1><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
-        case 2: k_glossy_features<2><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
-        default: k_glossy_features<3><<<gb, 256, 0, stream>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        case 1: k_glossy_features<1><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        case 2: k_glossy_features<2><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        default: k_glossy_features<3><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
       }
     }
     PRTGS_CHECK_LAUNCH();
@@ -294,9 +294,9 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
   const size_t smem = sizeof(float) * k * 3 * C;
   const unsigned blocks = (unsigned)((n_pix + kRelightThreads - 1) / kRelightThreads);
   switch (order) {
-    case 1: k_pixel_relight<4><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
-    case 2: k_pixel_relight<9><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
-    default: k_pixel_relight<16><<<blocks, kRelightThreads, smem, stream>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    case 1: k_pixel_relight<4><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    case 2: k_pixel_relight<9><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    default: k_pixel_relight<16><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
   }
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
@@ -346,9 +346,9 @@ static void launch_relight_batched_c(int64_t n, const float* T, int tch, const f
                                      cudaStream_t stream) {
   unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
   if (tch == 3)
-    k_relight_batched<C, 3><<<grid, kRelightThreads, 0, stream>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
+    k_relight_batched<C, 3><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
   else
-    k_relight_batched<C, 1><<<grid, kRelightThreads, 0, stream>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
+    k_relight_batched<C, 1><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offsets, n_scenes, L, k, colors);
 }
 
 int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
@@ -499,14 +499,185 @@ static void launch_relight_bwd(int64_t n, const float* T, int tch, const float* 
   unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
   int64_t nb = (n + kDLChunk - 1) / kDLChunk;
   if (tch == 3) {
-    k_relight_bwd_local<C, 3><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
-    k_relight_dL_partial<C, 3><<<(unsigned)nb, kRelightThreads, 0, stream>>>(n, T, albedo, k, dcol, partial);
+    k_relight_bwd_local<C, 3><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
+    k_relight_dL_partial<C, 3><<<(unsigned)nb, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, k, dcol, partial);
   } else {
-    k_relight_bwd_local<C, 1><<<grid, kRelightThreads, smem, stream>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
-    k_relight_dL_partial<C, 1><<<(unsigned)nb, kRelightThreads, 0, stream>>>(n, T, albedo, k, dcol, partial);
+    k_relight_bwd_local<C, 1><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
+    k_relight_dL_partial<C, 1><<<(unsigned)nb, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, k, dcol, partial);
   }
   int nout = k * 3 * C;
-  k_sum_partials<<<(nout + 255) / 256, 256, 0, stream>>>(partial, nb, nout, dL);
+  k_sum_partials<<<(nout + 255) / 256, 256, 0, counted(stream)>>>(partial, nb, nout, dL);
+}
+
+// ---- relight backward of many scenes (the layout of prtgs_relight_batched) -------------------
+// Scene b holds Gaussians offs[b] .. offs[b+1], lights L[b] ([k,3,C]) and the colour block
+// dcol + 3 k offs[b] ([k, n_b, 3]).
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_bwd_local_batched(
+    int64_t n, const float* __restrict__ T, const float* __restrict__ albedo, const int64_t* __restrict__ offs,
+    int B, const float* __restrict__ L, int k, const float* __restrict__ dcol, float* __restrict__ d_albedo,
+    float* __restrict__ dT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = find_scene(offs, B, i);
+  const int64_t o = offs[b], nb = offs[b + 1] - o;
+  const float* Lb = L + (int64_t)b * k * 3 * C;
+  const float* dc = dcol + 3 * (int64_t)k * o;
+  float t[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) t[c][m] = __ldg(T + (i * TCH + c) * C + m);
+  float rho[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) rho[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+  float da[3] = {0.f, 0.f, 0.f};
+  float gT[TCH][C];
+#pragma unroll
+  for (int c = 0; c < TCH; ++c)
+#pragma unroll
+    for (int m = 0; m < C; ++m) gT[c][m] = 0.f;
+  for (int l = 0; l < k; ++l) {
+    const float* Ll = Lb + l * 3 * C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float g = __ldg(dc + ((int64_t)l * nb + (i - o)) * 3 + c);
+      float dot = 0.f;
+#pragma unroll
+      for (int m = 0; m < C; ++m) {
+        const float lv = __ldg(Ll + c * C + m);
+        dot = fmaf(t[TCH > 1 ? c : 0][m], lv, dot);
+        gT[TCH > 1 ? c : 0][m] = fmaf(g * rho[c], lv, gT[TCH > 1 ? c : 0][m]);
+      }
+      da[c] = fmaf(g, dot, da[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d_albedo[3 * i + c] = da[c] * (1.0f / kPi);
+  if (dT) {
+#pragma unroll
+    for (int c = 0; c < TCH; ++c)
+#pragma unroll
+      for (int m = 0; m < C; ++m) dT[(i * TCH + c) * C + m] = gT[c][m];
+  }
+}
+
+// Partial sums of dL over chunk x of scene y (blockIdx), written to slot offs[y] / kDLChunk + y + x
+// (the slots of a scene are consecutive and disjoint from the other scenes').
+template <int C, int TCH>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_dL_partial_batched(
+    const int64_t* __restrict__ offs, const float* __restrict__ T, const float* __restrict__ albedo, int k,
+    const float* __restrict__ dcol, float* __restrict__ partial) {
+  __shared__ float sT[kDLBatch][TCH * C];
+  __shared__ float sW[kDLBatch][3 * 8];
+  const int b = blockIdx.y;
+  const int64_t o = offs[b], nb = offs[b + 1] - o;
+  const int64_t i0 = o + (int64_t)blockIdx.x * kDLChunk;
+  if ((int64_t)blockIdx.x * kDLChunk >= nb) return;  // uniform: past the scene's chunks
+  const int64_t i1 = min(o + nb, i0 + kDLChunk);
+  const float* dc = dcol + 3 * (int64_t)k * o;
+  const int outs_per_light = 3 * C;
+  const int64_t slot = o / kDLChunk + b + blockIdx.x;
+  for (int l0 = 0; l0 < k; l0 += 8) {
+    const int nl = min(8, k - l0);
+    const int nout = nl * outs_per_light;
+    float acc[2] = {0.f, 0.f};
+    for (int64_t bb = i0; bb < i1; bb += kDLBatch) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kDLBatch * TCH * C; e += blockDim.x) {
+        const int j = e / (TCH * C), r = e % (TCH * C);
+        const int64_t i = bb + j;
+        sT[j][r] = i < i1 ? T[i * TCH * C + r] : 0.f;
+      }
+      for (int e = threadIdx.x; e < kDLBatch * 3 * nl; e += blockDim.x) {
+        const int j = e / (3 * nl), r = e % (3 * nl);
+        const int l = r / 3, c = r % 3;
+        const int64_t i = bb + j;
+        sW[j][r] = i < i1 ? dc[((int64_t)(l0 + l) * nb + (i - o)) * 3 + c] * albedo[3 * i + c] * (1.0f / kPi) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int ot = threadIdx.x + q * kRelightThreads;
+        if (ot < nout) {
+          const int l = ot / outs_per_light, r = ot % outs_per_light;
+          const int c = r / C, m = r % C;
+          float a = acc[q];
+          for (int j = 0; j < kDLBatch; ++j) a = fmaf(sW[j][3 * l + c], sT[j][(TCH > 1 ? c : 0) * C + m], a);
+          acc[q] = a;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ot = threadIdx.x + q * kRelightThreads;
+      if (ot < nout) partial[slot * k * outs_per_light + (int64_t)l0 * outs_per_light + ot] = acc[q];
+    }
+  }
+}
+
+// dL[b] = the scene's partial sums in chunk order (compensated): deterministic.
+__global__ void k_sum_partials_batched(const float* __restrict__ partial, const int64_t* __restrict__ offs, int nout,
+                                       float* __restrict__ dL) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (o >= nout) return;
+  const int64_t nb = offs[b + 1] - offs[b];
+  const int64_t chunks = (nb + kDLChunk - 1) / kDLChunk;
+  const int64_t slot0 = offs[b] / kDLChunk + b;
+  float s = 0.f, c = 0.f;
+  for (int64_t x = 0; x < chunks; ++x) {
+    float t, e;
+    two_sum(s, partial[(slot0 + x) * nout + o], t, e);
+    s = t;
+    c += e;
+  }
+  dL[(int64_t)b * nout + o] = s + c;
+}
+
+size_t relight_backward_batched_workspace(int64_t n, int32_t n_scenes, int32_t order, int32_t k) {
+  const int64_t slots = n / kDLChunk + 2 * (int64_t)n_scenes + 1;
+  return align_up(sizeof(float) * (size_t)slots * k * 3 * sh_count(order));
+}
+
+template <int C>
+static void launch_relight_bwd_batched(int64_t n, const float* T, int tch, const float* albedo, const int64_t* offs,
+                                       int B, const float* L, int k, const float* dcol, float* d_albedo, float* dT,
+                                       float* dL, float* partial, cudaStream_t stream) {
+  const unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
+  const dim3 pgrid((unsigned)((n + kDLChunk - 1) / kDLChunk), (unsigned)B);
+  if (tch == 3) {
+    k_relight_bwd_local_batched<C, 3><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offs, B, L, k, dcol,
+                                                                            d_albedo, dT);
+    k_relight_dL_partial_batched<C, 3><<<pgrid, kRelightThreads, 0, counted(stream)>>>(offs, T, albedo, k, dcol, partial);
+  } else {
+    k_relight_bwd_local_batched<C, 1><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offs, B, L, k, dcol,
+                                                                            d_albedo, dT);
+    k_relight_dL_partial_batched<C, 1><<<pgrid, kRelightThreads, 0, counted(stream)>>>(offs, T, albedo, k, dcol, partial);
+  }
+  const int nout = k * 3 * C;
+  k_sum_partials_batched<<<dim3((unsigned)((nout + 255) / 256), (unsigned)B), 256, 0, counted(stream)>>>(partial, offs, nout,
+                                                                                                 dL);
+}
+
+int relight_backward_batched(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,
+                             const int64_t* offsets, int32_t n_scenes, const float* L, int32_t k,
+                             const float* dcolors, float* d_albedo, float* dT, float* dL, void* ws,
+                             cudaStream_t stream) {
+  if (k == 0) return PRTGS_OK;
+  if (n == 0) {
+    cudaMemsetAsync(dL, 0, sizeof(float) * n_scenes * k * 3 * sh_count(order), stream);
+    return PRTGS_OK;
+  }
+  float* partial = static_cast<float*>(ws);
+  switch (order) {
+    case 1: launch_relight_bwd_batched<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 2: launch_relight_bwd_batched<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 3: launch_relight_bwd_batched<16>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
+  }
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
 }
 
 int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo,

@@ -365,7 +365,7 @@ static void launch_tc(int grid, size_t smem, cudaStream_t stream, int64_t n, con
                       const float* L, int k, int n_pad, int slabs, int tmem_cols, const int64_t* offsets,
                       int n_scenes, float* colors, int32_t* status, unsigned wait_polls) {
   cudaFuncSetAttribute(k_relight_tc<C, TCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_relight_tc<C, TCH><<<grid, kTcThreads, smem, stream>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
+  k_relight_tc<C, TCH><<<grid, kTcThreads, smem, counted(stream)>>>(n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets,
                                                             n_scenes, colors, nullptr, status, wait_polls);
 }
 
@@ -409,7 +409,7 @@ int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float
   const int grid = (int)(tiles < want ? tiles : want);
 #define PRTGS_PIX_LAUNCH(CC)                                                                                     \
   cudaFuncSetAttribute(k_relight_tc<CC, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-  k_relight_tc<CC, 3, true><<<grid, kTcThreads, smem, stream>>>(n_pix, TI, final_T, L, k, n_pad, slabs, tmem_cols, \
+  k_relight_tc<CC, 3, true><<<grid, kTcThreads, smem, counted(stream)>>>(n_pix, TI, final_T, L, k, n_pad, slabs, tmem_cols, \
                                                                 nullptr, 1, image, bg, status, wait_polls)
   switch (order) {
     case 1: PRTGS_PIX_LAUNCH(4); break;

@@ -46,20 +46,61 @@ static Cam make_cam(const prtgs_camera* c) {
   return k;
 }
 
+// Where each Gaussian's camera, colours and image live. OneView: a single scene (colours
+// [k][n][3], image [k][3][H][W]). ManyViews: scene b holds Gaussians offs[b] .. offs[b+1], has its
+// own camera (every camera has the same image size), its colours are the [k][n_b][3] block at
+// 3 k offs[b] (the layout of prtgs_relight_batched) and its images the [k][3][H][W] block b. The
+// cameras travel by value in the kernel parameters (no device copy, graph-capturable).
+struct OneView {
+  Cam c;
+  __device__ __forceinline__ int scene_of(int64_t) const { return 0; }
+  __device__ __forceinline__ const Cam& cam(int) const { return c; }
+  __device__ __forceinline__ int64_t first(int) const { return 0; }
+  __device__ __forceinline__ int64_t count(int, int64_t n) const { return n; }
+};
+
+struct ManyViews {
+  Cam c[kMaxScenes];
+  const int64_t* offs;
+  int B;
+  __device__ __forceinline__ int scene_of(int64_t i) const { return find_scene(offs, B, i); }
+  __device__ __forceinline__ const Cam& cam(int b) const { return c[b]; }
+  __device__ __forceinline__ int64_t first(int b) const { return offs[b]; }
+  __device__ __forceinline__ int64_t count(int b, int64_t) const { return offs[b + 1] - offs[b]; }
+};
+
+// Colour of light l, channel ch of Gaussian g (in scene b).
+template <class V>
+__device__ __forceinline__ int64_t color_at(const V& v, int b, int64_t g, int l, int k, int64_t n) {
+  const int64_t o = v.first(b);
+  return 3 * (int64_t)k * o + ((int64_t)l * v.count(b, n) + (g - o)) * 3;
+}
+
 size_t render_state_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs) {
-  int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
-  int64_t px = (int64_t)width * height;
+  return render_state_bytes_batched(n, 1, width, height, max_pairs);
+}
+
+int render_state_layout(void* buffer, int64_t n, int32_t width, int32_t height, int64_t max_pairs,
+                        prtgs_render_state* out) {
+  return render_state_layout_batched(buffer, n, 1, width, height, max_pairs, out);
+}
+
+// B scenes of one image size: tile ranges, final transmittance and contributor counts per scene.
+size_t render_state_bytes_batched(int64_t n, int32_t B, int32_t width, int32_t height, int64_t max_pairs) {
+  int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile) * B;
+  int64_t px = (int64_t)width * height * B;
   return align_up(sizeof(float) * 2 * n) + align_up(sizeof(float) * 4 * n) + align_up(sizeof(float) * n) +
          align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + align_up(sizeof(uint64_t) * max_pairs) +
          align_up(sizeof(int32_t) * max_pairs) + align_up(sizeof(uint32_t) * 2 * tiles) +
          align_up(sizeof(float) * px) + align_up(sizeof(int32_t) * px) + align_up(sizeof(uint32_t));
 }
 
-int render_state_layout(void* buffer, int64_t n, int32_t width, int32_t height, int64_t max_pairs,
-                        prtgs_render_state* out) {
-  int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile);
-  int64_t px = (int64_t)width * height;
+int render_state_layout_batched(void* buffer, int64_t n, int32_t B, int32_t width, int32_t height,
+                                int64_t max_pairs, prtgs_render_state* out) {
+  int64_t tiles = (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile) * B;
+  int64_t px = (int64_t)width * height * B;
   Carver c(buffer);
+  out->n_scenes = B;
   out->n = n;
   out->max_pairs = max_pairs;
   out->width = width;
@@ -113,12 +154,14 @@ __device__ __forceinline__ void tile_rect(float mx, float my, int r, const Cam& 
   y1 = min(max((int)floorf((my + fr) / kTile) + 1, 0), c.gy);
 }
 
+template <class V>
 __global__ void k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict__ scales,
-                             const float* __restrict__ quats, const float* __restrict__ opacity, Cam c,
+                             const float* __restrict__ quats, const float* __restrict__ opacity, V v,
                              float* __restrict__ mean2d, float4* __restrict__ conic_op, float* __restrict__ depth,
                              int32_t* __restrict__ radius, uint32_t* __restrict__ touched) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const Cam& c = v.cam(v.scene_of(i));
   radius[i] = 0;
   touched[i] = 0;
   const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
@@ -168,7 +211,8 @@ __global__ void k_preprocess(int64_t n, const float* __restrict__ means, const f
   touched[i] = cnt;
 }
 
-__global__ void k_duplicate(int64_t n, Cam c, const float* __restrict__ mean2d, const float* __restrict__ depth,
+template <class V>
+__global__ void k_duplicate(int64_t n, V v, const float* __restrict__ mean2d, const float* __restrict__ depth,
                             const int32_t* __restrict__ radius, const uint32_t* __restrict__ incl,
                             int64_t max_pairs, uint64_t* __restrict__ keys, int32_t* __restrict__ ids,
                             int32_t* status) {
@@ -176,6 +220,9 @@ __global__ void k_duplicate(int64_t n, Cam c, const float* __restrict__ mean2d, 
   if (i >= n) return;
   const int r = radius[i];
   if (r <= 0) return;
+  const int b = v.scene_of(i);
+  const Cam& c = v.cam(b);
+  const uint64_t tile0 = (uint64_t)b * (uint64_t)(c.gx * c.gy);  // the scene's first tile
   int x0, y0, x1, y1;
   tile_rect(mean2d[2 * i], mean2d[2 * i + 1], r, c, x0, y0, x1, y1);
   const uint32_t end = incl[i];
@@ -185,7 +232,7 @@ __global__ void k_duplicate(int64_t n, Cam c, const float* __restrict__ mean2d, 
   for (int ty = y0; ty < y1; ++ty)
     for (int tx = x0; tx < x1; ++tx, ++p) {
       if (p >= max_pairs) return;
-      keys[p] = ((uint64_t)(ty * c.gx + tx) << 32) | dbits;
+      keys[p] = ((tile0 + (uint64_t)(ty * c.gx + tx)) << 32) | dbits;
       ids[p] = (int32_t)i;
     }
 }
@@ -205,8 +252,8 @@ __global__ void k_ranges(const uint64_t* __restrict__ keys, const uint32_t* __re
   if (p == n - 1 || (uint32_t)(keys[p + 1] >> 32) != tile) ranges[2 * tile + 1] = (uint32_t)(p + 1);
 }
 
-template <int KG>
-__global__ void __launch_bounds__(kTileThreads) k_composite(Cam c, const uint32_t* __restrict__ ranges,
+template <int KG, class V>
+__global__ void __launch_bounds__(kTileThreads) k_composite(V v, const uint32_t* __restrict__ ranges,
                                                             const int32_t* __restrict__ ids,
                                                             const float* __restrict__ mean2d,
                                                             const float4* __restrict__ conic_op,
@@ -216,13 +263,16 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(Cam c, const uint32_
   __shared__ float2 s_xy[kTileThreads];
   __shared__ float4 s_co[kTileThreads];
   __shared__ float s_col[kTileThreads][3 * KG];
-  const int tile = blockIdx.x;
+  const int gtile = blockIdx.x;  // scene-major tile index
+  const Cam& c = v.cam(0);
+  const int per_scene = c.gx * c.gy;
+  const int b = gtile / per_scene, tile = gtile % per_scene;
   const int l0 = blockIdx.y * KG;
   const int nl = min(KG, k - l0);
   const int tx = tile % c.gx, ty = tile / c.gx;
   const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
   const bool inside = px < c.W && py < c.H;
-  const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
   float T = 1.0f;
   float acc[KG][3];
 #pragma unroll
@@ -230,9 +280,9 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(Cam c, const uint32_
   bool done = !inside;
   uint32_t contributor = 0, last = 0;
   const float fpx = (float)px, fpy = (float)py;
-  for (uint32_t b = start; b < end; b += kTileThreads) {
+  for (uint32_t bt = start; bt < end; bt += kTileThreads) {
     if (__syncthreads_count(done) == kTileThreads) break;
-    uint32_t e = b + threadIdx.x;
+    uint32_t e = bt + threadIdx.x;
     if (e < end) {
       int g = ids[e];
       s_xy[threadIdx.x] = make_float2(mean2d[2 * g], mean2d[2 * g + 1]);
@@ -240,14 +290,14 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(Cam c, const uint32_
 #pragma unroll
       for (int l = 0; l < KG; ++l)
         if (l < nl) {
-          const float* cp = colors + ((int64_t)(l0 + l) * n + g) * 3;
+          const float* cp = colors + color_at(v, b, g, l0 + l, k, n);
           s_col[threadIdx.x][3 * l] = cp[0];
           s_col[threadIdx.x][3 * l + 1] = cp[1];
           s_col[threadIdx.x][3 * l + 2] = cp[2];
         }
     }
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kTileThreads, end - b);
+    const int cnt = (int)min((uint32_t)kTileThreads, end - bt);
     for (int j = 0; j < cnt && !done; ++j) {
       ++contributor;
       const float2 xy = s_xy[j];
@@ -274,24 +324,28 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(Cam c, const uint32_
     }
   }
   if (!inside) return;
-  const int64_t pix = (int64_t)py * c.W + px;
   const int64_t HW = (int64_t)c.W * c.H;
+  const int64_t pix = (int64_t)py * c.W + px;
   if (blockIdx.y == 0) {
-    final_T[pix] = T;
-    n_contrib[pix] = (int32_t)last;
+    final_T[b * HW + pix] = T;
+    n_contrib[b * HW + pix] = (int32_t)last;
   }
+  float* img = image + (int64_t)b * k * 3 * HW;
 #pragma unroll
   for (int l = 0; l < KG; ++l)
     if (l < nl)
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) image[((int64_t)(l0 + l) * 3 + ch) * HW + pix] = acc[l][ch] + T * bg[ch];
+      for (int ch = 0; ch < 3; ++ch) img[((int64_t)(l0 + l) * 3 + ch) * HW + pix] = acc[l][ch] + T * bg[ch];
 }
 
-int render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam, const float* bg,
-           float* image, prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream) {
+// Forward pass for B scenes of one image size (B = 1 with OneView): tiles are numbered
+// scene-major, so one sort and one composite launch cover every scene.
+template <class V>
+static int render_views(const prtgs_gaussians* g, const float* colors, int32_t k, const V& v, const Cam& c, int B,
+                        const float* bg, float* image, prtgs_render_state* st, int32_t* status, void* ws,
+                        cudaStream_t stream) {
   const int64_t n = g->n;
-  Cam c = make_cam(cam);
-  const int64_t tiles = (int64_t)c.gx * c.gy;
+  const int64_t tiles = (int64_t)c.gx * c.gy * B;
   Carver cv(ws);
   void* scan_ws = cv.take<char>(scan_workspace(n));
   uint64_t* keys_x = cv.take<uint64_t>(st->max_pairs);
@@ -302,48 +356,73 @@ int render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs
   cudaMemsetAsync(st->ranges, 0, sizeof(uint32_t) * 2 * tiles, stream);
   cudaMemsetAsync(st->n_pairs, 0, sizeof(uint32_t), stream);
   if (n > 0) {
-    k_preprocess<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
-        n, g->means, g->scales, g->quats, g->opacity, c, st->mean2d, reinterpret_cast<float4*>(st->conic_op),
+    k_preprocess<V><<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(
+        n, g->means, g->scales, g->quats, g->opacity, v, st->mean2d, reinterpret_cast<float4*>(st->conic_op),
         st->depth, st->radius, st->tiles_touched);
     PRTGS_CHECK_LAUNCH();
     int rc = scan_u32(st->tiles_touched, st->tiles_touched, n, false, st->n_pairs, scan_ws, stream);
     if (rc != PRTGS_OK) return rc;
-    k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, c, st->mean2d, st->depth, st->radius,
-                                                                st->tiles_touched, st->max_pairs, keys_x, ids_x,
-                                                                status);
-    k_clamp_count<<<1, 1, 0, stream>>>(st->n_pairs, st->max_pairs);
+    k_duplicate<V><<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, v, st->mean2d, st->depth, st->radius,
+                                                                   st->tiles_touched, st->max_pairs, keys_x, ids_x,
+                                                                   status);
+    k_clamp_count<<<1, 1, 0, counted(stream)>>>(st->n_pairs, st->max_pairs);
     PRTGS_CHECK_LAUNCH();
     int tile_bits = 0;
     while ((int64_t(1) << tile_bits) < tiles) ++tile_bits;
     rc = radix_sort_pairs(keys_x, ids_x, st->pair_keys, st->pair_ids, keys_y, ids_y, st->max_pairs, st->n_pairs, 0,
                           32 + tile_bits, sort_ws, stream);
     if (rc != PRTGS_OK) return rc;
-    k_ranges<<<(unsigned)((st->max_pairs + 255) / 256), 256, 0, stream>>>(st->pair_keys, st->n_pairs, tiles,
+    k_ranges<<<(unsigned)((st->max_pairs + 255) / 256), 256, 0, counted(stream)>>>(st->pair_keys, st->n_pairs, tiles,
                                                                             st->ranges);
     PRTGS_CHECK_LAUNCH();
   }
   const int kg = k <= 1 ? 1 : (k <= 4 ? 4 : 8);
   dim3 grid((unsigned)tiles, (unsigned)((k + kg - 1) / kg));
+  const float4* co = reinterpret_cast<const float4*>(st->conic_op);
   if (kg == 1)
-    k_composite<1><<<grid, kTileThreads, 0, stream>>>(c, st->ranges, st->pair_ids, st->mean2d,
-                                                      reinterpret_cast<const float4*>(st->conic_op), colors, n, k, bg,
-                                                      image, st->final_T, st->n_contrib);
+    k_composite<1, V><<<grid, kTileThreads, 0, counted(stream)>>>(v, st->ranges, st->pair_ids, st->mean2d, co, colors, n, k,
+                                                         bg, image, st->final_T, st->n_contrib);
   else if (kg == 4)
-    k_composite<4><<<grid, kTileThreads, 0, stream>>>(c, st->ranges, st->pair_ids, st->mean2d,
-                                                      reinterpret_cast<const float4*>(st->conic_op), colors, n, k, bg,
-                                                      image, st->final_T, st->n_contrib);
+    k_composite<4, V><<<grid, kTileThreads, 0, counted(stream)>>>(v, st->ranges, st->pair_ids, st->mean2d, co, colors, n, k,
+                                                         bg, image, st->final_T, st->n_contrib);
   else
-    k_composite<8><<<grid, kTileThreads, 0, stream>>>(c, st->ranges, st->pair_ids, st->mean2d,
-                                                      reinterpret_cast<const float4*>(st->conic_op), colors, n, k, bg,
-                                                      image, st->final_T, st->n_contrib);
+    k_composite<8, V><<<grid, kTileThreads, 0, counted(stream)>>>(v, st->ranges, st->pair_ids, st->mean2d, co, colors, n, k,
+                                                         bg, image, st->final_T, st->n_contrib);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }
 
+int render(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam, const float* bg,
+           float* image, prtgs_render_state* st, int32_t* status, void* ws, cudaStream_t stream) {
+  OneView v{make_cam(cam)};
+  return render_views(g, colors, k, v, v.c, 1, bg, image, st, status, ws, stream);
+}
+
+static int many_views(const prtgs_camera* cams, int32_t B, const int64_t* offsets, ManyViews& v) {
+  if (B < 1 || B > kMaxScenes) return PRTGS_ERR_UNSUPPORTED;
+  for (int b = 0; b < B; ++b) {
+    v.c[b] = make_cam(cams + b);
+    if (cams[b].width != cams[0].width || cams[b].height != cams[0].height) return PRTGS_ERR_SHAPE;
+  }
+  v.offs = offsets;
+  v.B = B;
+  return PRTGS_OK;
+}
+
+int render_batched(const prtgs_gaussians* g, const int64_t* offsets, int32_t B, const float* colors, int32_t k,
+                   const prtgs_camera* cams, const float* bg, float* images, prtgs_render_state* st, int32_t* status,
+                   void* ws, cudaStream_t stream) {
+  static_assert(sizeof(ManyViews) < 30000, "the cameras must fit the kernel parameter space");
+  ManyViews v;
+  const int rc = many_views(cams, B, offsets, v);
+  if (rc != PRTGS_OK) return rc;
+  return render_views(g, colors, k, v, v.c[0], B, bg, images, st, status, ws, stream);
+}
+
 // ---- backward ------------------------------------------------------------------------------
-template <int KG>
+template <int KG, class V>
 __global__ void __launch_bounds__(kTileThreads) k_composite_bwd(
-    Cam c, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ ids, const float* __restrict__ mean2d,
+    V v, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ ids, const float* __restrict__ mean2d,
     const float4* __restrict__ conic_op, const float* __restrict__ colors, int64_t n, int k,
     const float* __restrict__ bg, const float* __restrict__ final_T, const int32_t* __restrict__ n_contrib,
     const float* __restrict__ dimage, float* __restrict__ d_mean2d, float* __restrict__ d_conic,
@@ -354,26 +433,30 @@ __global__ void __launch_bounds__(kTileThreads) k_composite_bwd(
   __shared__ float s_col[kTileThreads][3 * KG];
   __shared__ int s_id[kTileThreads];
   __shared__ float s_acc[kTileThreads][NV];
-  const int tile = blockIdx.x;
+  const int gtile = blockIdx.x;  // scene-major tile index
+  const Cam& c = v.cam(0);
+  const int per_scene = c.gx * c.gy;
+  const int b = gtile / per_scene, tile = gtile % per_scene;
   const int l0 = blockIdx.y * KG;
   const int nl = min(KG, k - l0);
   const int tx = tile % c.gx, ty = tile / c.gx;
   const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
   const bool inside = px < c.W && py < c.H;
   const int lane = threadIdx.x & 31;
-  const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+  const uint32_t start = ranges[2 * gtile], end = ranges[2 * gtile + 1];
   const int64_t HW = (int64_t)c.W * c.H;
   const int64_t pix = (int64_t)py * c.W + px;
-  const float T_final = inside ? final_T[pix] : 0.f;
+  const float T_final = inside ? final_T[b * HW + pix] : 0.f;
   float T = T_final;
-  const uint32_t last = inside ? (uint32_t)n_contrib[pix] : 0u;
+  const uint32_t last = inside ? (uint32_t)n_contrib[b * HW + pix] : 0u;
+  const float* dimg = dimage + (int64_t)b * k * 3 * HW;
   float dpix[KG][3], accum[KG][3], last_col[KG][3];
   float bg_dot = 0.f;
 #pragma unroll
   for (int l = 0; l < KG; ++l)
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-      dpix[l][ch] = (inside && l < nl) ? dimage[((int64_t)(l0 + l) * 3 + ch) * HW + pix] : 0.f;
+      dpix[l][ch] = (inside && l < nl) ? dimg[((int64_t)(l0 + l) * 3 + ch) * HW + pix] : 0.f;
       accum[l][ch] = 0.f;
       last_col[l][ch] = 0.f;
       bg_dot += bg[ch] * dpix[l][ch];
@@ -396,7 +479,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite_bwd(
 #pragma unroll
         for (int l = 0; l < KG; ++l)
           if (l < nl) {
-            const float* cp = colors + ((int64_t)(l0 + l) * n + g) * 3;
+            const float* cp = colors + color_at(v, b, g, l0 + l, k, n);
             s_col[t][3 * l] = cp[0];
             s_col[t][3 * l + 1] = cp[1];
             s_col[t][3 * l + 2] = cp[2];
@@ -482,8 +565,8 @@ __global__ void __launch_bounds__(kTileThreads) k_composite_bwd(
           if (l < nl)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-              float v = a[6 + 3 * l + ch];
-              if (v != 0.f) atomicAdd(&d_colors[((int64_t)(l0 + l) * n + g) * 3 + ch], v);
+              const float gc = a[6 + 3 * l + ch];
+              if (gc != 0.f) atomicAdd(&d_colors[color_at(v, b, g, l0 + l, k, n) + ch], gc);
             }
       }
     }
@@ -491,13 +574,15 @@ __global__ void __launch_bounds__(kTileThreads) k_composite_bwd(
 }
 
 // 2D gradients -> means, scales, rotations (chain rule through Eq. 3 and Eq. 2).
+template <class V>
 __global__ void k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __restrict__ scales,
-                                 const float* __restrict__ quats, Cam c, const int32_t* __restrict__ radius,
+                                 const float* __restrict__ quats, V v, const int32_t* __restrict__ radius,
                                  const float* __restrict__ d_mean2d, const float* __restrict__ d_conic,
                                  float* __restrict__ d_means, float* __restrict__ d_scales,
                                  float* __restrict__ d_quats) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const Cam& c = v.cam(v.scene_of(i));
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   if (radius[i] > 0) {
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
@@ -653,7 +738,7 @@ int render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* de
   void* rws = static_cast<char*>(ws) + cv.off;
   cudaMemsetAsync(zero, 0, sizeof(float) * 4, stream);
   if (n > 0) {
-    k_geometry_features<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, make_cam(cam), g->means, g->normals, F);
+    k_geometry_features<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, make_cam(cam), g->means, g->normals, F);
     PRTGS_CHECK_LAUNCH();
   }
   const int rc = render(g, F, 2, cam, zero, img, st, status, rws, stream);
@@ -669,14 +754,14 @@ size_t render_backward_workspace(int64_t n, int32_t) {
   return align_up(sizeof(float) * 2 * n) + align_up(sizeof(float) * 3 * n);
 }
 
-int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
-                    const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,
-                    float* d_scales, float* d_quats, float* d_opacity, float* d_colors, void* ws,
-                    cudaStream_t stream) {
+template <class V>
+static int render_backward_views(const prtgs_gaussians* g, const float* colors, int32_t k, const V& v, const Cam& c,
+                                 int B, const float* bg, const prtgs_render_state* st, const float* dimage,
+                                 float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
+                                 void* ws, cudaStream_t stream) {
   const int64_t n = g->n;
   if (n == 0) return PRTGS_OK;
-  Cam c = make_cam(cam);
-  const int64_t tiles = (int64_t)c.gx * c.gy;
+  const int64_t tiles = (int64_t)c.gx * c.gy * B;
   Carver cv(ws);
   float* dm2 = cv.take<float>(2 * n);
   float* dcon = cv.take<float>(3 * n);
@@ -689,18 +774,39 @@ int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, co
   dim3 grid((unsigned)tiles, (unsigned)((k + kg - 1) / kg));
   const float4* co = reinterpret_cast<const float4*>(st->conic_op);
   if (kg == 1)
-    k_composite_bwd<1><<<grid, kTileThreads, 0, stream>>>(c, st->ranges, st->pair_ids, st->mean2d, co, colors, n, k,
-                                                          bg, st->final_T, st->n_contrib, dimage, dm2, dcon, d_opacity,
-                                                          d_colors);
+    k_composite_bwd<1, V><<<grid, kTileThreads, 0, counted(stream)>>>(v, st->ranges, st->pair_ids, st->mean2d, co, colors, n,
+                                                             k, bg, st->final_T, st->n_contrib, dimage, dm2, dcon,
+                                                             d_opacity, d_colors);
   else
-    k_composite_bwd<4><<<grid, kTileThreads, 0, stream>>>(c, st->ranges, st->pair_ids, st->mean2d, co, colors, n, k,
-                                                          bg, st->final_T, st->n_contrib, dimage, dm2, dcon, d_opacity,
-                                                          d_colors);
+    k_composite_bwd<4, V><<<grid, kTileThreads, 0, counted(stream)>>>(v, st->ranges, st->pair_ids, st->mean2d, co, colors, n,
+                                                             k, bg, st->final_T, st->n_contrib, dimage, dm2, dcon,
+                                                             d_opacity, d_colors);
   PRTGS_CHECK_LAUNCH();
-  k_preprocess_bwd<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, g->means, g->scales, g->quats, c, st->radius,
-                                                                   dm2, dcon, d_means, d_scales, d_quats);
+  k_preprocess_bwd<V><<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, g->means, g->scales, g->quats, v,
+                                                                      st->radius, dm2, dcon, d_means, d_scales,
+                                                                      d_quats);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
+}
+
+int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, const prtgs_camera* cam,
+                    const float* bg, const prtgs_render_state* st, const float* dimage, float* d_means,
+                    float* d_scales, float* d_quats, float* d_opacity, float* d_colors, void* ws,
+                    cudaStream_t stream) {
+  OneView v{make_cam(cam)};
+  return render_backward_views(g, colors, k, v, v.c, 1, bg, st, dimage, d_means, d_scales, d_quats, d_opacity,
+                               d_colors, ws, stream);
+}
+
+int render_backward_batched(const prtgs_gaussians* g, const int64_t* offsets, int32_t B, const float* colors,
+                            int32_t k, const prtgs_camera* cams, const float* bg, const prtgs_render_state* st,
+                            const float* dimages, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                            float* d_colors, void* ws, cudaStream_t stream) {
+  ManyViews v;
+  const int rc = many_views(cams, B, offsets, v);
+  if (rc != PRTGS_OK) return rc;
+  return render_backward_views(g, colors, k, v, v.c[0], B, bg, st, dimages, d_means, d_scales, d_quats, d_opacity,
+                               d_colors, ws, stream);
 }
 
 // ---- L2 loss ---------------------------------------------------------------------------------
@@ -743,6 +849,64 @@ __global__ void k_l2_final(const float* __restrict__ partial, int64_t nb, float 
   if (threadIdx.x == 0) *loss = (float)(sd[0] * (double)inv_count);
 }
 
+// Per-scene losses of B images of `count` elements each: loss[b] = mean over scene b, dimage =
+// 2 (image - target) / count. Blocks never straddle scenes (grid.y = scene).
+__global__ void k_l2_partial_batched(const float* __restrict__ a, const float* __restrict__ t, int64_t count,
+                                     float scale, float* __restrict__ grad, float* __restrict__ partial) {
+  __shared__ float sw[kLossThreads / 32];
+  const int64_t off = (int64_t)blockIdx.y * count;
+  const int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
+  float s = 0.f;
+  for (int q = 0; q < kLossItems; ++q) {
+    const int64_t i = base + (int64_t)q * kLossThreads + threadIdx.x;
+    if (i < count) {
+      const float d = a[off + i] - t[off + i];
+      grad[off + i] = scale * d;
+      s = fmaf(d, d, s);
+    }
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float u = 0.f;
+    for (int w = 0; w < kLossThreads / 32; ++w) u += sw[w];
+    partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = u;
+  }
+}
+
+__global__ void k_l2_final_batched(const float* __restrict__ partial, int64_t nb, float inv_count,
+                                   float* __restrict__ loss) {
+  __shared__ double sd[256];
+  const float* p = partial + (int64_t)blockIdx.x * nb;
+  double s = 0.0;
+  for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) s += (double)p[b];
+  sd[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) sd[threadIdx.x] += sd[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = (float)(sd[0] * (double)inv_count);
+}
+
+size_t l2_loss_batched_workspace(int64_t count, int32_t n_scenes) {
+  const int64_t nb = (count + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
+  return align_up(sizeof(float) * (size_t)(nb > 0 ? nb : 1) * (n_scenes > 0 ? n_scenes : 1));
+}
+
+int l2_loss_batched(const float* images, const float* targets, int64_t count, int32_t n_scenes, float* losses,
+                    float* dimages, void* ws, cudaStream_t stream) {
+  if (count <= 0 || n_scenes <= 0) return PRTGS_ERR_INVALID_ARG;
+  const int64_t nb = (count + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
+  float* partial = static_cast<float*>(ws);
+  k_l2_partial_batched<<<dim3((unsigned)nb, (unsigned)n_scenes), kLossThreads, 0, counted(stream)>>>(
+      images, targets, count, 2.0f / (float)count, dimages, partial);
+  k_l2_final_batched<<<(unsigned)n_scenes, 256, 0, counted(stream)>>>(partial, nb, 1.0f / (float)count, losses);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
 size_t l2_loss_workspace(int64_t count) {
   int64_t nb = (count + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
   return align_up(sizeof(float) * (size_t)(nb > 0 ? nb : 1));
@@ -753,8 +917,8 @@ int l2_loss(const float* image, const float* target, int64_t count, float* loss,
   if (count <= 0) return PRTGS_ERR_INVALID_ARG;
   int64_t nb = (count + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
   float* partial = static_cast<float*>(ws);
-  k_l2_partial<<<(unsigned)nb, kLossThreads, 0, stream>>>(image, target, count, 2.0f / (float)count, dimage, partial);
-  k_l2_final<<<1, 256, 0, stream>>>(partial, nb, 1.0f / (float)count, loss);
+  k_l2_partial<<<(unsigned)nb, kLossThreads, 0, counted(stream)>>>(image, target, count, 2.0f / (float)count, dimage, partial);
+  k_l2_final<<<1, 256, 0, counted(stream)>>>(partial, nb, 1.0f / (float)count, loss);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }

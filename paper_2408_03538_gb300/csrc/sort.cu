@@ -100,9 +100,9 @@ int scan_u32(const uint32_t* in, uint32_t* out, int64_t n, bool exclusive, uint3
   }
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   uint32_t* sums = static_cast<uint32_t*>(ws);
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, stream>>>(in, n, sums);
-  k_scan_block_sums<<<1, 1024, 0, stream>>>(sums, nb, total);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, stream>>>(in, out, n, sums, exclusive ? 1 : 0);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, counted(stream)>>>(in, n, sums);
+  k_scan_block_sums<<<1, 1024, 0, counted(stream)>>>(sums, nb, total);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, counted(stream)>>>(in, out, n, sums, exclusive ? 1 : 0);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }
@@ -217,10 +217,10 @@ int radix_sort_pairs(const uint64_t* keys_x, const int32_t* vals_x, uint64_t* ke
     uint64_t* kdst = to_f ? keys_f : keys_y;
     int32_t* vdst = to_f ? vals_f : vals_y;
     int shift = begin_bit + 8 * p;
-    k_radix_hist<<<tiles, kSortThreads, 0, stream>>>(ksrc, capacity, d_count, shift, tiles, hist);
+    k_radix_hist<<<tiles, kSortThreads, 0, counted(stream)>>>(ksrc, capacity, d_count, shift, tiles, hist);
     int rc = scan_u32(hist, hist, 256 * (int64_t)tiles, true, nullptr, scan_ws, stream);
     if (rc != PRTGS_OK) return rc;
-    k_radix_scatter<<<tiles, kSortThreads, 0, stream>>>(ksrc, vsrc, kdst, vdst, capacity, d_count, shift, tiles,
+    k_radix_scatter<<<tiles, kSortThreads, 0, counted(stream)>>>(ksrc, vsrc, kdst, vdst, capacity, d_count, shift, tiles,
                                                          hist);
     PRTGS_CHECK_LAUNCH();
     ksrc = kdst;

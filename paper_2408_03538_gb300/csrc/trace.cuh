@@ -59,6 +59,7 @@ struct TraceArgs {
   void* queue;                // [batch * S] per-ray candidate records, resolved by k_prefix / k_rounds
   uint32_t* pending;          // [batch * S] 1 = the ray has index-matrix candidates
   unsigned int* queue_count;
+  int packet_dirs;            // directions per packet work item (0: chosen from the problem size)
 };
 
 

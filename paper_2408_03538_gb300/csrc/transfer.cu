@@ -634,7 +634,7 @@ int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh
   int per_sm = 0;
   cudaFuncSetAttribute(k_trace_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bwd, kTraceThreads, smem);
-  k_trace_bwd<<<device_sms() * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a, g);
+  k_trace_bwd<<<device_sms() * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, counted(stream)>>>(a, g);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }
@@ -906,15 +906,15 @@ static int launch_trace(TraceArgs a, size_t smem, int sms, int64_t batch, uint32
     a.r0 = r0;
     a.r1 = r0 + batch < a.n ? r0 + batch : a.n;
     cudaMemsetAsync(a.work, 0, sizeof(unsigned int), stream);
-    k_trace<BOUNCE, KB><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, stream>>>(a);
+    k_trace<BOUNCE, KB><<<sms * (per_sm > 0 ? per_sm : 1), kTraceThreads, smem, counted(stream)>>>(a);
     if (BOUNCE) {
       const int64_t rays = (a.r1 - a.r0) * a.S;
       int rc = scan_u32(a.pending, incl, rays, false, a.queue_count, scan_ws, stream);
       if (rc != PRTGS_OK) return rc;
-      k_compact_pending<<<(unsigned)((rays + 255) / 256), 256, 0, stream>>>(rays, a.pending, incl, list);
+      k_compact_pending<<<(unsigned)((rays + 255) / 256), 256, 0, counted(stream)>>>(rays, a.pending, incl, list);
       cudaMemsetAsync(more_count, 0, sizeof(unsigned int), stream);
-      k_prefix<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, stream>>>(a, list, more, more_count);
-      k_rounds<KB><<<sms * (per_sm_r > 0 ? per_sm_r : 1), 128, 0, stream>>>(a, more, more_count);
+      k_prefix<KB><<<sms * (per_sm_b > 0 ? per_sm_b : 1), 128, 0, counted(stream)>>>(a, list, more, more_count);
+      k_rounds<KB><<<sms * (per_sm_r > 0 ? per_sm_r : 1), 128, 0, counted(stream)>>>(a, more, more_count);
     }
   }
   return PRTGS_OK;
@@ -967,10 +967,10 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
     void* sws = c.take<char>(scan_workspace(n));
     uint32_t* total = c.take<uint32_t>(1);
     Vg = c.take<float>((size_t)n_glossy * S);
-    k_mask_u32<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, g->glossy_mask, flags);
+    k_mask_u32<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, g->glossy_mask, flags);
     int rc = scan_u32(flags, flags, n, false, total, sws, stream);
     if (rc != PRTGS_OK) return rc;
-    k_glossy_slots<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, g->glossy_mask, flags, slot, gids);
+    k_glossy_slots<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, g->glossy_mask, flags, slot, gids);
   }
   TraceArgs a;
   a.nodes = reinterpret_cast<const float4*>(bvh->nodes);
@@ -985,7 +985,7 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.sh_order = p->sh_order;
   a.Ytab = ytab;
   if (ytab) {
-    k_sh_table<<<(unsigned)((S + 127) / 128), 128, 0, stream>>>(S, p->sh_order, p->dirs, ytab);
+    k_sh_table<<<(unsigned)((S + 127) / 128), 128, 0, counted(stream)>>>(S, p->sh_order, p->dirs, ytab);
     PRTGS_CHECK_LAUNCH();
   }
   a.t_min = p->t_min;
@@ -1003,6 +1003,7 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.queue = queue;
   a.pending = pending;
   a.queue_count = qcount;
+  a.packet_dirs = p->packet_dirs;
   size_t smem = trace_smem(S);
   int sms = device_sms();
   const int64_t batch = bounce ? trace_batch(n, S) : n;
@@ -1032,12 +1033,12 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
     const int nb = n_bounces_of(p);
     const unsigned blocks = (unsigned)((n + 7) / 8);
     float* cur = nb > 1 ? tb[0] : nullptr;
-    k_bounce<true><<<blocks, 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, nullptr, idx, T, cur,
+    k_bounce<true><<<blocks, 256, 0, counted(stream)>>>(n, C, S, p->dirs, g->normals, g->albedo, P, nullptr, idx, T, cur,
                                                status);
     for (int b = 2; b <= nb; ++b) {  // Eq. 34-35: each bounce gathers the previous one
       float* prev = cur;
       cur = b < nb ? tb[(b - 1) & 1] : nullptr;
-      k_bounce<false><<<blocks, 256, 0, stream>>>(n, C, S, p->dirs, g->normals, g->albedo, P, prev, idx, T, cur,
+      k_bounce<false><<<blocks, 256, 0, counted(stream)>>>(n, C, S, p->dirs, g->normals, g->albedo, P, prev, idx, T, cur,
                                                   status);
     }
     PRTGS_CHECK_LAUNCH();
@@ -1049,7 +1050,7 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_glossy, kGlossyThreads, gsm);
     int64_t blocks = (int64_t)sms * (gper > 0 ? gper : 1);
     if (blocks > n_glossy) blocks = n_glossy;
-    k_glossy<<<(unsigned)blocks, kGlossyThreads, gsm, stream>>>(n_glossy, gids, S, p->sh_order, p->dirs, g->normals,
+    k_glossy<<<(unsigned)blocks, kGlossyThreads, gsm, counted(stream)>>>(n_glossy, gids, S, p->sh_order, p->dirs, g->normals,
                                                                g->roughness, g->metallic, Vg, M);
     PRTGS_CHECK_LAUNCH();
   }

@@ -35,6 +35,10 @@ int main(void) {
   CHECK(prtgs_build_bvh(&g, &bvh, NULL, NULL, 0, NULL) == PRTGS_ERR_INVALID_ARG);
   CHECK(prtgs_precompute_transfer(&g, NULL, &p, NULL, NULL, NULL, NULL, 0, NULL, NULL, 0, NULL) ==
         PRTGS_ERR_INVALID_ARG);
+  /* struct layouts, compared with the binding's mirrors by the Python side */
+  printf("sizes %zu %zu %zu %zu %zu %zu %zu\n", sizeof(prtgs_gaussians), sizeof(prtgs_bvh),
+         sizeof(prtgs_transfer_params), sizeof(prtgs_camera), sizeof(prtgs_render_state), sizeof(prtgs_tune_transfer),
+         sizeof(prtgs_tune_relight));
   printf("ok\n");
   return 0;
 }

@@ -22,7 +22,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ("prtgs_build_bvh", "prtgs_precompute_transfer", "prtgs_relight", "prtgs_render",
-                     "prtgs_relight_backward", "prtgs_render_backward"):
+                     "prtgs_relight_backward", "prtgs_render_backward", "prtgs_relight_batched",
+                     "prtgs_render_batched", "prtgs_render_backward_batched", "prtgs_relight_backward_batched"):
         assert required in names
 
 
@@ -38,9 +39,23 @@ def test_struct_sizes_match_c_layout():
     # sizes implied by include/prtgs.h on LP64
     assert ctypes.sizeof(L.Gaussians) == 8 + 9 * 8
     assert ctypes.sizeof(L.BVH) == 8 + 4 + 4 + 7 * 8
-    assert ctypes.sizeof(L.TransferParams) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4  # n_bounces + tail padding
+    assert ctypes.sizeof(L.TransferParams) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 4  # + tail padding
     assert ctypes.sizeof(L.Camera) == 4 * (9 + 3 + 4) + 4 * 2 + 4 + 4 * 3
-    assert ctypes.sizeof(L.RenderState) == 8 + 8 + 4 * 4 + 11 * 8
+    assert ctypes.sizeof(L.RenderState) == 8 + 8 + 4 * 4 + 11 * 8 + 4 + 4  # n_scenes + tail padding
+
+
+def test_graph_and_autotune_argument_checks_without_gpu():
+    lib = L.load()
+    g = ctypes.c_void_p()
+    assert lib.prtgs_graph_begin(None) == L.ERR_INVALID_ARG  # the legacy default stream cannot be captured
+    assert lib.prtgs_graph_end(None, ctypes.byref(g)) == L.ERR_INVALID_ARG
+    assert lib.prtgs_graph_launch(None, None) == L.ERR_INVALID_ARG
+    assert lib.prtgs_graph_destroy(None) == L.OK
+    best = ctypes.c_int32(-1)
+    buf = ctypes.create_string_buffer(1024)
+    assert lib.prtgs_autotune(99, ctypes.byref(L.TuneRelight()), 1, None, ctypes.byref(best), buf, 1024) \
+        == L.ERR_INVALID_ARG
+    assert lib.prtgs_autotune(L.TUNE_RELIGHT, None, 1, None, ctypes.byref(best), buf, 1024) == L.ERR_INVALID_ARG
 
 
 def test_host_side_validation_without_gpu():

@@ -25,4 +25,10 @@ def test_header_compiles_as_c_and_links(tmp_path):
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr
-    assert out.stdout.strip() == "ok"
+    lines = out.stdout.strip().splitlines()
+    assert lines[-1] == "ok"
+    import ctypes
+
+    sizes = [int(x) for x in lines[0].split()[1:]]
+    assert sizes == [ctypes.sizeof(t) for t in (L.Gaussians, L.BVH, L.TransferParams, L.Camera, L.RenderState,
+                                                L.TuneTransfer, L.TuneRelight)]

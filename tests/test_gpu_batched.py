@@ -5,6 +5,7 @@ import pytest
 import torch
 
 import oracle
+from oracle import render as OR
 from paper_2408_03538_gb300 import api, autotune, batched, scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -57,26 +58,196 @@ def test_relight_batched_equals_per_scene(precision):
         assert err.max() < 1e-4
 
 
+def _batch_case(sizes, seed, k=3, W=96, H=64):
+    parts = _scenes(sizes, seed)
+    merged, offs = S.concat_scenes(parts)
+    rng = np.random.default_rng(seed)
+    cams = [S.look_at_camera((0.3 * b - 0.5, -3.5, 1.0 + 0.2 * b), (0, 0, 0), 50, W, H) for b in range(len(sizes))]
+    colors = rng.uniform(0, 1, 3 * k * merged.n).astype(np.float32)  # [k, n_b, 3] blocks per scene
+    return parts, merged, offs, cams, colors
+
+
+def test_render_batched_forward_and_backward_equal_per_scene():
+    """One launch per stage over every scene (ragged sizes, an empty and a one-Gaussian scene,
+    per-scene cameras) equals the single-scene calls scene by scene."""
+    sizes = [1500, 0, 1, 800, 2600]
+    k = 3
+    parts, merged, offs, cams, colors = _batch_case(sizes, 31, k)
+    g = api.GaussianTensors.from_scene(merged)
+    offs_d = torch.from_numpy(offs).cuda()
+    bg = torch.tensor([0.1, 0.2, 0.3], device="cuda")
+    st = api.Status()
+    state = api.RenderState(g.n, cams[0].width, cams[0].height, 2_000_000, n_scenes=len(sizes))
+    col_d = torch.from_numpy(colors).cuda()
+    images = api.render_batched(g, offs_d, col_d, k, cams, bg, state, status=st)
+    rng = np.random.default_rng(5)
+    dimg = torch.from_numpy(rng.standard_normal(tuple(images.shape)).astype(np.float32)).cuda()
+    dm, ds, dq, do, dcol = api.render_backward_batched(g, offs_d, col_d, k, cams, bg, state, dimg)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    for b, sc in enumerate(parts):
+        o0, o1 = int(offs[b]), int(offs[b + 1])
+        gb = api.GaussianTensors.from_scene(sc)
+        cb = torch.from_numpy(colors[3 * k * o0:3 * k * o1].reshape(k, o1 - o0, 3)).cuda().contiguous()
+        img, stb = api.render(gb, cb, cams[b], bg, max_pairs=2_000_000)
+        torch.testing.assert_close(images[b], img, rtol=0, atol=1e-6)
+        if sc.n == 0:
+            continue
+        ref = api.render_backward(gb, cb, cams[b], bg, stb, dimg[b].contiguous())
+        got = (dm[o0:o1], ds[o0:o1], dq[o0:o1], do[o0:o1], dcol[3 * k * o0:3 * k * o1].view(k, o1 - o0, 3))
+        for x, y in zip(got, ref):
+            torch.testing.assert_close(x, y, rtol=1e-4, atol=1e-6)
+    assert float(images.std()) > 1e-3
+    # and one scene against the FP64 oracle
+    b = 3
+    o0, o1 = int(offs[b]), int(offs[b + 1])
+    t = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    cref = colors[3 * k * o0:3 * k * o1].reshape(k, o1 - o0, 3)
+    ref = OR.render(t(parts[b].means), t(parts[b].scales), t(parts[b].quats), t(parts[b].opacity), t(cref), cams[b],
+                    (0.1, 0.2, 0.3)).numpy()
+    assert OR.psnr(images[b].cpu().numpy(), ref, peak=1.0) >= 50.0
+
+
+def test_relight_backward_and_loss_batched_equal_per_scene():
+    rng = np.random.default_rng(7)
+    sizes = [129, 1000, 1, 2100, 0, 64]
+    offs = np.zeros(len(sizes) + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    n, C, k = int(offs[-1]), 16, 8
+    for tch in (1, 3):
+        T = torch.from_numpy(rng.standard_normal((n, C) if tch == 1 else (n, 3, C)).astype(np.float32)).cuda()
+        alb = torch.from_numpy(rng.uniform(0, 1, (n, 3)).astype(np.float32)).cuda()
+        Lsh = torch.from_numpy(rng.standard_normal((len(sizes), k, 3, C)).astype(np.float32)).cuda()
+        dcol = torch.from_numpy(rng.standard_normal(3 * k * n).astype(np.float32)).cuda()
+        da, dT, dL = api.relight_backward_batched(T, alb, torch.from_numpy(offs).cuda(), Lsh, 3, dcol, need_dT=True)
+        for b in range(len(sizes)):
+            o0, o1 = int(offs[b]), int(offs[b + 1])
+            if o1 == o0:
+                assert float(dL[b].abs().max()) == 0.0
+                continue
+            db = dcol[3 * k * o0:3 * k * o1].view(k, o1 - o0, 3).contiguous()
+            ra, rT, rL = api.relight_backward(T[o0:o1].contiguous(), alb[o0:o1].contiguous(), Lsh[b].contiguous(), 3,
+                                              db, need_dT=True)
+            torch.testing.assert_close(da[o0:o1], ra, rtol=1e-6, atol=1e-6)
+            torch.testing.assert_close(dT[o0:o1], rT, rtol=1e-6, atol=1e-6)
+            torch.testing.assert_close(dL[b], rL, rtol=1e-5, atol=1e-5)
+    imgs = torch.from_numpy(rng.uniform(0, 1, (4, 2, 3, 20, 30)).astype(np.float32)).cuda()
+    tgts = torch.from_numpy(rng.uniform(0, 1, (4, 2, 3, 20, 30)).astype(np.float32)).cuda()
+    losses, dimg = api.l2_loss_batched(imgs, tgts)
+    for b in range(4):
+        lb, db = api.l2_loss(imgs[b].contiguous(), tgts[b].contiguous())
+        torch.testing.assert_close(losses[b:b + 1], lb, rtol=1e-6, atol=0)
+        torch.testing.assert_close(dimg[b], db, rtol=0, atol=0)
+
+
+def test_graph_capture_through_the_c_abi_replays_the_calls():
+    """prtgs_graph_begin / _end / _launch around BVH build, transfer, batched relight and batched
+    render (preallocated buffers and workspaces): the replay reproduces the eager outputs."""
+    import ctypes
+
+    from paper_2408_03538_gb300 import _lib as L
+
+    lib = L.load()
+    sizes = [900, 400, 1300]
+    k = 2
+    parts, merged, offs, cams, _ = _batch_case(sizes, 41, k)
+    g = api.GaussianTensors.from_scene(merged)
+    offs_d = torch.from_numpy(offs).cuda()
+    dirs = torch.from_numpy(S.direction_set(64, 8)).cuda()
+    Lsh = torch.from_numpy(np.stack([S.env_lights(k, 3, 60 + b) for b in range(len(sizes))])).cuda()
+    bg = torch.zeros(3, device="cuda")
+    n, C = g.n, 16
+    P = torch.empty((n, C), device="cuda")
+    colors = torch.empty(3 * k * n, device="cuda")
+    state = api.RenderState(n, cams[0].width, cams[0].height, 1_000_000, n_scenes=len(sizes))
+    images = torch.empty((len(sizes), k, 3, cams[0].height, cams[0].width), device="cuda")
+    bvh = api.Bvh(n, offs_d)
+    p = L.TransferParams(3, 64, api._ptr(dirs), float(api.DEFAULT_T_MIN), 1.0, L.SHADOW, 0, None, 1, 0, 0)
+    ws_b, nb_b = api._ws(lib.prtgs_build_bvh_workspace_size(n, len(sizes)), "cuda")
+    ws_t, nb_t = api._ws(lib.prtgs_transfer_workspace_size(n, 0, ctypes.byref(p)), "cuda")
+    ws_r, nb_r = api._ws(lib.prtgs_render_batched_workspace_size(n, len(sizes), cams[0].width, cams[0].height,
+                                                                 state.max_pairs), "cuda")
+    gs = g.struct()
+    ca = api.camera_array(cams)
+    stream = torch.cuda.Stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def calls():
+        assert lib.prtgs_build_bvh(ctypes.byref(gs), ctypes.byref(bvh.s), None, api._ptr(ws_b), nb_b, sp) == 0
+        assert lib.prtgs_precompute_transfer(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), api._ptr(P), None,
+                                             None, None, 0, None, api._ptr(ws_t), nb_t, sp) == 0
+        assert lib.prtgs_relight_batched(n, 3, api._ptr(P), 1, api._ptr(g.albedo), api._ptr(offs_d), len(sizes),
+                                         api._ptr(Lsh), k, L.PREC_BF16X3, api._ptr(colors), None, L.TC_WAIT_POLLS,
+                                         sp) == 0
+        assert lib.prtgs_render_batched(ctypes.byref(gs), api._ptr(offs_d), len(sizes), api._ptr(colors), k, ca,
+                                        api._ptr(bg), api._ptr(images), ctypes.byref(state.s), None, api._ptr(ws_r),
+                                        nb_r, sp) == 0
+
+    torch.cuda.synchronize()
+    calls()  # eager, on the side stream
+    stream.synchronize()
+    eager = (P.clone(), images.clone())
+    graph = ctypes.c_void_p()
+    assert lib.prtgs_graph_begin(sp) == 0
+    calls()
+    assert lib.prtgs_graph_end(sp, ctypes.byref(graph)) == 0
+    P.zero_()
+    images.fill_(-1.0)
+    torch.cuda.synchronize()
+    assert lib.prtgs_graph_launch(graph, sp) == 0
+    stream.synchronize()
+    torch.testing.assert_close(P, eager[0], rtol=0, atol=0)
+    torch.testing.assert_close(images, eager[1], rtol=0, atol=0)
+    assert lib.prtgs_graph_destroy(graph) == 0
+    assert float(images.abs().sum()) > 0
+
+
+def test_autotune_reports_every_variant_and_the_choice_keeps_results(tmp_path, monkeypatch):
+    monkeypatch.setenv("PRTGS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    import json
+
+    sc = S.surface_scene(3000, 23)
+    g = api.GaussianTensors.from_scene(sc)
+    bvh = api.build_bvh(g)
+    dirs = torch.from_numpy(S.direction_set(64, 9)).cuda()
+    best = autotune.tune_transfer(g, bvh, dirs, 3, True)
+    assert best in (1, 2, 4, 8, 16, 32)
+    rep = next(iter(json.load(open(tmp_path / "tune.json")).values()))
+    assert set(rep["ms"]) == {"1", "2", "4", "8", "16", "32"} and all(v > 0 for v in rep["ms"].values())
+    a = api.precompute_transfer(g, bvh, dirs, 3, bounce=True)
+    b = api.precompute_transfer(g, bvh, dirs, 3, bounce=True, packet_dirs=best)
+    torch.testing.assert_close(a["T"], b["T"], rtol=0, atol=0)
+    torch.testing.assert_close(a["idx"], b["idx"], rtol=0, atol=0)
+    assert autotune.tune_transfer(g, bvh, dirs, 3, True) == best  # from the cache
+
+
 def test_graph_replay_matches_eager_and_autotuner_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("PRTGS_TUNE_CACHE", str(tmp_path / "tune.json"))
     sizes = [2000, 500, 4000]
     parts = _scenes(sizes, 9)
     lights = np.stack([S.env_lights(4, 3, 50 + b) for b in range(len(sizes))])
-    cams = [S.look_at_camera((0, -3.5, 1.5), (0, 0, 0), 50, 160, 96) for _ in sizes]
-    pipe = batched.BatchedPipeline(parts, S.direction_set(64, 4), 3, lights, cams)
+    cams = [S.look_at_camera((0.2 * b, -3.5, 1.5), (0, 0, 0), 50, 160, 96) for b in range(len(sizes))]
+    pipe = batched.BatchedPipeline(parts, S.direction_set(64, 4), 3, lights, cams, bounce=True)
     assert (tmp_path / "tune.json").exists()
     eager = pipe.step()
-    imgs = [im.clone() for im in pipe.images]
-    dL = [d.clone() for d in eager["dL"]]
-    g_means = [g[0].clone() for g in eager["grads"]]
+    imgs = pipe.images.clone()
+    dL = eager["dL"].clone()
+    g_means = eager["grads"][0].clone()
+    losses = eager["losses"].clone()
     pipe.capture()
     # perturb the outputs, replay, and compare with the eager pass
-    for im in pipe.images:
-        im.fill_(-1)
+    pipe.images.fill_(-1)
     cap = pipe.replay()
     torch.cuda.synchronize()
-    for b in range(len(sizes)):
-        torch.testing.assert_close(pipe.images[b], imgs[b], rtol=0, atol=1e-6)
-        torch.testing.assert_close(cap["dL"][b], dL[b], rtol=1e-4, atol=1e-6)
-        torch.testing.assert_close(cap["grads"][b][0], g_means[b], rtol=1e-3, atol=1e-6)
-    assert all(float(im.abs().sum()) > 0 for im in imgs)
+    torch.testing.assert_close(pipe.images, imgs, rtol=0, atol=1e-6)
+    torch.testing.assert_close(cap["dL"], dL, rtol=1e-4, atol=1e-6)
+    torch.testing.assert_close(cap["grads"][0], g_means, rtol=1e-3, atol=1e-6)
+    torch.testing.assert_close(cap["losses"], losses, rtol=1e-6, atol=0)
+    assert float(imgs.abs().sum()) > 0
+    # the batched step equals the per-scene calls: scene 1's image
+    T = pipe.T
+    o0, o1 = int(pipe.offs_h[1]), int(pipe.offs_h[2])
+    gb = pipe.scene(1)
+    col = api.relight(T[o0:o1].contiguous(), gb.albedo, pipe.L[1].contiguous(), 3, precision=pipe.precision)
+    img1, _ = api.render(gb, col, cams[1], pipe.bg, max_pairs=2_000_000)
+    torch.testing.assert_close(imgs[1], img1, rtol=0, atol=1e-5)
