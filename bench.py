@@ -623,7 +623,8 @@ def run_batched(args):
     def per_scene_step():
         for b, gb in enumerate(gts):
             bvh = api.build_bvh(gb)
-            P = api.precompute_transfer(gb, bvh, pipe.dirs, w["order"], packet_dirs=pipe.packet_dirs)["P"]
+            P = api.precompute_transfer(gb, bvh, pipe.dirs, w["order"], packet_dirs=pipe.packet_dirs,
+                                        walk=pipe.walk)["P"]
             col = api.relight(P, gb.albedo, pipe.L[b], w["order"], precision=pipe.precision)
             img, _ = api.render(gb, col, cams[b], pipe.bg, state=states[b])
             loss, dimg = api.l2_loss(img, tgt[b])
@@ -650,7 +651,8 @@ def run_batched(args):
                        "sizes_min_max": [min(p.n for p in parts), max(p.n for p in parts)], "sh_order": w["order"],
                        "n_dirs": int(dirs.shape[0]), "lights_per_scene": w["lights"],
                        "image": f"{cams[0].width}x{cams[0].height}", "relight": "tcgen05 BF16x3",
-                       "packet_dirs": int(pipe.packet_dirs), "l2": "flushed between steps (256 MB write)"},
+                       "transfer_walk": "per-ray" if pipe.walk else f"packets of {pipe.packet_dirs} directions",
+                       "l2": "flushed between steps (256 MB write)"},
             "frames_per_s": frames * args.steps / (graph_ms / 1e3),
             "eager_ms_per_step": eager_ms / args.steps, "graph_ms_per_step": graph_ms / args.steps,
             "per_scene_calls_ms_per_step": per_scene_ms,

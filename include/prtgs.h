@@ -466,7 +466,10 @@ int prtgs_relight_backward_batched(int64_t n, int32_t sh_order, const float* T, 
  * json_bytes >= 512 suggested; PRTGS_ERR_INVALID_ARG if it does not fit):
  *   {"kernel": ..., "variant": ..., "shape": {...}, "ms": {"<variant>": <mean ms>, ...}, "best": ...}
  *   PRTGS_TUNE_TRANSFER   args: prtgs_tune_transfer (the arguments of prtgs_precompute_transfer);
- *                         variant: packet_dirs in {1, 2, 4, 8, 16, 32}
+ *                         variant: the packet walk with packet_dirs in {1, 2, 4, 8, 16, 32}, or
+ *                         the per-ray walk, reported as packet_dirs 0 (use walk = 1 then); the
+ *                         workspace must hold both walks' (the larger prtgs_transfer_workspace_size
+ *                         of walk 0 and walk 1)
  *   PRTGS_TUNE_RELIGHT    args: prtgs_tune_relight (the arguments of prtgs_relight_batched; one
  *                         scene is scene_offsets {0, n}); variant: precision among the
  *                         FP32-accurate ones, PRTGS_PREC_FP32 and (when the shape fits the tensor

@@ -4,8 +4,8 @@ The timing itself is the library's: prtgs_autotune (C) runs every launch variant
 the caller's inputs with CUDA events and returns a JSON report. This module keeps those reports
 in a JSON file keyed by (device, call, shape bucket), so later runs and CUDA-graph captures reuse
 the choice without timing again:
-  * transfer: directions per packet work item (the walk's work tile: 32 receivers x packet_dirs
-    directions), 1..32;
+  * transfer: the warp-packet walk with its directions per work item (the work tile: 32
+    receivers x packet_dirs directions), 1..32, or the per-ray walk (reported as 0);
   * relight: FP32 CUDA cores or the FP32-accurate 3-term BF16 split on the tensor cores.
 """
 from __future__ import annotations
@@ -82,7 +82,8 @@ def _cached(call: str, shape: dict, measure, force: bool):
 
 
 def tune_transfer(g, bvh, dirs, order, bounce: bool, repeats: int = 1, force: bool = False) -> int:
-    """Directions per packet work item of the transfer walk for this shape."""
+    """The fastest transfer walk for this shape: packet_dirs of the packet walk, or 0 for the
+    per-ray walk (walk=1)."""
     from . import _lib as L
     from . import api
 
@@ -96,9 +97,12 @@ def tune_transfer(g, bvh, dirs, order, bounce: bool, repeats: int = 1, force: bo
         P = torch.empty((g.n, C), dtype=torch.float32, device=dev)
         T = torch.empty((g.n, 3, C), dtype=torch.float32, device=dev) if bounce else None
         idx = torch.empty((g.n, S), dtype=torch.int32, device=dev) if bounce else None
-        p = L.TransferParams(order, S, api._ptr(dirs), float(api.DEFAULT_T_MIN), 1.0, flags, 0, None, 1, 0, 0)
+        p = L.TransferParams(order, S, api._ptr(dirs), float(api.DEFAULT_T_MIN), 1.0, flags, 0, None, 1, 1, 0)
         lib = L.load()
-        ws, nb = api._ws(lib.prtgs_transfer_workspace_size(g.n, 0, ctypes.byref(p)), dev)
+        need = lib.prtgs_transfer_workspace_size(g.n, 0, ctypes.byref(p))  # the per-ray walk's
+        p.walk = 0
+        need = max(need, lib.prtgs_transfer_workspace_size(g.n, 0, ctypes.byref(p)))  # and the packet walk's
+        ws, nb = api._ws(need, dev)
         gs = g.struct()
         args = L.TuneTransfer(ctypes.addressof(gs), ctypes.addressof(bvh.s), p, api._ptr(P), api._ptr(T),
                               api._ptr(idx), None, 0, None, api._ptr(ws), nb)

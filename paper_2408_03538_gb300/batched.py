@@ -40,6 +40,7 @@ class BatchedPipeline:
         self.colors = torch.empty(3 * self.k * self.n, dtype=torch.float32, device=device)
         self.bg = torch.zeros(3, dtype=torch.float32, device=device)
         self.packet_dirs = 0
+        self.walk = 0  # the autotuner may pick the per-ray walk (1)
         self.precision = L.PREC_FP32 if precision == "auto" else precision
         W, H = int(self.cams[0].width), int(self.cams[0].height)
         self.images = torch.empty((self.B, self.k, 3, H, W), dtype=torch.float32, device=device)
@@ -47,7 +48,8 @@ class BatchedPipeline:
         self._sizing_pass(device)
         if tune:
             bvh = api.build_bvh(self.g, self.offs_d)
-            self.packet_dirs = autotune.tune_transfer(self.g, bvh, self.dirs, order, bounce)
+            best = autotune.tune_transfer(self.g, bvh, self.dirs, order, bounce)
+            self.walk, self.packet_dirs = (1, 0) if best == 0 else (0, best)
             if precision == "auto":
                 Tt = self._transfer_out(bvh)
                 self.precision = autotune.tune_relight_batched(Tt, self.g.albedo, self.offs_d, self.L, order)
@@ -65,7 +67,8 @@ class BatchedPipeline:
 
     def _transfer_out(self, bvh):
         out = api.precompute_transfer(self.g, bvh, self.dirs, self.order, bounce=self.bounce,
-                                      out={"P": self.P, "T": self.T, "idx": self.idx}, packet_dirs=self.packet_dirs)
+                                      out={"P": self.P, "T": self.T, "idx": self.idx}, packet_dirs=self.packet_dirs,
+                                      walk=self.walk)
         return out["T"] if self.bounce else self.P
 
     def _sizing_pass(self, device):

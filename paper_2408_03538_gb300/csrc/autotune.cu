@@ -3,8 +3,9 @@
 // with CUDA events on the caller's stream and reports the times as JSON, so that a caller (the
 // Python side keeps a cache keyed by device and shape bucket) can pass the fastest to later calls.
 //
-//   PRTGS_TUNE_TRANSFER   directions per packet work item of the transfer walk (its work tile
-//                         is 32 receivers x packet_dirs directions): 1, 2, 4, 8, 16, 32
+//   PRTGS_TUNE_TRANSFER   the walk of the transfer: warp packets with packet_dirs directions per
+//                         work item (the work tile is 32 receivers x packet_dirs directions:
+//                         1, 2, 4, 8, 16, 32), or one ray per lane (reported as 0)
 //   PRTGS_TUNE_RELIGHT    relight precision among the FP32-accurate ones: FP32 CUDA cores or the
 //                         3-term BF16 split on the tensor cores (where the shape fits them)
 #include <stdio.h>
@@ -81,8 +82,9 @@ int prtgs_autotune(int32_t kernel_id, const void* args, int32_t repeats, prtgs_s
         !put(out_json, json_bytes, len, ", \"sh_order\": %.0f, \"flags\": %.0f}, \"ms\": {", (double)p.sh_order,
              (double)p.flags))
       return PRTGS_ERR_INVALID_ARG;
-    const int dirs[] = {1, 2, 4, 8, 16, 32};
-    for (int v = 0; v < 6; ++v) {
+    const int dirs[] = {1, 2, 4, 8, 16, 32, 0};  // 0: the per-ray walk
+    for (int v = 0; v < 7; ++v) {
+      p.walk = dirs[v] == 0 ? 1 : 0;
       p.packet_dirs = dirs[v];
       const float ms = time_variant(
           [&]() {

@@ -211,13 +211,14 @@ def test_autotune_reports_every_variant_and_the_choice_keeps_results(tmp_path, m
     bvh = api.build_bvh(g)
     dirs = torch.from_numpy(S.direction_set(64, 9)).cuda()
     best = autotune.tune_transfer(g, bvh, dirs, 3, True)
-    assert best in (1, 2, 4, 8, 16, 32)
+    assert best in (0, 1, 2, 4, 8, 16, 32)
     rep = next(iter(json.load(open(tmp_path / "tune.json")).values()))
-    assert set(rep["ms"]) == {"1", "2", "4", "8", "16", "32"} and all(v > 0 for v in rep["ms"].values())
+    assert set(rep["ms"]) == {"0", "1", "2", "4", "8", "16", "32"} and all(v > 0 for v in rep["ms"].values())
     a = api.precompute_transfer(g, bvh, dirs, 3, bounce=True)
-    b = api.precompute_transfer(g, bvh, dirs, 3, bounce=True, packet_dirs=best)
-    torch.testing.assert_close(a["T"], b["T"], rtol=0, atol=0)
-    torch.testing.assert_close(a["idx"], b["idx"], rtol=0, atol=0)
+    for pd in (1, 32):  # the packet work-tile shape does not change any result
+        b = api.precompute_transfer(g, bvh, dirs, 3, bounce=True, packet_dirs=pd)
+        torch.testing.assert_close(a["T"], b["T"], rtol=0, atol=0)
+        torch.testing.assert_close(a["idx"], b["idx"], rtol=0, atol=0)
     assert autotune.tune_transfer(g, bvh, dirs, 3, True) == best  # from the cache
 
 
