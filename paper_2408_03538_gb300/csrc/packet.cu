@@ -29,12 +29,12 @@ constexpr int kPStack = 384;     // node stack of a warp (ints)
 #endif
 constexpr int kPacketRoundHits = PRTGS_PACKET_ROUND_HITS;  // hits per index-matrix search round
 #ifndef PRTGS_PACKET_LEAVES
-#define PRTGS_PACKET_LEAVES 128
+#define PRTGS_PACKET_LEAVES 96
 #endif
 #ifndef PRTGS_PACKET_MIN_BLOCKS
-#define PRTGS_PACKET_MIN_BLOCKS 1
+#define PRTGS_PACKET_MIN_BLOCKS 4  // the visibility-only kernel fits 4 blocks per SM without spills
 #endif
-constexpr int kPLeaves = PRTGS_PACKET_LEAVES;  // leaf chunk of a warp (> 64)
+constexpr int kPLeaves = PRTGS_PACKET_LEAVES;  // leaf chunk of a warp (> 64; 96 and 128 measured alike)
 // wide pops (32 nodes) only while the stack keeps room for their pushes plus a full one-node-
 // at-a-time descent of the deepest possible tree (64 levels)
 constexpr int kPHeadroom = 64 + 64 + 4;
@@ -45,6 +45,11 @@ struct PacketSmem {
   float4 la[kPLeaves];     // leaf box lo xyz, sorted position
   float4 lb[kPLeaves];     // leaf box hi xyz, unused
   float4 stage[32][5];     // a group of leaves, staged: q0, q1, q2, (a22, A d), (1/|A d|^2, sqrt, m, pos)
+  // the work item's window of 64 receivers: record row 0 (mean, opacity), scene root, Gaussian
+  // index; and, per direction, the window slots of the receivers that face it
+  float4 wq0[64];
+  int wroot[64], wgid[64];
+  int rlist[64];
 };
 // Bounce mode, per warp after the PacketSmem array: the search round's nearest hits of each lane,
 // hits[k][lane] = (t*, position, alpha, m).
@@ -392,8 +397,9 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
   for (int i = threadIdx.x; i < 3 * a.S; i += blockDim.x) sdir[i] = a.dirs[i];
   __syncthreads();
   const int64_t batch = a.r1 - a.r0;
-  const int64_t n_packets = (batch + 31) / 32;
+  const int64_t n_windows = (batch + 63) / 64;
   const int dblocks = (a.S + dpi - 1) / dpi;  // dpi directions per work item
+  const unsigned below = (1u << lane) - 1u;
   RayStats rs{0u, 0u, 0u, 0u, 0u, 0u};
   unsigned traced = 0, walks = 0;
   for (;;) {
@@ -401,25 +407,55 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
     __syncwarp();
     const unsigned item = s_item[warp];
     __syncwarp();
-    if ((int64_t)item >= n_packets * dblocks) break;
-    const int64_t p = item / dblocks;
+    if ((int64_t)item >= n_windows * dblocks) break;
+    // a window of 64 receivers adjacent in Morton order; each lane stages two of them
+    const int64_t base = a.r0 + 64 * (item / dblocks);
     const int s0 = (int)(item % dblocks) * dpi;
-    const int64_t self64 = a.r0 + 32 * p + lane;
-    const bool valid = self64 < a.r1;
-    const int self = valid ? (int)self64 : (int)a.r0;
-    const float4 q0 = __ldg(a.recs + 4 * self);
-    const float4 q3 = __ldg(a.recs + 4 * self + 3);
-    int root = INT32_MIN;
-    if (valid) {
-      const int gid = a.order[self];
-      root = a.roots[find_scene(a.offsets, a.n_scenes, gid)];
-      if (root != INT32_MIN && !child_ok(root, a.n, a.status)) root = INT32_MIN;
+    float4 nq[2];  // record row 3 of the lane's two receivers (its .yzw: the normal)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const bool vj = base + j < a.r1;
+      const int sj = vj ? (int)(base + j) : (int)a.r0;
+      sm.wq0[j] = __ldg(a.recs + 4 * sj);
+      nq[h] = __ldg(a.recs + 4 * sj + 3);
+      int rt = INT32_MIN, gj = -1;
+      if (vj) {
+        gj = a.order[sj];
+        rt = a.roots[find_scene(a.offsets, a.n_scenes, gj)];
+        if (rt != INT32_MIN && !child_ok(rt, a.n, a.status)) rt = INT32_MIN;
+      }
+      sm.wroot[j] = rt;
+      sm.wgid[j] = gj;
     }
+    __syncwarp();
     const int s1 = min(a.S, s0 + dpi);
     for (int s = s0; s < s1; ++s) {
       const float* d = sdir + 3 * s;
-      const float c = ray_cos(q3.y, q3.z, q3.w, d);
-      const bool up = valid && c > 0.0f;
+      // the receivers of the window that face direction s, compacted into packets of 32 lanes
+      // (a window whose receivers all face it gives the two packets of its halves)
+      bool upj[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        const bool vj = base + j < a.r1;
+        upj[h] = vj && ray_cos(nq[h].y, nq[h].z, nq[h].w, d) > 0.0f;
+        if (vj && !upj[h]) {  // untraced ray: no visibility, no index-matrix entry
+          V[(int64_t)s * batch + (base + j - a.r0)] = 0.0f;
+          if (BOUNCE) a.idx[(int64_t)sm.wgid[j] * a.S + s] = -1;
+        }
+      }
+      const unsigned m0 = __ballot_sync(0xffffffffu, upj[0]), m1 = __ballot_sync(0xffffffffu, upj[1]);
+      const int total = __popc(m0) + __popc(m1);
+      if (upj[0]) sm.rlist[__popc(m0 & below)] = lane;
+      if (upj[1]) sm.rlist[__popc(m0) + __popc(m1 & below)] = lane + 32;
+      __syncwarp();
+      for (int pass = 0; pass * 32 < total; ++pass) {
+      const bool up = pass * 32 + lane < total;
+      const int jw = up ? sm.rlist[pass * 32 + lane] : 0;
+      const float4 q0 = sm.wq0[jw];
+      const int root = up ? sm.wroot[jw] : INT32_MIN;
+      const int self = (int)(base + jw);
       float vis = up ? 1.0f : 0.0f;
       int best = -1;  // index-matrix entry (sorted position of the chosen hit)
       if ((a.flags & PRTGS_SHADOW) && __any_sync(0xffffffffu, up)) {
@@ -497,11 +533,15 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
           todo &= ~grp;
         }
       }
-      if (valid) {
-        V[(int64_t)s * batch + (self64 - a.r0)] = vis;
-        if (BOUNCE) a.idx[(int64_t)a.order[self] * a.S + s] = best >= 0 ? a.order[best] : -1;
+      if (up) {
+        V[(int64_t)s * batch + (self - a.r0)] = vis;
+        if (BOUNCE) a.idx[(int64_t)sm.wgid[jw] * a.S + s] = best >= 0 ? a.order[best] : -1;
       }
+      __syncwarp();
+      }  // pass
+      __syncwarp();  // the compacted list is rewritten for the next direction
     }
+    __syncwarp();  // the window is restaged by the next work item
   }
   if (a.stats) {
     unsigned long long c0 = warp_sum_u64(rs.nodes), c1 = warp_sum_u64(rs.search_nodes),
@@ -578,7 +618,7 @@ static int launch_packet_t(const TraceArgs& a, float* V, int sms, cudaStream_t s
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_packet<BOUNCE>, kPacketThreads, smem);
   const int warps = sms * (per_sm > 0 ? per_sm : 1) * kPacketWarps;
   // directions per work item: kPacketDirs, fewer when that would leave too few items per warp
-  const int64_t n_packets = (a.r1 - a.r0 + 31) / 32;
+  const int64_t n_packets = (a.r1 - a.r0 + 63) / 64;  // windows of 64 receivers
   int dpi = a.packet_dirs;
   if (dpi <= 0) {
     dpi = kPacketDirs;
