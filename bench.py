@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true",
+                    help="run the warm-up and timed steps of the default workload only (for a launch list)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, SURFACE, "batched-32", "diff-300k"],
                     help="tiled-1m-glossy (default): 1M splats, 30 %% glossy, 64 lights on the tensor cores; "
                          "surface-100k: the differentiable 100k step; batched-32: 32 isotropic scenes, one "
@@ -845,6 +847,11 @@ def run_tiled(args):
         for i in range(3):
             stage_ms[i] += ev[i].elapsed_time(ev[i + 1])
         total += ev[0].elapsed_time(ev[3])
+    if args.only_steps:
+        sampler.stop()
+        if rank == 0:
+            print(json.dumps({"workload": WORKLOAD, "steps": args.steps, "ms_per_step": total / args.steps}))
+        return
     # end to end through the public API: host (pinned) inputs copied in and the 64 images copied
     # out every step
     gbuf = api.GaussianTensors(*(torch.empty_like(getattr(g, f)) for f in fields))

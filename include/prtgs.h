@@ -161,9 +161,11 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  *   walk            tuning: 0 = warp packets (default: the rays that 32 receivers adjacent in
  *                   Morton order cast along one direction walk the BVH together), 1 = one ray
  *                   per lane (the plain per-ray walk); both give the same results
- *   packet_dirs     tuning: directions per work item of the packet walk (its work tile:
- *                   32 receivers x packet_dirs directions), 1..64; 0 = chosen from the problem
- *                   size (see prtgs_autotune); the results do not depend on it
+ *   packet_dirs     tuning: directions per work item of the packet walk (a work item is a
+ *                   window of 64 receivers adjacent in Morton order x packet_dirs directions;
+ *                   for each direction the window's receivers that face it are compacted into
+ *                   packets of 32 lanes), 1..64; 0 = the default (1, see prtgs_autotune); the
+ *                   results do not depend on it
  *   stats           optional device uint64[10] that the call ADDS its work counters to:
  *                   BVH node visits of the visibility walks, node visits of the index-matrix
  *                   search, leaf tests, ray-Gaussian hits, search rounds, traced rays, rays
