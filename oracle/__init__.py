@@ -14,9 +14,12 @@ Contents and the passages they follow:
 * ``glossy``             the 16x16 glossy transfer matrix (Eq. 36-41) with the Disney-style
                          BRDF split of Eq. 15.
 * ``relight``            L . T per Gaussian (Eq. 14), or L . M . Y(v) for glossy splats (Eq. 41).
+* ``training_transfer``  the training-stage transfer vector for one known view (Eq. 28), and its
+                         roughness / metallic derivatives by complex step.
 * ``morton_lbvh``        Morton codes and the binary radix tree used as the BVH (Sec. 4.4).
 * ``render`` (module)    3DGS projection (Eq. 3) and front-to-back compositing (Eq. 4), in
-                         FP64 PyTorch so that autograd gives the oracle's gradients.
+                         FP64 PyTorch so that autograd gives the oracle's gradients; the
+                         pseudo-normal of a depth map and the normal loss (Eq. 23-25).
 
 Every float input is promoted exactly to FP64. Readings of under-specified or garbled
 passages are stated where they are used.
@@ -280,6 +283,66 @@ def glossy(scene, dirs, order: int, recv, V, allow_V=None):
         if allow_V is not None:
             allow[r] = np.sum(w * c * allow_V[r] * np.linalg.norm(Y, axis=1) * np.linalg.norm(B, axis=1))
     return M, allow
+
+
+# ------------------------------------------------------------------------------------------
+# Training-stage transfer for one known view direction (Sec. 4.5, Eq. 28)
+# ------------------------------------------------------------------------------------------
+def view_dirs(means, cam_pos):
+    """v_i = (cam_pos - mu_i) / |cam_pos - mu_i|: the direction from a splat to the camera."""
+    v = np.asarray(cam_pos, dtype=np.float64)[None, :] - np.asarray(means, dtype=np.float64)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def training_transfer(scene, dirs, order: int, recv, V, cam_pos, specular: bool = True, roughness=None,
+                      metallic=None):
+    """t_i[c] = sum_s w k_i(w_s, v_i) (n_i.w_s)^+ V_is Y_c(w_s), w = 4 pi / S (Eq. 28).
+
+    Reading: Eq. 28 is printed as (f_s(w_i,v) + f_d)(v.n)V(v,x), but the text defines the
+    transfer on the sphere of incident directions w_i, so the cosine and the visibility are
+    read as those of w_i; the view direction v enters through the BRDF only. The BRDF is the
+    same k = (1-m) + pi f_s as the glossy matrices (Eq. 15 times pi; albedo and 1/pi applied
+    at relight, as for P), so with f_s = 0 (``specular=False``) and m = 0 the vector is
+    exactly the diffuse transfer P of Eq. 29. v_i = normalize(cam_pos - mu_i). No bounce term
+    (the paper trades the indirect light's accuracy for speed during training).
+    V [R,S] is the visibility of the receivers ``recv`` (as ``trace`` returns it).
+    ``roughness`` / ``metallic`` [R] override the scene's (complex values are allowed: they
+    flow through k, which is what ``training_transfer_grad`` uses).
+    """
+    recv = np.asarray(recv, dtype=np.int64).reshape(-1)
+    d = np.asarray(dirs, dtype=np.float64)
+    S = d.shape[0]
+    w = 4.0 * math.pi / S
+    Y = sh(order, d)
+    v = view_dirs(np.asarray(scene.means, dtype=np.float64)[recv], cam_pos)
+    rough = np.asarray(scene.roughness, dtype=np.float64)[recv] if roughness is None else roughness
+    metal = np.asarray(scene.metallic, dtype=np.float64)[recv] if metallic is None else metallic
+    dtype = np.result_type(np.asarray(rough), np.asarray(metal), np.float64)
+    t = np.zeros((recv.size, Y.shape[1]), dtype=dtype)
+    for r, i in enumerate(recv):
+        n = np.asarray(scene.normals[i], dtype=np.float64)
+        c = np.maximum(d @ n, 0.0)
+        if specular:
+            k = brdf_kernel(n[None, :], d, v[r][None, :], rough[r], metal[r])  # [S]
+        else:
+            nu = n / np.linalg.norm(n)
+            k = np.where((d @ nu > 0) & (float(v[r] @ nu) > 0), 1.0 - metal[r], 0.0)
+        t[r] = (w * k * c * np.asarray(V[r], dtype=np.float64)) @ Y
+    return t
+
+
+def training_transfer_grad(scene, dirs, order: int, recv, V, cam_pos, dT, h: float = 1e-30):
+    """d(sum_c dT[r,c] t_r[c]) / d roughness_r and / d metallic_r for each receiver r of
+    ``training_transfer``: complex-step differentiation (Squire and Trapp 1998), exact to
+    rounding since k is analytic in both; t_r depends only on receiver r's own parameters, so
+    one complex evaluation gives every receiver's derivative."""
+    recv = np.asarray(recv, dtype=np.int64).reshape(-1)
+    dT = np.asarray(dT, dtype=np.float64)
+    rough = np.asarray(scene.roughness, dtype=np.float64)[recv]
+    metal = np.asarray(scene.metallic, dtype=np.float64)[recv]
+    tr = training_transfer(scene, dirs, order, recv, V, cam_pos, roughness=rough + 1j * h, metallic=metal)
+    tm = training_transfer(scene, dirs, order, recv, V, cam_pos, roughness=rough, metallic=metal + 1j * h)
+    return (dT * tr.imag).sum(1) / h, (dT * tm.imag).sum(1) / h
 
 
 def multi_bounce(scene, dirs, order: int, tr, n_bounces: int, tol: float = 1e-4):

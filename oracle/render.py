@@ -180,3 +180,63 @@ def psnr(a, b, peak=None):
     if peak is None:
         peak = max(float(np.max(np.abs(b))), 1e-12)
     return float("inf") if mse == 0 else 10.0 * math.log10(peak * peak / mse)
+
+
+# ------------------------------------------------------------------------------------------
+# Pseudo-normal from the depth map and the normal loss (Sec. 4.3, Eq. 23-25)
+# ------------------------------------------------------------------------------------------
+def backproject(depth, cam):
+    """World-space points X[H,W,3] of a view-space depth map: the pixel (u, v) (centre at
+    integer coordinates, the projection u = fx x/z + cx of ``preprocess``) at depth z is the
+    camera-space point z ((u - cx)/fx, (v - cy)/fy, 1), taken to the world by R^T (x - t)."""
+    D = np.asarray(depth, dtype=np.float64)
+    H, W = D.shape
+    R = np.asarray(cam.rot, dtype=np.float64)
+    t = np.asarray(cam.trans, dtype=np.float64)
+    u = (np.arange(W, dtype=np.float64) - float(cam.cx)) / float(cam.fx)
+    v = (np.arange(H, dtype=np.float64) - float(cam.cy)) / float(cam.fy)
+    Xc = np.stack([D * u[None, :], D * v[:, None], D], axis=-1)
+    return (Xc - t) @ R
+
+
+def pseudo_normal(depth, cam):
+    """Pseudo-normal map N'[3,H,W] of a depth map (Eq. 24: "computed from D").
+
+    Reading: the paper does not say how. As in the works it cites for it, each pixel is
+    back-projected to its 3D point (``backproject``) and N' is the unit normal of the surface
+    those points span, from central differences: N' ~ (X(u,v+1) - X(u,v-1)) x (X(u+1,v) -
+    X(u-1,v)), the orientation that faces the camera, in world space. It is defined where the
+    pixel and its four neighbours all have depth > 0 (the composite of Eq. 23 is 0 where no
+    splat contributes) and the pixel is not on the image border; elsewhere N' = 0.
+    """
+    D = np.asarray(depth, dtype=np.float64)
+    H, W = D.shape
+    X = backproject(D, cam)
+    N = np.zeros((3, H, W))
+    if H < 3 or W < 3:
+        return N
+    du = X[1:-1, 2:] - X[1:-1, :-2]
+    dv = X[2:, 1:-1] - X[:-2, 1:-1]
+    n = np.cross(dv, du)
+    ln = np.linalg.norm(n, axis=-1)
+    ok = ((D[1:-1, 1:-1] > 0) & (D[1:-1, 2:] > 0) & (D[1:-1, :-2] > 0) & (D[2:, 1:-1] > 0) & (D[:-2, 1:-1] > 0)
+          & (ln > 0))
+    n = np.where(ok[..., None], n / np.where(ln > 0, ln, 1.0)[..., None], 0.0)
+    N[:, 1:-1, 1:-1] = np.moveaxis(n, -1, 0)
+    return N
+
+
+def normal_loss(normal, pseudo):
+    """L_normal = ||N - N'|| (Eq. 25) and dL/dN.
+
+    Reading: ||.|| is the Euclidean (Frobenius) norm of the difference of the two maps, taken
+    over the pixels where N' is defined (N' != 0); N' is the guide and carries no gradient
+    (it serves as guidance for the splats' normals). dL/dN = (N - N') / L on those pixels,
+    0 elsewhere and when L = 0.
+    """
+    N = np.asarray(normal, dtype=np.float64)
+    Np = np.asarray(pseudo, dtype=np.float64)
+    m = np.any(Np != 0, axis=0)
+    diff = np.where(m[None], N - Np, 0.0)
+    L = float(np.sqrt(np.sum(diff * diff)))
+    return L, (diff / L if L > 0 else np.zeros_like(diff))
