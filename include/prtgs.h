@@ -239,6 +239,48 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                        size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Visibility cache for training (Sec. 4.4-4.5): the same walk as prtgs_precompute_transfer with
+ * flags = PRTGS_SHADOW, keeping every ray's visibility.
+ *  V[n,S]   out (device): V_is, the transmittance of the ray from mu_i along w_s as in P below;
+ *           0 where n_i.w_s <= 0 (the ray is not traced)
+ *  P[n,C]   out (device, required): the shadowed diffuse transfer of the same rays (Eq. 29)
+ * Geometry is frozen after the ray tracing (Sec. 4.4), so V serves every later training step's
+ * prtgs_training_transfer. p->flags must be exactly PRTGS_SHADOW (else PRTGS_ERR_UNSUPPORTED);
+ * sh_order 1..6; walk and packet_dirs as for prtgs_precompute_transfer.
+ * Workspace: prtgs_visibility_workspace_size. Errors: as prtgs_precompute_transfer.
+ */
+size_t prtgs_visibility_workspace_size(int64_t n, const prtgs_transfer_params* p);
+int prtgs_precompute_visibility(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                float* V, float* P, int32_t* status, void* workspace, size_t workspace_bytes,
+                                prtgs_stream_t stream);
+
+/*
+ * Training-stage transfer for one known view (Sec. 4.5, Eq. 28):
+ *   t[i,c] = sum_s (4 pi/S) k_i(w_s, v_i) max(0, n_i.w_s) V[i,s] Y_c(w_s),
+ *   v_i = (cam_pos - mu_i) / |cam_pos - mu_i|,
+ * k the BRDF kernel of the glossy matrices (see prtgs_precompute_transfer's M; zero when
+ * n_i.v_i <= 0). Eq. 28 is printed with the cosine and visibility of v; they are read as those
+ * of the incident direction w_s, the view entering through the BRDF only, so that with f_s = 0
+ * and metallic 0 the vector is the diffuse P of Eq. 29. Relight it like P (t_channels = 1):
+ * colors = (albedo/pi) (t . L). No bounce term (the paper trades indirect accuracy for speed here).
+ *   g: n, means, normals, roughness[n], metallic[n] (device)
+ *   dirs[S,3], V[n,S] (device; V from prtgs_precompute_visibility); cam_pos[3] (HOST)
+ *   t[n,C] out (device)
+ * sh_order 1..6, S 1..1024. Workspace: prtgs_training_transfer_workspace_size (the SH table).
+ * The backward takes dt[n,C] = dLoss/dt and writes d_roughness[n], d_metallic[n] (device;
+ * overwritten, no atomics: deterministic). Gradients to the normals, means and visibility are
+ * not formed (the normals are guided by the normal loss, Eq. 25; geometry is frozen).
+ */
+size_t prtgs_training_transfer_workspace_size(int32_t sh_order, int32_t n_dirs);
+int prtgs_training_transfer(const prtgs_gaussians* g, int32_t sh_order, int32_t n_dirs, const float* dirs,
+                            const float* V, const float* cam_pos, float* t, void* workspace, size_t workspace_bytes,
+                            prtgs_stream_t stream);
+int prtgs_training_transfer_backward(const prtgs_gaussians* g, int32_t sh_order, int32_t n_dirs, const float* dirs,
+                                     const float* V, const float* cam_pos, const float* dt, float* d_roughness,
+                                     float* d_metallic, void* workspace, size_t workspace_bytes,
+                                     prtgs_stream_t stream);
+
+/*
  * Relight (Eq. 14; glossy Eq. 41):
  *   colors[k,n,3] = (albedo_i/pi) * (T_i[c] . L[k,c,:]) per channel c,
  * with T [n,C] (t_channels = 1) or [n,3,C] (t_channels = 3). Glossy splats (n_glossy > 0,
@@ -391,6 +433,32 @@ size_t prtgs_render_geometry_workspace_size(int64_t n, int32_t width, int32_t he
 int prtgs_render_geometry(const prtgs_gaussians* g, const prtgs_camera* cam, float* depth, float* normal,
                           prtgs_render_state* st, int32_t* status, void* workspace, size_t workspace_bytes,
                           prtgs_stream_t stream);
+
+/*
+ * Pseudo-normal map of a depth map (Sec. 4.3, Eq. 24: "computed from D"). Each pixel is
+ * back-projected with the camera (pixel centre (x, y) at depth D: camera point
+ * D ((x - cx)/fx, (y - cy)/fy, 1)) and N' is the unit normal of the central differences
+ * (X(x,y+1) - X(x,y-1)) x (X(x+1,y) - X(x-1,y)), which faces the camera, rotated to world space.
+ *   depth[H,W] in (device; e.g. from prtgs_render_geometry), pseudo[3,H,W] out (device)
+ * N' = 0 on the image border and wherever the pixel or one of its four neighbours has depth <= 0
+ * (no splat there). Only cam->rot, fx, fy, cx, cy, width and height are used.
+ */
+int prtgs_pseudo_normal(const prtgs_camera* cam, const float* depth, float* pseudo, prtgs_stream_t stream);
+
+/*
+ * Normal loss (Sec. 4.3, Eq. 25): L = ||N - N'||, the Euclidean norm of the difference of the
+ * two [3,H,W] maps over the pixels where N' is defined (N' != 0), and dL/dN = (N - N') / L on
+ * those pixels (0 elsewhere and when L = 0). N' is the guide and gets no gradient. The sum is a
+ * fixed-order reduction, so the result is the same from run to run.
+ *   normal[3,H,W], pseudo[3,H,W] in (device); loss[1] out (device); d_normal[3,H,W] out
+ *   (device, may be NULL). Feed d_normal to prtgs_render_backward with the normals as the
+ *   colours (k = 1, bg 0) and the state of prtgs_render_geometry to reach the splats' normals
+ *   (and geometry) through Eq. 25's composite.
+ * Workspace: prtgs_normal_loss_workspace_size.
+ */
+size_t prtgs_normal_loss_workspace_size(int32_t width, int32_t height);
+int prtgs_normal_loss(int32_t width, int32_t height, const float* normal, const float* pseudo, float* loss,
+                      float* d_normal, void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
  * Render backward: dimage[k,3,H,W] in; gradients out (overwritten): d_means[n,3],

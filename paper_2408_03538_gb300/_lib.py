@@ -131,6 +131,18 @@ _SIGS = {
     "prtgs_relight_backward_batched": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                                  c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                                  c_size_t, c_void_p]),
+    "prtgs_visibility_workspace_size": (c_size_t, [c_int64, P(TransferParams)]),
+    "prtgs_precompute_visibility": (c_int32, [P(Gaussians), P(BVH), P(TransferParams), c_void_p, c_void_p, c_void_p,
+                                              c_void_p, c_size_t, c_void_p]),
+    "prtgs_training_transfer_workspace_size": (c_size_t, [c_int32, c_int32]),
+    "prtgs_training_transfer": (c_int32, [P(Gaussians), c_int32, c_int32, c_void_p, c_void_p, P(c_float), c_void_p,
+                                          c_void_p, c_size_t, c_void_p]),
+    "prtgs_training_transfer_backward": (c_int32, [P(Gaussians), c_int32, c_int32, c_void_p, c_void_p, P(c_float),
+                                                   c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_pseudo_normal": (c_int32, [P(Camera), c_void_p, c_void_p, c_void_p]),
+    "prtgs_normal_loss_workspace_size": (c_size_t, [c_int32, c_int32]),
+    "prtgs_normal_loss": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                    c_void_p]),
     "prtgs_autotune": (c_int32, [c_int32, c_void_p, c_int32, c_void_p, P(c_int32), ctypes.c_char_p, c_size_t]),
     "prtgs_graph_begin": (c_int32, [c_void_p]),
     "prtgs_graph_end": (c_int32, [c_void_p, P(c_void_p)]),

@@ -194,6 +194,91 @@ def precompute_transfer_backward(g: GaussianTensors, bvh: Bvh, dirs: torch.Tenso
 
 
 # ------------------------------------------------------------------------------------------
+# Training stage: visibility cache, view transfer (Eq. 28), pseudo-normal and normal loss (Eq. 24-25)
+# ------------------------------------------------------------------------------------------
+def precompute_visibility(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int,
+                          t_min: float = DEFAULT_T_MIN, status: Status | None = None, walk: int = 0,
+                          packet_dirs: int = 0, out: dict | None = None):
+    """Visibility V [n,S] of every Gaussian along the direction set (0 where n.w <= 0) and the
+    shadowed diffuse transfer P [n,C] of the same walk."""
+    lib = L.load()
+    dev = g.means.device
+    S = int(dirs.shape[0])
+    out = out or {}
+    V = out.get("V") if out.get("V") is not None else torch.empty((g.n, S), dtype=torch.float32, device=dev)
+    P = out.get("P") if out.get("P") is not None else torch.empty((g.n, sh_count(order)), dtype=torch.float32,
+                                                                    device=dev)
+    p = L.TransferParams(order, S, _ptr(dirs), float(t_min), 1.0, L.SHADOW, 0, None, 1, int(walk), int(packet_dirs))
+    ws, nb = _ws(lib.prtgs_visibility_workspace_size(g.n, ctypes.byref(p)), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_precompute_visibility(ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(V), _ptr(P),
+                                            status.ptr() if status else None, _ptr(ws), nb, _stream()),
+            "prtgs_precompute_visibility")
+    return {"V": V, "P": P, "_ws": ws}
+
+
+def _cam3(cam_pos):
+    c = np.asarray(cam_pos, dtype=np.float32).reshape(3)
+    return (ctypes.c_float * 3)(*[float(x) for x in c])
+
+
+def training_transfer(g: GaussianTensors, V: torch.Tensor, dirs: torch.Tensor, order: int, cam_pos,
+                      out: torch.Tensor | None = None):
+    """Training-stage transfer t [n,C] for the view from ``cam_pos`` (Eq. 28)."""
+    lib = L.load()
+    dev = g.means.device
+    S = int(dirs.shape[0])
+    t = out if out is not None else torch.empty((g.n, sh_count(order)), dtype=torch.float32, device=dev)
+    ws, nb = _ws(lib.prtgs_training_transfer_workspace_size(order, S), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_training_transfer(ctypes.byref(gs), order, S, _ptr(dirs), _ptr(V), _cam3(cam_pos), _ptr(t),
+                                        _ptr(ws), nb, _stream()), "prtgs_training_transfer")
+    return t
+
+
+def training_transfer_backward(g: GaussianTensors, V: torch.Tensor, dirs: torch.Tensor, order: int, cam_pos,
+                               dt: torch.Tensor):
+    """d_roughness [n], d_metallic [n] from dLoss/dt [n,C] of ``training_transfer``."""
+    lib = L.load()
+    dev = g.means.device
+    S = int(dirs.shape[0])
+    dr = torch.empty(g.n, dtype=torch.float32, device=dev)
+    dm = torch.empty(g.n, dtype=torch.float32, device=dev)
+    dt = dt.contiguous()
+    ws, nb = _ws(lib.prtgs_training_transfer_workspace_size(order, S), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_training_transfer_backward(ctypes.byref(gs), order, S, _ptr(dirs), _ptr(V), _cam3(cam_pos),
+                                                 _ptr(dt), _ptr(dr), _ptr(dm), _ptr(ws), nb, _stream()),
+            "prtgs_training_transfer_backward")
+    return dr, dm
+
+
+def pseudo_normal(depth: torch.Tensor, cam, out: torch.Tensor | None = None):
+    """Pseudo-normal map N' [3,H,W] (world space, 0 where undefined) of a depth map [H,W] (Eq. 24)."""
+    lib = L.load()
+    H, W = int(depth.shape[0]), int(depth.shape[1])
+    Np = out if out is not None else torch.empty((3, H, W), dtype=torch.float32, device=depth.device)
+    cs = camera_struct(cam)
+    L.check(lib.prtgs_pseudo_normal(ctypes.byref(cs), _ptr(depth.contiguous()), _ptr(Np), _stream()),
+            "prtgs_pseudo_normal")
+    return Np
+
+
+def normal_loss(normal: torch.Tensor, pseudo: torch.Tensor, need_grad: bool = True):
+    """L = ||N - N'|| over the pixels where N' is defined (Eq. 25) as a device scalar [1], and
+    dL/dN [3,H,W] (None without ``need_grad``)."""
+    lib = L.load()
+    H, W = int(normal.shape[1]), int(normal.shape[2])
+    dev = normal.device
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    dN = torch.empty((3, H, W), dtype=torch.float32, device=dev) if need_grad else None
+    ws, nb = _ws(lib.prtgs_normal_loss_workspace_size(W, H), dev)
+    L.check(lib.prtgs_normal_loss(W, H, _ptr(normal.contiguous()), _ptr(pseudo.contiguous()), _ptr(loss), _ptr(dN),
+                                  _ptr(ws), nb, _stream()), "prtgs_normal_loss")
+    return loss, dN
+
+
+# ------------------------------------------------------------------------------------------
 # Relight
 # ------------------------------------------------------------------------------------------
 def relight(T: torch.Tensor, albedo: torch.Tensor, Lsh: torch.Tensor, order: int, precision: int = L.PREC_FP32,

@@ -172,6 +172,95 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                              workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+// ---- visibility cache, training-stage transfer, pseudo-normal, normal loss ----
+
+size_t prtgs_visibility_workspace_size(int64_t n, const prtgs_transfer_params* p) {
+  if (!p || n < 0) return 0;
+  return transfer_workspace(n, 0, p, true);
+}
+
+int prtgs_precompute_visibility(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
+                                float* V, float* P, int32_t* status, void* workspace, size_t workspace_bytes,
+                                prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
+  if ((rc = check_order_high(p->sh_order))) return rc;
+  if (p->flags != PRTGS_SHADOW) return PRTGS_ERR_UNSUPPORTED;
+  if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
+  if (p->walk < 0 || p->walk > 1 || p->packet_dirs < 0 || p->packet_dirs > 64) return PRTGS_ERR_INVALID_ARG;
+  if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
+  if (g->n == 0) return PRTGS_OK;
+  if (!V || !P || !g->normals) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, transfer_workspace(g->n, 0, p, true));
+  if (rc) return rc;
+  return finish(precompute_transfer(g, bvh, p, P, nullptr, nullptr, nullptr, 0, status, workspace,
+                                    reinterpret_cast<cudaStream_t>(stream), V));
+}
+
+size_t prtgs_training_transfer_workspace_size(int32_t sh_order, int32_t n_dirs) {
+  if (check_order_high(sh_order) || prtgs::transfer_check_dirs(n_dirs)) return 0;
+  return training_transfer_workspace(sh_order, n_dirs);
+}
+
+static int check_training(const prtgs_gaussians* g, int32_t sh_order, int32_t n_dirs, const float* dirs,
+                          const float* V, const float* cam_pos, const void* out, void* workspace,
+                          size_t workspace_bytes) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
+  if (prtgs::transfer_check_dirs(n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!cam_pos || !(cam_pos[0] == cam_pos[0] && cam_pos[1] == cam_pos[1] && cam_pos[2] == cam_pos[2]))
+    return PRTGS_ERR_INVALID_ARG;
+  if (g->n == 0) return PRTGS_OK;
+  if (!dirs || !V || !out || !g->normals || !g->roughness || !g->metallic) return PRTGS_ERR_INVALID_ARG;
+  return check_ws(workspace, workspace_bytes, training_transfer_workspace(sh_order, n_dirs));
+}
+
+int prtgs_training_transfer(const prtgs_gaussians* g, int32_t sh_order, int32_t n_dirs, const float* dirs,
+                            const float* V, const float* cam_pos, float* t, void* workspace, size_t workspace_bytes,
+                            prtgs_stream_t stream) {
+  int rc = check_training(g, sh_order, n_dirs, dirs, V, cam_pos, t, workspace, workspace_bytes);
+  if (rc || g->n == 0) return rc;
+  return finish(training_transfer(g, sh_order, n_dirs, dirs, V, cam_pos, nullptr, t, nullptr, nullptr, workspace,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int prtgs_training_transfer_backward(const prtgs_gaussians* g, int32_t sh_order, int32_t n_dirs, const float* dirs,
+                                     const float* V, const float* cam_pos, const float* dt, float* d_roughness,
+                                     float* d_metallic, void* workspace, size_t workspace_bytes,
+                                     prtgs_stream_t stream) {
+  int rc = check_training(g, sh_order, n_dirs, dirs, V, cam_pos, dt, workspace, workspace_bytes);
+  if (rc || g->n == 0) return rc;
+  if (!d_roughness || !d_metallic) return PRTGS_ERR_INVALID_ARG;
+  return finish(training_transfer(g, sh_order, n_dirs, dirs, V, cam_pos, dt, nullptr, d_roughness, d_metallic,
+                                  workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int prtgs_pseudo_normal(const prtgs_camera* cam, const float* depth, float* pseudo, prtgs_stream_t stream) {
+  if (!cam || cam->width < 0 || cam->height < 0) return PRTGS_ERR_INVALID_ARG;
+  if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return PRTGS_ERR_INVALID_ARG;
+  if ((int64_t)cam->width * cam->height == 0) return PRTGS_OK;
+  if (!depth || !pseudo) return PRTGS_ERR_INVALID_ARG;
+  return finish(pseudo_normal(cam, depth, pseudo, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t prtgs_normal_loss_workspace_size(int32_t width, int32_t height) {
+  if (width < 0 || height < 0) return 0;
+  return normal_loss_workspace(width, height);
+}
+
+int prtgs_normal_loss(int32_t width, int32_t height, const float* normal, const float* pseudo, float* loss,
+                      float* d_normal, void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  if (width < 0 || height < 0 || !loss) return PRTGS_ERR_INVALID_ARG;
+  if ((int64_t)width * height > 0 && (!normal || !pseudo)) return PRTGS_ERR_INVALID_ARG;
+  int rc = check_ws(workspace, workspace_bytes, normal_loss_workspace(width, height));
+  if (rc) return rc;
+  return finish(normal_loss(width, height, normal, pseudo, loss, d_normal, workspace,
+                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // ---- relight ----
 size_t prtgs_relight_workspace_size(int64_t n, int32_t sh_order, int32_t k, int32_t precision) {
   if (n < 0 || k < 0) return 0;

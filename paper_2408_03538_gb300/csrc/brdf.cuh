@@ -1,0 +1,89 @@
+// The BRDF kernel of the glossy and training-stage transfers (Eq. 15 times pi):
+//   k(w_i, w_o) = (1 - m) + pi f_s,  f_s = D F G / (4 (n.w_i)(n.w_o)),
+// GGX D with alpha = r^2, Schlick F with F0 = 0.04 on w_o.h, Smith-Schlick G with k = alpha / 2,
+// each for the unit normal n / |n|. Zero unless n.w_i > 0 and n.w_o > 0 (the callers test that).
+#pragma once
+#include "common.cuh"
+
+namespace prtgs {
+
+// a b - c d without cancellation (Kahan's difference of products with an FMA: the rounding
+// error of c d is recovered exactly and added back).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+  const float w = c * d;
+  const float e = fmaf(-c, d, w);
+  return fmaf(a, b, -w) + e;
+}
+
+// k(w_i, w_o) of Eq. 15 times pi for the unit normal n / |n|. ni, no: n . w_i, n . w_o (> 0).
+// The GGX denominator (n.h)^2 (a^2 - 1) + 1 is evaluated as (a^2 (n.v)^2 + |n x v|^2) / (|n|^2 |v|^2)
+// with v = w_i + w_o kept unnormalised (exactly, as a TwoSum pair) and n x v formed without
+// cancellation: near a sharp lobe peak 1 - (n.h)^2 is tiny, and neither the rounding of h nor an
+// FP32 normal that is unit only to rounding may leak into it.
+__device__ __forceinline__ float brdf_kernel(float nx, float ny, float nz, const float* wi, const float* wo,
+                                             float ni, float no, float alpha, float metal) {
+  float vx, vy, vz, ex, ey, ez;
+  two_sum(wi[0], wo[0], vx, ex);
+  two_sum(wi[1], wo[1], vy, ey);
+  two_sum(wi[2], wo[2], vz, ez);
+  const float cx = diff_prod(ny, vz, nz, vy) + (ny * ez - nz * ey);
+  const float cy = diff_prod(nz, vx, nx, vz) + (nz * ex - nx * ez);
+  const float cz = diff_prod(nx, vy, ny, vx) + (nx * ey - ny * ex);
+  const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
+  const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float a2 = alpha * alpha;
+  const float den = fmaf(a2 * nv, nv, cc) / (nn * vv);
+  const float D = a2 / (kPi * den * den);
+  const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
+  const float x = 1.0f - oh;
+  const float x2 = x * x;
+  const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
+  const float rn = rsqrtf(nn);
+  const float kk = 0.5f * alpha;
+  const float gi = 1.0f / fmaf(ni * rn, 1.0f - kk, kk);
+  const float go = 1.0f / fmaf(no * rn, 1.0f - kk, kk);
+  return (1.0f - metal) + kPi * 0.25f * D * F * gi * go;
+}
+
+// k and dk/dr (r the roughness, alpha = r^2) for the same arguments as brdf_kernel. With
+// t = (n.v)^2 / (|n|^2 |v|^2), s = |n x v|^2 / (|n|^2 |v|^2) (v = w_i + w_o), den = a2 t + s,
+// a2 = alpha^2 = r^4, D = a2 / (pi den^2) and g = 1 / (x (1 - kk) + kk), kk = r^2 / 2:
+//   dD/da2 = (s - a2 t) / (pi den^3),  dg/dkk = -(1 - x) g^2,
+//   dk/dr  = pi/4 F [dD/da2 4 r^3 g_i g_o - D r g_i g_o ((1 - x_i) g_i + (1 - x_o) g_o)].
+__device__ __forceinline__ float brdf_kernel_dr(float nx, float ny, float nz, const float* wi, const float* wo,
+                                                float ni, float no, float r, float metal, float& k) {
+  float vx, vy, vz, ex, ey, ez;
+  two_sum(wi[0], wo[0], vx, ex);
+  two_sum(wi[1], wo[1], vy, ey);
+  two_sum(wi[2], wo[2], vz, ez);
+  const float cx = diff_prod(ny, vz, nz, vy) + (ny * ez - nz * ey);
+  const float cy = diff_prod(nz, vx, nx, vz) + (nz * ex - nx * ez);
+  const float cz = diff_prod(nx, vy, ny, vx) + (nx * ey - ny * ex);
+  const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
+  const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float alpha = r * r;
+  const float a2 = alpha * alpha;
+  const float inv = 1.0f / (nn * vv);
+  const float tt = nv * nv * inv, ss = cc * inv;
+  const float den = fmaf(a2, tt, ss);
+  const float D = a2 / (kPi * den * den);
+  const float dD = (ss - a2 * tt) / (kPi * den * den * den);
+  const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
+  const float x = 1.0f - oh;
+  const float x2 = x * x;
+  const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
+  const float rn = rsqrtf(nn);
+  const float kk = 0.5f * alpha;
+  const float xi = ni * rn, xo = no * rn;
+  const float gi = 1.0f / fmaf(xi, 1.0f - kk, kk);
+  const float go = 1.0f / fmaf(xo, 1.0f - kk, kk);
+  const float q = kPi * 0.25f * F * gi * go;
+  k = (1.0f - metal) + q * D;
+  return q * (dD * 4.0f * alpha * r - D * r * ((1.0f - xi) * gi + (1.0f - xo) * go));
+}
+
+}  // namespace prtgs

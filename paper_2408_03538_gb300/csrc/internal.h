@@ -25,10 +25,13 @@ size_t build_bvh_workspace(int64_t n, int32_t n_scenes);
 int build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, void* ws, cudaStream_t stream);
 
 // transfer.cu
-size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p);
+// want_V / V_out: also write every receiver's visibility row V[n,S] (not with glossy matrices)
+size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p, bool want_V = false);
 int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p, float* P,
                         float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
-                        cudaStream_t stream);
+                        cudaStream_t stream, float* V_out = nullptr);
+// Y[S, (order+1)^2] of the direction set, orders 1..6 (FP64, rounded once)
+int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream);
 
 struct TraceArgs;
 // packet.cu
@@ -104,5 +107,15 @@ int render_backward(const prtgs_gaussians* g, const float* colors, int32_t k, co
 size_t l2_loss_workspace(int64_t count);
 int l2_loss(const float* image, const float* target, int64_t count, float* loss, float* dimage, void* ws,
             cudaStream_t stream);
+
+// training.cu: training-stage transfer (Eq. 28), pseudo-normal and normal loss (Eq. 24-25)
+size_t training_transfer_workspace(int32_t order, int32_t n_dirs);
+int training_transfer(const prtgs_gaussians* g, int32_t order, int32_t S, const float* dirs, const float* V,
+                      const float* cam_pos, const float* dt, float* t, float* d_roughness, float* d_metallic,
+                      void* ws, cudaStream_t stream);
+int pseudo_normal(const prtgs_camera* cam, const float* depth, float* pseudo, cudaStream_t stream);
+size_t normal_loss_workspace(int32_t width, int32_t height);
+int normal_loss(int32_t width, int32_t height, const float* normal, const float* pseudo, float* loss,
+                float* d_normal, void* ws, cudaStream_t stream);
 
 }  // namespace prtgs

@@ -13,6 +13,7 @@
 //  k_bounce  one warp per receiver: T = P + sum_s w (n.w_s)^+ (rho_j / pi) P_j (Eq. 33).
 //  k_glossy  one block per glossy splat: M = sum_s sum_o w^2 Y(w_s) k(w_s,w_o) (n.w_s)^+ V_s
 //            Y(w_o)^T (Eq. 40), factored as U^T B with B_s = sum_o k(s,o) Y(o).
+#include "brdf.cuh"
 #include "trace.cuh"
 
 namespace prtgs {
@@ -718,47 +719,6 @@ __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs
 // ---- glossy transfer matrices (Eq. 36-41) ---------------------------------------------------
 constexpr int kGlossyThreads = 128;
 
-// k(w_i, w_o) = (1 - m) + pi f_s, f_s = D F G / (4 (n.w_i)(n.w_o)); GGX D (alpha = r^2),
-// Schlick F (F0 = 0.04, on w_o.h), Smith-Schlick G (k = alpha / 2). ni, no > 0.
-// a b - c d without cancellation (Kahan's difference of products with an FMA: the rounding
-// error of c d is recovered exactly and added back).
-__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
-  const float w = c * d;
-  const float e = fmaf(-c, d, w);
-  return fmaf(a, b, -w) + e;
-}
-
-// k(w_i, w_o) of Eq. 15 times pi for the unit normal n / |n|. ni, no: n . w_i, n . w_o (> 0).
-// The GGX denominator (n.h)^2 (a^2 - 1) + 1 is evaluated as (a^2 (n.v)^2 + |n x v|^2) / (|n|^2 |v|^2)
-// with v = w_i + w_o kept unnormalised (exactly, as a TwoSum pair) and n x v formed without
-// cancellation: near a sharp lobe peak 1 - (n.h)^2 is tiny, and neither the rounding of h nor an
-// FP32 normal that is unit only to rounding may leak into it.
-__device__ __forceinline__ float brdf_kernel(float nx, float ny, float nz, const float* wi, const float* wo,
-                                             float ni, float no, float alpha, float metal) {
-  float vx, vy, vz, ex, ey, ez;
-  two_sum(wi[0], wo[0], vx, ex);
-  two_sum(wi[1], wo[1], vy, ey);
-  two_sum(wi[2], wo[2], vz, ez);
-  const float cx = diff_prod(ny, vz, nz, vy) + (ny * ez - nz * ey);
-  const float cy = diff_prod(nz, vx, nx, vz) + (nz * ex - nx * ez);
-  const float cz = diff_prod(nx, vy, ny, vx) + (nx * ey - ny * ex);
-  const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-  const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-  const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
-  const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-  const float a2 = alpha * alpha;
-  const float den = fmaf(a2 * nv, nv, cc) / (nn * vv);
-  const float D = a2 / (kPi * den * den);
-  const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
-  const float x = 1.0f - oh;
-  const float x2 = x * x;
-  const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
-  const float rn = rsqrtf(nn);
-  const float kk = 0.5f * alpha;
-  const float gi = 1.0f / fmaf(ni * rn, 1.0f - kk, kk);
-  const float go = 1.0f / fmaf(no * rn, 1.0f - kk, kk);
-  return (1.0f - metal) + kPi * 0.25f * D * F * gi * go;
-}
 
 __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, const int32_t* __restrict__ glossy_ids,
                                                            int S, int order, const float* __restrict__ dirs,
@@ -838,6 +798,11 @@ __global__ void k_glossy_slots(int64_t n, const uint8_t* __restrict__ mask, cons
   }
 }
 
+__global__ void k_iota_i32(int64_t n, int32_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)i;
+}
+
 __global__ void k_mask_u32(int64_t n, const uint8_t* __restrict__ mask, uint32_t* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = mask[i] ? 1u : 0u;
@@ -871,8 +836,9 @@ static int64_t packet_batch(int64_t n, int S) {
 
 static bool use_packets(const prtgs_transfer_params* p) { return p->walk == 0; }
 
-size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p) {
+size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_params* p, bool want_V) {
   size_t b = 2 * align_up(sizeof(unsigned int));
+  if (want_V) b += align_up(sizeof(int32_t) * (size_t)n);
   if (use_packets(p)) b += align_up(sizeof(float) * (size_t)packet_batch(n, p->n_dirs) * p->n_dirs);
   if (sh_count(p->sh_order) > kMaxC) b += align_up(sizeof(float) * (size_t)p->n_dirs * sh_count(p->sh_order));
   if (p->flags & PRTGS_BOUNCE) {
@@ -931,7 +897,7 @@ static int device_sms() {
 
 int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p, float* P,
                         float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, float* V_out) {
   const int64_t n = g->n;
   if (n == 0) return PRTGS_OK;
   const int S = p->n_dirs;
@@ -960,7 +926,11 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   int32_t* slot = nullptr;
   int32_t* gids = nullptr;
   float* Vg = nullptr;
-  if (p->flags & PRTGS_GLOSSY) {
+  if (V_out) {  // every receiver's visibility row: identity slots into V_out (no glossy matrices)
+    slot = c.take<int32_t>(n);
+    Vg = V_out;
+    k_iota_i32<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, slot);
+  } else if (p->flags & PRTGS_GLOSSY) {
     slot = c.take<int32_t>(n);
     gids = c.take<int32_t>(n);
     uint32_t* flags = c.take<uint32_t>(n);
@@ -993,7 +963,7 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   a.flags = p->flags;
   a.P = P;
   a.idx = idx;
-  a.Vg = glossy ? Vg : nullptr;
+  a.Vg = (glossy || V_out) ? Vg : nullptr;
   a.glossy_slot = slot;
   a.status = status;
   a.work = work;
@@ -1054,6 +1024,13 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
                                                                g->roughness, g->metallic, Vg, M);
     PRTGS_CHECK_LAUNCH();
   }
+  return PRTGS_OK;
+}
+
+int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream) {
+  if (S <= 0) return PRTGS_OK;
+  k_sh_table<<<(unsigned)((S + 127) / 128), 128, 0, counted(stream)>>>(S, order, dirs, Y);
+  PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }
 

@@ -113,3 +113,55 @@ def test_layout_queries_are_consistent():
     g0 = L.Gaussians()
     bvh0 = L.BVH(0, 1, 0, None, None, None, None, None, None, ctypes.c_void_p(256))
     assert lib.prtgs_build_bvh(ctypes.byref(g0), ctypes.byref(bvh0), None, None, 0, None) == L.OK
+
+
+def test_training_calls_validate_on_the_host():
+    """The visibility cache, training transfer, pseudo-normal and normal-loss entry points reject
+    bad arguments before any device work."""
+    lib = L.load()
+    fake = ctypes.c_void_p(256)
+    g = L.Gaussians(10, fake, fake, fake, fake, fake, fake, fake, fake, None)
+    bvh = L.BVH(10, 1, 0, fake, fake, fake, fake, fake, fake, fake)
+    cam = (ctypes.c_float * 3)(0.0, -3.0, 1.0)
+    # visibility: only PRTGS_SHADOW, P and V required
+    pb = L.TransferParams(3, 64, fake, 0.0, 1.0, L.SHADOW | L.BOUNCE, 0)
+    assert lib.prtgs_precompute_visibility(ctypes.byref(g), ctypes.byref(bvh), ctypes.byref(pb), fake, fake, None,
+                                           None, 0, None) == L.ERR_UNSUPPORTED
+    ps = L.TransferParams(3, 64, fake, 0.0, 1.0, L.SHADOW, 0)
+    assert lib.prtgs_precompute_visibility(ctypes.byref(g), ctypes.byref(bvh), ctypes.byref(ps), None, fake, None,
+                                           None, 0, None) == L.ERR_INVALID_ARG
+    assert lib.prtgs_precompute_visibility(ctypes.byref(g), ctypes.byref(bvh), ctypes.byref(ps), fake, fake, None,
+                                           None, 0, None) == L.ERR_WORKSPACE
+    assert lib.prtgs_visibility_workspace_size(10, ctypes.byref(ps)) > lib.prtgs_transfer_workspace_size(
+        10, 0, ctypes.byref(ps))  # the identity slots
+    # training transfer: order 1..6, directions 1..1024, camera, BRDF parameters, workspace
+    need = lib.prtgs_training_transfer_workspace_size(3, 64)
+    assert need >= 64 * 16 * 4 and lib.prtgs_training_transfer_workspace_size(7, 64) == 0
+    assert lib.prtgs_training_transfer(ctypes.byref(g), 7, 64, fake, fake, cam, fake, fake, need, None) == \
+        L.ERR_UNSUPPORTED
+    assert lib.prtgs_training_transfer(ctypes.byref(g), 3, 2000, fake, fake, cam, fake, fake, need, None) == \
+        L.ERR_UNSUPPORTED
+    assert lib.prtgs_training_transfer(ctypes.byref(g), 3, 64, fake, fake, None, fake, fake, need, None) == \
+        L.ERR_INVALID_ARG
+    nan_cam = (ctypes.c_float * 3)(0.0, float("nan"), 1.0)
+    assert lib.prtgs_training_transfer(ctypes.byref(g), 3, 64, fake, fake, nan_cam, fake, fake, need, None) == \
+        L.ERR_INVALID_ARG
+    g_nobrdf = L.Gaussians(10, fake, fake, fake, fake, fake, fake, None, None, None)
+    assert lib.prtgs_training_transfer(ctypes.byref(g_nobrdf), 3, 64, fake, fake, cam, fake, fake, need, None) == \
+        L.ERR_INVALID_ARG
+    assert lib.prtgs_training_transfer(ctypes.byref(g), 3, 64, fake, fake, cam, fake, fake, need - 1, None) == \
+        L.ERR_WORKSPACE
+    assert lib.prtgs_training_transfer_backward(ctypes.byref(g), 3, 64, fake, fake, cam, fake, None, fake, fake,
+                                                need, None) == L.ERR_INVALID_ARG
+    # pseudo-normal and normal loss
+    c = L.Camera()
+    c.width, c.height, c.fx, c.fy = 8, 6, 0.0, 10.0
+    assert lib.prtgs_pseudo_normal(ctypes.byref(c), fake, fake, None) == L.ERR_INVALID_ARG
+    c.fx = 10.0
+    assert lib.prtgs_pseudo_normal(ctypes.byref(c), None, fake, None) == L.ERR_INVALID_ARG
+    c.width = 0
+    assert lib.prtgs_pseudo_normal(ctypes.byref(c), None, None, None) == L.OK  # empty image: nothing to do
+    assert lib.prtgs_normal_loss(8, 6, fake, fake, None, None, fake, 1 << 20, None) == L.ERR_INVALID_ARG
+    nl = lib.prtgs_normal_loss_workspace_size(1920, 1080)
+    assert nl >= 8 and lib.prtgs_normal_loss(1920, 1080, fake, fake, fake, None, fake, nl - 1, None) == \
+        L.ERR_WORKSPACE
