@@ -52,10 +52,14 @@ def parse():
                          "surface-100k: the differentiable 100k step; batched-32: 32 isotropic scenes, one "
                          "graph-captured step (measurement of batching); diff-300k: differentiable relight + "
                          "1080p render of 300k isotropic splats")
-    ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders", "transfer-traffic"],
+    ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders", "transfer-traffic", "training",
+                                                       "training-small"],
                     help="kernels-small: the small profiling case of the ncu captures; sh-orders: relight + "
                          "render and transfer times at SH orders 1-6; transfer-traffic: two transfer calls of "
-                         "the workload for a DRAM-traffic capture, instead of the bench")
+                         "the workload for a DRAM-traffic capture; training: the training-stage calls (visibility "
+                         "cache, view transfer and its backward, pseudo-normal, normal loss) on the 1M workload; "
+                         "training-small: one view transfer forward and backward on 200k surface splats (S = 256, "
+                         "V of 205 MB, larger than L2) for an ncu capture; each instead of the bench")
     return ap.parse_args()
 
 
@@ -487,8 +491,14 @@ def run_kernels_small():
     for prec in (0, 1):
         api.render_relit(gg, outg["T"], L8, cam, 3, bg=bg, precision=prec, glossy_ids=gids, M=outg["M"],
                          max_pairs=4_000_000)
-    # depth and normal maps; SH order 6 transfer and relight
-    api.render_geometry(gg, cam, max_pairs=4_000_000)
+    # depth and normal maps, pseudo-normal and normal loss; the training-stage visibility cache and
+    # view transfer (forward and backward)
+    depth, nmap, _ = api.render_geometry(gg, cam, max_pairs=4_000_000)
+    api.normal_loss(nmap, api.pseudo_normal(depth, cam))
+    vis = api.precompute_visibility(gg, api.build_bvh(gg), dirs, 3)
+    tt = api.training_transfer(gg, vis["V"], dirs, 3, (0.0, -7.0, 3.0))
+    api.training_transfer_backward(gg, vis["V"], dirs, 3, (0.0, -7.0, 3.0), tt)
+    # SH order 6 transfer and relight
     P6 = api.precompute_transfer(gg, api.build_bvh(gg), dirs, 6)["P"]
     api.relight(P6, gg.albedo, torch.randn((2, 3, 49), device="cuda", generator=gen), 6)
     torch.cuda.synchronize()
@@ -516,6 +526,119 @@ def run_transfer_traffic(args):
     batch = max(32, ((1 << 26) // dirs_np.shape[0]) // 32 * 32)
     print(json.dumps({"case": "transfer-traffic", "workload": sc.n, "traced_rays_per_call": traced,
                       "k_packet_launches_per_call": math.ceil(sc.n / batch), "source_sha16": source_sha16()}))
+
+
+# Flops of one BRDF kernel evaluation in the training transfer (brdf.cuh: three TwoSums, three
+# differences of products, four dot products, D, F, G and the combination) and of the rest of
+# one (receiver, direction) term: the weight and C fused multiply-adds.
+BRDF_FLOPS = 97
+TT_TERM_FLOPS = 6
+
+
+def run_training(args):
+    """The training-stage calls on the tiled 1M workload (order 3, S = 256): the visibility cache
+    (once, with its walk), then per step the view transfer of Eq. 28, its roughness / metallic
+    backward, the pseudo-normal of the 1920x1080 depth map and the normal loss; each timed alone
+    with CUDA events (median of ``--steps``; V of 1 GB is larger than L2, the image maps are
+    re-read after an L2 flush). Algorithmic bytes and flops per launch are printed beside the
+    times, with the measured peaks."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    w, sc, dirs_np, _, _, cam = workload_inputs(WORKLOAD)
+    order, S_ = w["order"], dirs_np.shape[0]
+    C = (order + 1) ** 2
+    rng = np.random.default_rng(8)
+    sc.roughness = rng.uniform(0.15, 1.0, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    g = api.GaussianTensors.from_scene(sc)
+    dirs = torch.from_numpy(dirs_np).cuda()
+    bvh = api.build_bvh(g)
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    cam_pos = tuple(float(x) for x in cam.position)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    vis = api.precompute_visibility(g, bvh, dirs, order)
+    torch.cuda.synchronize()
+    t_vis = timed(lambda: api.precompute_visibility(g, bvh, dirs, order, out=vis), 2)
+    V = vis["V"]
+    t = api.training_transfer(g, V, dirs, order, cam_pos)
+    dt = torch.randn(t.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    reps = max(3, args.steps)
+    for _ in range(args.warmup):
+        api.training_transfer(g, V, dirs, order, cam_pos, out=t)
+        api.training_transfer_backward(g, V, dirs, order, cam_pos, dt)
+    t_fwd = timed(lambda: api.training_transfer(g, V, dirs, order, cam_pos, out=t), reps)
+    t_bwd = timed(lambda: api.training_transfer_backward(g, V, dirs, order, cam_pos, dt), reps)
+    depth, nmap, _ = api.render_geometry(g, cam, max_pairs=40_000_000)
+    Np = api.pseudo_normal(depth, cam)
+    t_pn = timed(lambda: api.pseudo_normal(depth, cam, out=Np), reps)
+    t_nl = timed(lambda: api.normal_loss(nmap, Np), reps)
+    torch.cuda.synchronize()
+    # algorithmic work: terms = (receiver, direction) pairs with n.w > 0, V > 0 and a view in front
+    nrm = sc.normals.astype(np.float64)
+    v = np.asarray(cam_pos, np.float64)[None, :] - sc.means.astype(np.float64)
+    front = np.einsum("ik,ik->i", v, nrm) > 0
+    Vh = V.cpu().numpy()
+    terms = int(((Vh > 0) & front[:, None]).sum())
+    flops_f = terms * (BRDF_FLOPS + TT_TERM_FLOPS + 2 * C)
+    bytes_f = sc.n * (S_ * 4 + 32 + C * 4)  # V row, mean, normal, roughness, metallic; t out
+    bytes_b = sc.n * (S_ * 4 + 32 + C * 4 + 8)
+    hw = cam.width * cam.height
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32 = sms * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    res = {
+        "case": "training", "workload": WORKLOAD, "n": sc.n, "n_dirs": S_, "sh_order": order,
+        "visibility_ms": t_vis, "visibility_rays_per_s": float((sc.normals.astype(np.float64) @ dirs_np.T > 0).sum())
+        / (t_vis * 1e-3),
+        "view_transfer": {"ms": t_fwd, "terms": terms, "gflop": flops_f / 1e9, "tflops": flops_f / (t_fwd * 1e-3) / 1e12,
+                          "frac_fp32_alu": flops_f / (t_fwd * 1e-3) / 1e12 / fp32, "bytes": bytes_f,
+                          "gbs": bytes_f / (t_fwd * 1e-3) / 1e9,
+                          "frac_hbm": bytes_f / (t_fwd * 1e-3) / 1e9 / pk["hbm_gbs"]},
+        "view_transfer_backward": {"ms": t_bwd, "gbs": bytes_b / (t_bwd * 1e-3) / 1e9,
+                                   "frac_hbm": bytes_b / (t_bwd * 1e-3) / 1e9 / pk["hbm_gbs"]},
+        "pseudo_normal": {"ms": t_pn, "image": f"{cam.width}x{cam.height}", "bytes": hw * 16,
+                          "gbs": hw * 16 / (t_pn * 1e-3) / 1e9},
+        "normal_loss": {"ms": t_nl, "bytes": hw * 48, "gbs": hw * 48 / (t_nl * 1e-3) / 1e9},
+        "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_alu_tflops": fp32, "source": pk_kind},
+    }
+    print(json.dumps(res))
+
+
+def run_training_small():
+    """The profiling case of the view transfer: 200k surface splats, S = 256, order 3 (V is 205 MB,
+    larger than L2, so DRAM counters mean something); one forward and one backward launch after
+    the visibility cache."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    sc = S.surface_scene(200_000, 12)
+    rng = np.random.default_rng(9)
+    sc.roughness = rng.uniform(0.15, 1.0, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    g = api.GaussianTensors.from_scene(sc)
+    dirs = torch.from_numpy(S.direction_set(256, 2)).cuda()
+    vis = api.precompute_visibility(g, api.build_bvh(g), dirs, 3)
+    cam_pos = (0.0, -7.0, 3.0)
+    t = api.training_transfer(g, vis["V"], dirs, 3, cam_pos)
+    dr, dm = api.training_transfer_backward(g, vis["V"], dirs, 3, cam_pos, t)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "training-small", "n": sc.n, "t_abs_sum": float(t.abs().sum()),
+                      "d_roughness_abs_sum": float(dr.abs().sum())}))
 
 
 def run_sh_orders():
@@ -992,6 +1115,10 @@ def main():
         run_sh_orders()
     elif args.case == "transfer-traffic":
         run_transfer_traffic(args)
+    elif args.case == "training":
+        run_training(args)
+    elif args.case == "training-small":
+        run_training_small()
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched-32":

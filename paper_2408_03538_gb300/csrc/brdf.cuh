@@ -2,6 +2,8 @@
 //   k(w_i, w_o) = (1 - m) + pi f_s,  f_s = D F G / (4 (n.w_i)(n.w_o)),
 // GGX D with alpha = r^2, Schlick F with F0 = 0.04 on w_o.h, Smith-Schlick G with k = alpha / 2,
 // each for the unit normal n / |n|. Zero unless n.w_i > 0 and n.w_o > 0 (the callers test that).
+// Quotients use the fast single-precision divide (__fdividef, 2 ulp): every divisor is a positive
+// normal number well inside its range here (den >= min(1, alpha^2), the Smith terms >= alpha/2).
 #pragma once
 #include "common.cuh"
 
@@ -34,16 +36,16 @@ __device__ __forceinline__ float brdf_kernel(float nx, float ny, float nz, const
   const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
   const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
   const float a2 = alpha * alpha;
-  const float den = fmaf(a2 * nv, nv, cc) / (nn * vv);
-  const float D = a2 / (kPi * den * den);
+  const float den = __fdividef(fmaf(a2 * nv, nv, cc), nn * vv);
+  const float D = __fdividef(a2, kPi * den * den);
   const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
   const float x = 1.0f - oh;
   const float x2 = x * x;
   const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
   const float rn = rsqrtf(nn);
   const float kk = 0.5f * alpha;
-  const float gi = 1.0f / fmaf(ni * rn, 1.0f - kk, kk);
-  const float go = 1.0f / fmaf(no * rn, 1.0f - kk, kk);
+  const float gi = __fdividef(1.0f, fmaf(ni * rn, 1.0f - kk, kk));
+  const float go = __fdividef(1.0f, fmaf(no * rn, 1.0f - kk, kk));
   return (1.0f - metal) + kPi * 0.25f * D * F * gi * go;
 }
 
@@ -67,11 +69,12 @@ __device__ __forceinline__ float brdf_kernel_dr(float nx, float ny, float nz, co
   const float cc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
   const float alpha = r * r;
   const float a2 = alpha * alpha;
-  const float inv = 1.0f / (nn * vv);
+  const float inv = __fdividef(1.0f, nn * vv);
   const float tt = nv * nv * inv, ss = cc * inv;
   const float den = fmaf(a2, tt, ss);
-  const float D = a2 / (kPi * den * den);
-  const float dD = (ss - a2 * tt) / (kPi * den * den * den);
+  const float pid2 = __fdividef(1.0f, kPi * den * den);
+  const float D = a2 * pid2;
+  const float dD = __fdividef((ss - a2 * tt) * pid2, den);
   const float oh = fminf(fmaxf(fmaf(wo[0], vx, fmaf(wo[1], vy, wo[2] * vz)) * rsqrtf(vv), 0.f), 1.f);
   const float x = 1.0f - oh;
   const float x2 = x * x;
@@ -79,8 +82,8 @@ __device__ __forceinline__ float brdf_kernel_dr(float nx, float ny, float nz, co
   const float rn = rsqrtf(nn);
   const float kk = 0.5f * alpha;
   const float xi = ni * rn, xo = no * rn;
-  const float gi = 1.0f / fmaf(xi, 1.0f - kk, kk);
-  const float go = 1.0f / fmaf(xo, 1.0f - kk, kk);
+  const float gi = __fdividef(1.0f, fmaf(xi, 1.0f - kk, kk));
+  const float go = __fdividef(1.0f, fmaf(xo, 1.0f - kk, kk));
   const float q = kPi * 0.25f * F * gi * go;
   k = (1.0f - metal) + q * D;
   return q * (dD * 4.0f * alpha * r - D * r * ((1.0f - xi) * gi + (1.0f - xo) * go));

@@ -39,18 +39,62 @@ struct TTArgs {
   float* d_metal;       // [n] (backward)
 };
 
+// The live terms of one receiver (n.w_s > 0 and V > 0; about a third of the directions) are
+// compacted through a per-warp queue of 64 entries, and the BRDF is evaluated 32 queued terms at
+// a time, so that every lane works on a live term instead of idling on the dead ones.
+constexpr int kTTQueue = 64;
+
+// Warp sum of N <= 32 per-lane values v[0..N) by recursive halving (a reduce-scatter): at the
+// step with xor offset o (16, 8, ...) a lane keeps the half of its values selected by its bit o
+// and adds its partner's copy of that half, so each step halves the values held; when one value
+// is left, the remaining offsets add it across the lanes that hold the same coefficient. Returns
+// the sum of coefficient k (set on every lane; k = -1 on lanes that duplicate another's k) with
+// log2(P) + (5 - log2(P)) shuffles in all, P the power of two >= N, instead of 5 N.
+template <int N>
+__device__ __forceinline__ float reduce_scatter(float* v, int lane, int& k) {
+  constexpr int P = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : (N <= 8 ? 8 : (N <= 16 ? 16 : 32))));
+  float w[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) w[j] = j < N ? v[j] : 0.0f;
+  int idx = 0;
+  int off = 16;
+#pragma unroll
+  for (int h = P / 2; h >= 1; h >>= 1, off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = upper ? w[j] : w[j + h];
+      const float keep = upper ? w[j + h] : w[j];
+      w[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+    if (upper) idx += h;
+  }
+  float x = w[0];
+  for (; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  // lanes that differ only in the bits below the last halving offset hold the same coefficient
+  const int dup_mask = (32 / P) - 1;
+  k = (lane & dup_mask) == 0 ? idx : -1;
+  return x;
+}
+
 template <int ORDER, bool BACKWARD>
-__global__ void __launch_bounds__(kTTThreads) k_training_transfer(TTArgs a) {
+__global__ void __launch_bounds__(kTTThreads, ORDER <= 3 ? 4 : 2) k_training_transfer(TTArgs a) {
   constexpr int C = (ORDER + 1) * (ORDER + 1);
   extern __shared__ float sm[];
   const int S = a.S;
   float* sdir = sm;              // [3S]
-  float* sY = sdir + 3 * S;      // [S][C]
+  float* sY = sdir + 3 * S;      // [C][S]: coefficient-major, so that the lanes (consecutive
+                                 // directions) read consecutive words, free of bank conflicts
   float* sdt = sY + S * C;       // [warps][C] (backward)
+  __shared__ int qs_all[kTTWarps][kTTQueue];    // queued direction
+  __shared__ float qw_all[kTTWarps][kTTQueue];  // its (n.w_s) V_s
   for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sdir[i] = a.dirs[i];
-  for (int i = threadIdx.x; i < S * C; i += blockDim.x) sY[i] = a.Ytab[i];
+  for (int i = threadIdx.x; i < S * C; i += blockDim.x) sY[i] = a.Ytab[(i % S) * C + i / S];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int* qs = qs_all[warp];
+  float* qw = qw_all[warp];
   const float wq = 4.0f * kPi / (float)S;
   for (int64_t i = (int64_t)blockIdx.x * kTTWarps + warp; i < a.n; i += (int64_t)gridDim.x * kTTWarps) {
     const float nx = __ldg(a.normals + 3 * i), ny = __ldg(a.normals + 3 * i + 1), nz = __ldg(a.normals + 3 * i + 2);
@@ -65,58 +109,94 @@ __global__ void __launch_bounds__(kTTThreads) k_training_transfer(TTArgs a) {
     const float alpha = r * r;
     const bool front = no > 0.0f;  // k = 0 for a view below the splat's horizon
     const float* Vi = a.V + i * S;
-    if (!BACKWARD) {
-      float acc[C];
+    float acc[BACKWARD ? 1 : C];
 #pragma unroll
-      for (int k = 0; k < C; ++k) acc[k] = 0.0f;
-      if (front) {
-        for (int s = lane; s < S; s += 32) {
-          const float* d = sdir + 3 * s;
-          const float c = fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));
-          if (!(c > 0.0f)) continue;
-          const float vis = __ldg(Vi + s);
-          if (vis == 0.0f) continue;
-          const float f = wq * brdf_kernel(nx, ny, nz, d, v, c, no, alpha, m) * c * vis;
-          const float* y = sY + s * C;
-#pragma unroll
-          for (int k = 0; k < C; ++k) acc[k] = fmaf(f, y[k], acc[k]);
-        }
-      }
-      float out0 = 0.0f, out1 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < C; ++k) {
-        const float val = warp_sum(acc[k]);
-        if ((k & 31) == lane) {
-          if (k < 32) out0 = val;
-          else out1 = val;
-        }
-      }
-      float* ti = a.t + i * C;
-      if (lane < C) ti[lane] = out0;
-      if (32 + lane < C) ti[32 + lane] = out1;
-    } else {
-      float* dts = sdt + warp * C;
+    for (int k = 0; k < (BACKWARD ? 1 : C); ++k) acc[k] = 0.0f;
+    float gr = 0.0f, gm = 0.0f;
+    float* dts = sdt + warp * C;
+    if (BACKWARD) {
       for (int k = lane; k < C; k += 32) dts[k] = __ldg(a.dt + i * C + k);
       __syncwarp();
-      float gr = 0.0f, gm = 0.0f;
-      if (front) {
-        for (int s = lane; s < S; s += 32) {
+    }
+    // one live term (direction s, cv = (n.w_s) V_s) on this lane
+    auto term = [&](int s, float cv) {
+      const float* d = sdir + 3 * s;
+      if (!BACKWARD) {
+        const float c = fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));  // > 0 for a queued term
+        const float f = wq * brdf_kernel(nx, ny, nz, d, v, c, no, alpha, m) * cv;
+#pragma unroll
+        for (int k = 0; k < (BACKWARD ? 1 : C); ++k) acc[k] = fmaf(f, sY[k * S + s], acc[k]);
+      } else {
+        float q = 0.0f;
+#pragma unroll
+        for (int k = 0; k < C; ++k) q = fmaf(dts[k], sY[k * S + s], q);
+        float kv;
+        const float dk = brdf_kernel_dr(nx, ny, nz, d, v, fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2])), no, r, m, kv);
+        const float f = wq * cv * q;
+        gr = fmaf(f, dk, gr);
+        gm -= f;  // dk/dm = -1
+      }
+    };
+    if (front) {
+      int qn = 0;  // warp-uniform queue length, < 32 between chunks
+      for (int base = 0; base < S; base += 32) {
+        const int s = base + lane;
+        float cv = 0.0f;
+        if (s < S) {
           const float* d = sdir + 3 * s;
           const float c = fmaf(nx, d[0], fmaf(ny, d[1], nz * d[2]));
-          if (!(c > 0.0f)) continue;
-          const float vis = __ldg(Vi + s);
-          if (vis == 0.0f) continue;
-          const float* y = sY + s * C;
-          float q = 0.0f;
-#pragma unroll
-          for (int k = 0; k < C; ++k) q = fmaf(dts[k], y[k], q);
-          float kv;
-          const float dk = brdf_kernel_dr(nx, ny, nz, d, v, c, no, r, m, kv);
-          const float f = wq * c * vis * q;
-          gr = fmaf(f, dk, gr);
-          gm -= f;  // dk/dm = -1
+          if (c > 0.0f) cv = c * __ldg(Vi + s);
+        }
+        const bool live = cv != 0.0f;  // a NaN visibility stays live and reaches the output
+        const unsigned mask = __ballot_sync(0xffffffffu, live);
+        if (live) {
+          const int pos = qn + __popc(mask & lt_mask);
+          qs[pos] = s;
+          qw[pos] = cv;
+        }
+        qn += __popc(mask);
+        __syncwarp();
+        if (qn >= 32) {  // 32 live terms: one per lane
+          term(qs[lane], qw[lane]);
+          const int rest = qn - 32;
+          int ts = 0;
+          float tw = 0.0f;
+          if (lane < rest) {
+            ts = qs[32 + lane];
+            tw = qw[32 + lane];
+          }
+          __syncwarp();
+          if (lane < rest) {
+            qs[lane] = ts;
+            qw[lane] = tw;
+          }
+          qn = rest;
+          __syncwarp();
         }
       }
+      if (lane < qn) term(qs[lane], qw[lane]);
+      __syncwarp();
+    }
+    if (!BACKWARD) {
+      float* ti = a.t + i * C;
+      if (C <= 32) {
+        int k;
+        const float val = reduce_scatter<(BACKWARD ? 1 : C)>(acc, lane, k);
+        if (k >= 0 && k < C) ti[k] = val;
+      } else {
+        float out0 = 0.0f, out1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < (BACKWARD ? 1 : C); ++k) {
+          const float val = warp_sum(acc[k]);
+          if ((k & 31) == lane) {
+            if (k < 32) out0 = val;
+            else out1 = val;
+          }
+        }
+        if (lane < C) ti[lane] = out0;
+        if (32 + lane < C) ti[32 + lane] = out1;
+      }
+    } else {
       gr = warp_sum(gr);
       gm = warp_sum(gm);
       if (lane == 0) {
