@@ -26,8 +26,8 @@
  *    no further tensor-core work.
  *
  * Notation follows the paper: N Gaussians, S sphere directions, C = (order+1)^2 real SH
- * coefficients (order <= 3, so C <= 16, for every path; orders 4-6, C <= 49, where a call says
- * so), k lights, H x W image.
+ * coefficients (orders 1-6, so C <= 49, on every path; the tensor-core relight pads K = C to a
+ * multiple of 16), k lights, H x W image.
  */
 #ifndef PRTGS_H
 #define PRTGS_H
@@ -45,7 +45,7 @@ typedef struct CUstream_st* prtgs_stream_t; /* a cudaStream_t; NULL = legacy def
 #define PRTGS_OK 0
 #define PRTGS_ERR_INVALID_ARG (-1)  /* null pointer, negative size, value out of range */
 #define PRTGS_ERR_SHAPE (-2)        /* inconsistent sizes */
-#define PRTGS_ERR_UNSUPPORTED (-3)  /* SH order outside 1..3, too many scenes, ... */
+#define PRTGS_ERR_UNSUPPORTED (-3)  /* SH order outside 1..6, too many scenes, ... */
 #define PRTGS_ERR_WORKSPACE (-4)    /* workspace too small or misaligned */
 #define PRTGS_ERR_CUDA (-5)         /* a CUDA launch or copy failed */
 
@@ -144,9 +144,10 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
 
 /*
  * Transfer precompute parameters (Sec. 4.4-4.5).
- *   sh_order        1..3 (C = (order+1)^2 coefficients); 4..6 (25-49 coefficients, the SH of the
- *                   direction set tabulated per call) without PRTGS_GLOSSY (else
- *                   PRTGS_ERR_UNSUPPORTED)
+ *   sh_order        1..6 (C = (order+1)^2 coefficients; for 4..6 the SH of the direction set
+ *                   are tabulated per call). With PRTGS_GLOSSY the block of the glossy matrices
+ *                   holds 3 S + 3 S C floats of shared memory: S x C above 227 KB of it (e.g.
+ *                   S > 384 at order 6) -> PRTGS_ERR_UNSUPPORTED
  *   n_dirs, dirs    S shared world-space directions [S,3] (device); weight 4 pi / S each
  *   t_min           a ray stops once its transmittance falls below t_min (bounded error
  *                   t_min per ray); 0 disables early exit. Suggested 2^-30.
@@ -286,11 +287,13 @@ int prtgs_training_transfer_backward(const prtgs_gaussians* g, int32_t sh_order,
  * with T [n,C] (t_channels = 1) or [n,3,C] (t_channels = 3). Glossy splats (n_glossy > 0,
  * glossy_ids[n_glossy] their Gaussian indices, M[n_glossy,C,C]) use
  *   t_eff[a] = sum_b M[a,b] Y_b(v_i), v_i = normalize(cam_pos - mean_i).
- * L[k,3,C] light SH per light and channel. sh_order 1..3, or 4..6 with PRTGS_PREC_FP32 and no
- * glossy splats. precision: PRTGS_PREC_*. The tensor-core paths
- * take every row through tcgen05 (one MMA of N = 3k for t_channels = 1, three of N = k for
- * t_channels = 3) and then rewrite the glossy rows in FP32; they need 3k <= 256 (t_channels 1)
- * or k <= 160 (t_channels 3: three accumulators in the 512 TMEM columns), otherwise
+ * L[k,3,C] light SH per light and channel. sh_order 1..6. precision: PRTGS_PREC_*. The
+ * tensor-core paths take every row through tcgen05 (one MMA chain of N = 3k for t_channels = 1,
+ * three of N = k for t_channels = 3, K = C padded to 16 per K block: one block for orders 1-3,
+ * 2-4 for orders 4-6) and then rewrite the glossy rows in FP32; they need 3k <= 256
+ * (t_channels 1) or k <= 160 (t_channels 3: three accumulators in the 512 TMEM columns), and the
+ * lights of every K block plus one K block of the rows in one CTA's shared memory (e.g. at order
+ * 6 with BF16x3: k <= 64 for t_channels 3), otherwise
  * PRTGS_ERR_UNSUPPORTED.
  * cam_pos and means may be NULL when n_glossy == 0.
  * status (device int32, may be NULL) receives PRTGS_STATUS_TIMEOUT when a tensor-core wait gave

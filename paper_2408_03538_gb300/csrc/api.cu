@@ -30,8 +30,7 @@ int check_gaussians(const prtgs_gaussians* g) {
   return PRTGS_OK;
 }
 
-int check_order(int32_t order) { return (order >= 1 && order <= 3) ? PRTGS_OK : PRTGS_ERR_UNSUPPORTED; }
-// Orders 4-6 (25-49 coefficients) for the shadowed transfer and the FP32 relight.
+// SH orders 1-6 (4-49 coefficients).
 static int check_order_high(int32_t order) { return (order >= 1 && order <= 6) ? PRTGS_OK : PRTGS_ERR_UNSUPPORTED; }
 
 int finish(int rc) {
@@ -127,8 +126,8 @@ int prtgs_precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, co
   if (rc) return rc;
   if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
   if ((rc = check_order_high(p->sh_order))) return rc;
-  if (p->sh_order > 3 && (p->flags & PRTGS_GLOSSY)) return PRTGS_ERR_UNSUPPORTED;
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if ((p->flags & PRTGS_GLOSSY) && !prtgs::glossy_fits(p->n_dirs, p->sh_order)) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f) || !(p->same_surface_t >= 0.f)) return PRTGS_ERR_INVALID_ARG;
   if (p->n_bounces < 0 || p->n_bounces > 64) return PRTGS_ERR_INVALID_ARG;
   if (p->walk < 0 || p->walk > 1 || p->packet_dirs < 0 || p->packet_dirs > 64) return PRTGS_ERR_INVALID_ARG;
@@ -158,7 +157,7 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
   int rc = check_gaussians(g);
   if (rc) return rc;
   if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
-  if ((rc = check_order(p->sh_order))) return rc;
+  if ((rc = check_order_high(p->sh_order))) return rc;
   if (p->flags & ~PRTGS_SHADOW) return PRTGS_ERR_UNSUPPORTED;
   if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
   if (!p->dirs || !(p->t_min >= 0.f)) return PRTGS_ERR_INVALID_ARG;
@@ -277,8 +276,9 @@ int prtgs_relight(int64_t n, int32_t sh_order, const float* T, int32_t t_channel
   if ((rc = check_order_high(sh_order))) return rc;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
-  if (sh_order > 3 && (precision != PRTGS_PREC_FP32 || n_glossy > 0)) return PRTGS_ERR_UNSUPPORTED;
   if (n == 0 || k == 0) return PRTGS_OK;
+  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_fits(sh_order, k, t_channels, precision))
+    return PRTGS_ERR_UNSUPPORTED;
   if (!T || !albedo || !L || !colors) return PRTGS_ERR_INVALID_ARG;
   if (n_glossy > 0 && (!glossy_ids || !M || !means || !cam_pos)) return PRTGS_ERR_INVALID_ARG;
   rc = check_ws(workspace, workspace_bytes, relight_workspace(n, sh_order, k, precision));
@@ -293,19 +293,19 @@ int prtgs_relight_batched(int64_t n, int32_t sh_order, const float* T, int32_t t
                           prtgs_stream_t stream) {
   int rc;
   if (n < 0 || k < 0 || n_scenes < 1) return PRTGS_ERR_SHAPE;
-  if ((rc = check_order(sh_order))) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
   if (n == 0 || k == 0) return PRTGS_OK;
   if (!T || !albedo || !L || !colors || !scene_offsets) return PRTGS_ERR_INVALID_ARG;
-  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_shape(k, t_channels, nullptr, nullptr))
+  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_fits(sh_order, k, t_channels, precision))
     return PRTGS_ERR_UNSUPPORTED;
   return finish(relight_batched(n, sh_order, T, t_channels, albedo, scene_offsets, n_scenes, L, k, precision,
                                 colors, status, tc_wait_polls, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 size_t prtgs_relight_backward_workspace_size(int64_t n, int32_t sh_order, int32_t k) {
-  if (n < 0 || k < 0 || check_order(sh_order)) return 0;
+  if (n < 0 || k < 0 || check_order_high(sh_order)) return 0;
   return relight_backward_workspace(n, sh_order, k);
 }
 
@@ -314,7 +314,7 @@ int prtgs_relight_backward(int64_t n, int32_t sh_order, const float* T, int32_t 
                            void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
   int rc;
   if (n < 0 || k < 0) return PRTGS_ERR_SHAPE;
-  if ((rc = check_order(sh_order))) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (k == 0) return PRTGS_OK;
   if (!dL || (n > 0 && (!T || !albedo || !L || !dcolors || !d_albedo))) return PRTGS_ERR_INVALID_ARG;
@@ -354,7 +354,7 @@ static int check_camera(const prtgs_camera* cam) {
 
 size_t prtgs_render_relit_workspace_size(int64_t n, int32_t sh_order, int32_t width, int32_t height,
                                          int64_t max_pairs) {
-  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0 || check_order(sh_order)) return 0;
+  if (n < 0 || width <= 0 || height <= 0 || max_pairs < 0 || check_order_high(sh_order)) return 0;
   return render_relit_workspace(n, sh_order, width, height, max_pairs);
 }
 
@@ -366,7 +366,7 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
   int rc = check_gaussians(g);
   if (rc) return rc;
   if ((rc = check_camera(cam))) return rc;
-  if ((rc = check_order(sh_order))) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
   if (!st || st->n != g->n || st->n_scenes != 1 || st->width != cam->width || st->height != cam->height)
     return PRTGS_ERR_SHAPE;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
@@ -374,7 +374,7 @@ int prtgs_render_relit(const prtgs_gaussians* g, int32_t sh_order, const float* 
   if (precision < PRTGS_PREC_FP32 || precision > PRTGS_PREC_BF16) return PRTGS_ERR_INVALID_ARG;
   if (k < 1 || k > 256 || !L || !bg || !image || (g->n > 0 && (!T || !g->albedo))) return PRTGS_ERR_INVALID_ARG;
   if (n_glossy > 0 && (!glossy_ids || !M || !g->means)) return PRTGS_ERR_INVALID_ARG;
-  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_shape(k, 3, nullptr, nullptr)) return PRTGS_ERR_UNSUPPORTED;
+  if (precision != PRTGS_PREC_FP32 && !prtgs::relight_tc_fits(sh_order, k, 3, precision)) return PRTGS_ERR_UNSUPPORTED;
   rc = check_ws(workspace, workspace_bytes,
                 render_relit_workspace(g->n, sh_order, cam->width, cam->height, st->max_pairs));
   if (rc) return rc;
@@ -527,7 +527,7 @@ int prtgs_l2_loss_batched(const float* images, const float* targets, int64_t cou
 }
 
 size_t prtgs_relight_backward_batched_workspace_size(int64_t n, int32_t n_scenes, int32_t sh_order, int32_t k) {
-  if (n < 0 || k < 0 || n_scenes < 1 || check_order(sh_order)) return 0;
+  if (n < 0 || k < 0 || n_scenes < 1 || check_order_high(sh_order)) return 0;
   return relight_backward_batched_workspace(n, n_scenes, sh_order, k);
 }
 
@@ -538,7 +538,7 @@ int prtgs_relight_backward_batched(int64_t n, int32_t sh_order, const float* T, 
   int rc;
   if (n < 0 || k < 0 || n_scenes < 1) return PRTGS_ERR_SHAPE;
   if (n_scenes > 65535) return PRTGS_ERR_UNSUPPORTED;
-  if ((rc = check_order(sh_order))) return rc;
+  if ((rc = check_order_high(sh_order))) return rc;
   if (t_channels != 1 && t_channels != 3) return PRTGS_ERR_SHAPE;
   if (k == 0) return PRTGS_OK;
   if (!dL || !scene_offsets || (n > 0 && (!T || !albedo || !L || !dcolors || !d_albedo))) return PRTGS_ERR_INVALID_ARG;

@@ -109,7 +109,7 @@ int prtgs_autotune(int32_t kernel_id, const void* args, int32_t repeats, prtgs_s
              (double)a->t_channels, (double)a->n_scenes))
       return PRTGS_ERR_INVALID_ARG;
     int precs[2] = {PRTGS_PREC_FP32, PRTGS_PREC_BF16X3};
-    const int nv = prtgs::relight_tc_shape(a->k, a->t_channels, nullptr, nullptr) ? 2 : 1;
+    const int nv = prtgs::relight_tc_fits(a->sh_order, a->k, a->t_channels, PRTGS_PREC_BF16X3) ? 2 : 1;
     for (int v = 0; v < nv; ++v) {
       const float ms = time_variant(
           [&]() {

@@ -92,6 +92,57 @@ __device__ __forceinline__ void sh_eval_dyn(int order, float x, float y, float z
   }
 }
 
+// ---- real SH of orders 4-6 in FP32 (the same basis and index l*l+l+m): Y_l0 = K_l0 Q_l^0(z),
+// Y_l(+-m) = sqrt2 K_lm Q_l^m(z) {Re, Im}(x + i y)^m with Q_l^m = P_l^m / sin^m (Condon-Shortley
+// phase): Q_m^m = (-1)^m (2m-1)!!, Q_{m+1}^m = (2m+1) z Q_m^m,
+// (l-m) Q_l^m = (2l-1) z Q_{l-1}^m - (l+m-1) Q_{l-2}^m, K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+__host__ __device__ constexpr double sh_k2(int l, int m) {
+  double r = (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846);
+  for (int j = l - m + 1; j <= l + m; ++j) r /= (double)j;
+  return r;
+}
+
+template <int ORDER>
+__device__ __forceinline__ void sh_eval_rec(float x, float y, float z, float* Y) {
+  float re = 1.0f, im = 0.0f, qmm = 1.0f;
+#pragma unroll
+  for (int m = 0; m <= ORDER; ++m) {
+    if (m > 0) {
+      const float r2 = re * x - im * y, i2 = re * y + im * x;
+      re = r2;
+      im = i2;
+      qmm *= -(2.0f * m - 1.0f);
+    }
+    float q2 = 0.0f, q1 = qmm;
+#pragma unroll
+    for (int l = m; l <= ORDER; ++l) {
+      float q;
+      if (l == m) q = qmm;
+      else if (l == m + 1) q = (2.0f * m + 1.0f) * z * qmm;
+      else q = ((2.0f * l - 1.0f) * z * q1 - (float)(l + m - 1) * q2) * (1.0f / (float)(l - m));
+      if (l > m) {
+        q2 = q1;
+        q1 = q;
+      }
+      const float K = (float)sh_k2(l, m);
+      if (m == 0) {
+        Y[l * l + l] = sqrtf(K) * q;
+      } else {
+        const float f = sqrtf(2.0f * K) * q;
+        Y[l * l + l + m] = f * re;
+        Y[l * l + l - m] = f * im;
+      }
+    }
+  }
+}
+
+// Orders 1-3 in the Cartesian form above, 4-6 by the recurrence.
+template <int ORDER>
+__device__ __forceinline__ void sh_eval_any(float x, float y, float z, float* Y) {
+  if constexpr (ORDER <= 3) sh_eval<ORDER>(x, y, z, Y);
+  else sh_eval_rec<ORDER>(x, y, z, Y);
+}
+
 // ---- error-free transformations (Knuth TwoSum) for compensated sums
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);

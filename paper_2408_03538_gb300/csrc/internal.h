@@ -30,6 +30,8 @@ size_t transfer_workspace(int64_t n, int64_t n_glossy, const prtgs_transfer_para
 int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p, float* P,
                         float* T, int32_t* idx, float* M, int64_t n_glossy, int32_t* status, void* ws,
                         cudaStream_t stream, float* V_out = nullptr);
+// whether the glossy matrices of S directions at this order fit one block's shared memory
+bool glossy_fits(int S, int order);
 // Y[S, (order+1)^2] of the direction set, orders 1..6 (FP64, rounded once)
 int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream);
 
@@ -53,6 +55,7 @@ int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels
                     float* colors, int32_t* status, unsigned tc_wait_polls, cudaStream_t stream);
 // relight_tc.cu
 int relight_tc_shape(int32_t k, int32_t t_channels, int* n_pad, int* tmem_cols);
+int relight_tc_fits(int32_t order, int32_t k, int32_t t_channels, int32_t precision);
 int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, const float* albedo, const float* L,
                int32_t k, int32_t precision, const int64_t* offsets, int32_t n_scenes, float* colors,
                int32_t* status, unsigned tc_wait_polls, cudaStream_t stream);

@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_glossy(int64_t n, i
   const int64_t i = ids[g];
   float vx = cam[0] - means[3 * i], vy = cam[1] - means[3 * i + 1], vz = cam[2] - means[3 * i + 2];
   float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
-  float Y[kMaxC];
-  sh_eval<ORDER>(vx * rn, vy * rn, vz * rn, Y);
+  float Y[C];
+  sh_eval_any<ORDER>(vx * rn, vy * rn, vz * rn, Y);
   float te[C];
 #pragma unroll
   for (int a = 0; a < C; ++a) {
@@ -119,6 +119,18 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_any(int64_t n, int 
 
 size_t relight_workspace(int64_t, int32_t, int32_t, int32_t) { return 0; }
 
+template <int ORDER>
+static void launch_relight_glossy(int64_t n, int64_t n_glossy, const int32_t* ids, const float* M, const float* means,
+                                  const float* cam, const float* albedo, const float* L, int k, float* colors,
+                                  cudaStream_t stream) {
+  constexpr int C = (ORDER + 1) * (ORDER + 1);
+  const size_t smem = sizeof(float) * k * 3 * C;
+  cudaFuncSetAttribute(k_relight_glossy<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const unsigned grid = (unsigned)((n_glossy + kRelightThreads - 1) / kRelightThreads);
+  k_relight_glossy<ORDER><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, ids, M, means, cam, albedo, L, k,
+                                                                            colors);
+}
+
 template <int C>
 static void launch_relight_c(int64_t n, const float* T, int tch, const float* albedo, const float* L, int k,
                              float* colors, cudaStream_t stream) {
@@ -160,16 +172,14 @@ int relight(int64_t n, int32_t order, const float* T, int32_t t_channels, const 
     PRTGS_CHECK_LAUNCH();
   }
   if (n_glossy > 0) {
-    const int C = sh_count(order);
-    size_t smem = sizeof(float) * k * 3 * C;
-    unsigned grid = (unsigned)((n_glossy + kRelightThreads - 1) / kRelightThreads);
     switch (order) {
-      case 1: k_relight_glossy<1><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
-                                                                          albedo, L, k, colors); break;
-      case 2: k_relight_glossy<2><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means, cam_pos,
-                                                                          albedo, L, k, colors); break;
-      default: k_relight_glossy<3><<<grid, kRelightThreads, smem, counted(stream)>>>(n, n_glossy, glossy_ids, M, means,
-                                                                           cam_pos, albedo, L, k, colors); break;
+      case 1: launch_relight_glossy<1>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      case 2: launch_relight_glossy<2>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      case 3: launch_relight_glossy<3>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      case 4: launch_relight_glossy<4>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      case 5: launch_relight_glossy<5>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      case 6: launch_relight_glossy<6>(n, n_glossy, glossy_ids, M, means, cam_pos, albedo, L, k, colors, stream); break;
+      default: return PRTGS_ERR_UNSUPPORTED;
     }
     PRTGS_CHECK_LAUNCH();
   }
@@ -203,8 +213,8 @@ __global__ void k_glossy_features(int64_t n, int64_t n_glossy, const int32_t* __
   const int64_t i = ids[g];
   const float vx = cx - means[3 * i], vy = cy - means[3 * i + 1], vz = cz - means[3 * i + 2];
   const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
-  float Y[kMaxC];
-  sh_eval<ORDER>(vx * rn, vy * rn, vz * rn, Y);
+  float Y[C];
+  sh_eval_any<ORDER>(vx * rn, vy * rn, vz * rn, Y);
   float r[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) r[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
@@ -251,6 +261,45 @@ __global__ void __launch_bounds__(kRelightThreads) k_pixel_relight(int64_t n_pix
   }
 }
 
+// Orders 4-6: one thread per pixel, one channel at a time (its C coefficients in registers), the
+// lights in shared memory.
+template <int C>
+__global__ void __launch_bounds__(kRelightThreads) k_pixel_relight_hi(int64_t n_pix, const float* __restrict__ TI,
+                                                                      const float* __restrict__ final_T,
+                                                                      const float* __restrict__ bg,
+                                                                      const float* __restrict__ L, int k,
+                                                                      float* __restrict__ image) {
+  extern __shared__ float sL[];  // [k][3][C]
+  for (int e = threadIdx.x; e < k * 3 * C; e += blockDim.x) sL[e] = L[e];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  const float ft = __ldg(final_T + p);
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    float t[C];
+#pragma unroll
+    for (int m = 0; m < C; ++m) t[m] = __ldg(TI + ((int64_t)m * 3 + c) * n_pix + p);
+    const float b = bg[c] * ft;
+    for (int l = 0; l < k; ++l) {
+      const float* Ll = sL + (l * 3 + c) * C;
+      float d = b;
+#pragma unroll
+      for (int m = 0; m < C; ++m) d = fmaf(t[m], Ll[m], d);
+      image[((int64_t)l * 3 + c) * n_pix + p] = d;
+    }
+  }
+}
+
+template <int C>
+static void launch_pixel_relight_hi(int64_t n_pix, const float* TI, const float* final_T, const float* bg,
+                                    const float* L, int k, float* image, cudaStream_t stream) {
+  const size_t smem = sizeof(float) * k * 3 * C;
+  cudaFuncSetAttribute(k_pixel_relight_hi<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const unsigned blocks = (unsigned)((n_pix + kRelightThreads - 1) / kRelightThreads);
+  k_pixel_relight_hi<C><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, final_T, bg, L, k, image);
+}
+
 size_t render_relit_workspace(int64_t n, int32_t order, int32_t width, int32_t height, int64_t max_pairs) {
   const int C = sh_count(order);
   const int64_t n_pix = (int64_t)width * height;
@@ -278,11 +327,17 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
     if (n_glossy > 0) {
       const unsigned gb = (unsigned)((n_glossy + 255) / 256);
       const float px = cam->pos[0], py = cam->pos[1], pz = cam->pos[2];
+#define PRTGS_GF(O) k_glossy_features<O><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, \
+                                                                         g->albedo, F)
       switch (order) {
-        case 1: k_glossy_features<1><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
-        case 2: k_glossy_features<2><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
-        default: k_glossy_features<3><<<gb, 256, 0, counted(stream)>>>(n, n_glossy, glossy_ids, M, g->means, px, py, pz, g->albedo, F); break;
+        case 1: PRTGS_GF(1); break;
+        case 2: PRTGS_GF(2); break;
+        case 3: PRTGS_GF(3); break;
+        case 4: PRTGS_GF(4); break;
+        case 5: PRTGS_GF(5); break;
+        default: PRTGS_GF(6); break;
       }
+#undef PRTGS_GF
     }
     PRTGS_CHECK_LAUNCH();
   }
@@ -296,7 +351,10 @@ int render_relit(const prtgs_gaussians* g, int32_t order, const float* T, int32_
   switch (order) {
     case 1: k_pixel_relight<4><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
     case 2: k_pixel_relight<9><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
-    default: k_pixel_relight<16><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    case 3: k_pixel_relight<16><<<blocks, kRelightThreads, smem, counted(stream)>>>(n_pix, TI, st->final_T, bg, L, k, image); break;
+    case 4: launch_pixel_relight_hi<25>(n_pix, TI, st->final_T, bg, L, k, image, stream); break;
+    case 5: launch_pixel_relight_hi<36>(n_pix, TI, st->final_T, bg, L, k, image, stream); break;
+    default: launch_pixel_relight_hi<49>(n_pix, TI, st->final_T, bg, L, k, image, stream); break;
   }
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
@@ -340,6 +398,91 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_batched(int64_t n, 
   }
 }
 
+// Orders 4-6, many scenes: as k_relight_any, scene b's lights L[b] and colour block [k, n_b, 3].
+__global__ void __launch_bounds__(kRelightThreads) k_relight_any_batched(int64_t n, int C, int tch,
+                                                                         const float* __restrict__ T,
+                                                                         const float* __restrict__ albedo,
+                                                                         const int64_t* __restrict__ offsets,
+                                                                         int n_scenes, const float* __restrict__ L,
+                                                                         int k, float* __restrict__ colors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = find_scene(offsets, n_scenes, i);
+  const int64_t ob = offsets[b], nb = offsets[b + 1] - ob;
+  const float* Lb = L + (int64_t)b * k * 3 * C;
+  float* cb = colors + 3 * (int64_t)k * ob;
+  float r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[c] = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+  for (int l = 0; l < k; ++l) {
+    float* out = cb + ((int64_t)l * nb + (i - ob)) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* t = T + (i * tch + (tch > 1 ? c : 0)) * C;
+      const float* Ll = Lb + ((int64_t)l * 3 + c) * C;
+      float d = 0.f;
+      for (int m = 0; m < C; ++m) d = fmaf(__ldg(t + m), __ldg(Ll + m), d);
+      out[c] = r[c] * d;
+    }
+  }
+}
+
+// Orders 4-6 backward, per Gaussian and one channel at a time: with G[c][m] = sum_k dc[k,i,c]
+// L_k[c][m] (C registers), d_albedo[c] = (T_i[c] . G[c]) / pi and dT[c][m] = (rho[c]/pi) G[c][m]
+// (summed over c for a one-channel T): the same sums as k_relight_bwd_local, reassociated so that
+// only C accumulators (2 C for a one-channel T) are live instead of 2 x 3 C.
+template <int C, bool BATCHED>
+__global__ void __launch_bounds__(kRelightThreads) k_relight_bwd_local_hi(
+    int64_t n, int tch, const float* __restrict__ T, const float* __restrict__ albedo,
+    const int64_t* __restrict__ offs, int B, const float* __restrict__ L, int k, const float* __restrict__ dcol,
+    float* __restrict__ d_albedo, float* __restrict__ dT) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = 0;
+  int64_t o = 0, nb = n;
+  if (BATCHED) {
+    b = find_scene(offs, B, i);
+    o = offs[b];
+    nb = offs[b + 1] - o;
+  }
+  const float* Lb = L + (int64_t)b * k * 3 * C;
+  const float* dc = dcol + 3 * (int64_t)k * o;
+  float acc[C];
+#pragma unroll
+  for (int m = 0; m < C; ++m) acc[m] = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    float G[C];
+#pragma unroll
+    for (int m = 0; m < C; ++m) G[m] = 0.f;
+    for (int l = 0; l < k; ++l) {
+      const float g = __ldg(dc + ((int64_t)l * nb + (i - o)) * 3 + c);
+      const float* Ll = Lb + ((int64_t)l * 3 + c) * C;
+#pragma unroll
+      for (int m = 0; m < C; ++m) G[m] = fmaf(g, __ldg(Ll + m), G[m]);
+    }
+    const float* t = T + (i * tch + (tch > 1 ? c : 0)) * C;
+    float da = 0.f;
+#pragma unroll
+    for (int m = 0; m < C; ++m) da = fmaf(__ldg(t + m), G[m], da);
+    d_albedo[3 * i + c] = da * (1.0f / kPi);
+    const float rho = __ldg(albedo + 3 * i + c) * (1.0f / kPi);
+    if (dT) {
+      if (tch > 1) {
+#pragma unroll
+        for (int m = 0; m < C; ++m) dT[(i * 3 + c) * C + m] = rho * G[m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < C; ++m) acc[m] = fmaf(rho, G[m], acc[m]);
+      }
+    }
+  }
+  if (dT && tch == 1) {
+#pragma unroll
+    for (int m = 0; m < C; ++m) dT[i * C + m] = acc[m];
+  }
+}
+
 template <int C>
 static void launch_relight_batched_c(int64_t n, const float* T, int tch, const float* albedo,
                                      const int64_t* offsets, int n_scenes, const float* L, int k, float* colors,
@@ -362,6 +505,13 @@ int relight_batched(int64_t n, int32_t order, const float* T, int32_t t_channels
     case 1: launch_relight_batched_c<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
     case 2: launch_relight_batched_c<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
     case 3: launch_relight_batched_c<16>(n, T, t_channels, albedo, offsets, n_scenes, L, k, colors, stream); break;
+    case 4:
+    case 5:
+    case 6:
+      k_relight_any_batched<<<(unsigned)((n + kRelightThreads - 1) / kRelightThreads), kRelightThreads, 0,
+                              counted(stream)>>>(n, sh_count(order), t_channels, T, albedo, offsets, n_scenes, L, k,
+                                                 colors);
+      break;
     default: return PRTGS_ERR_UNSUPPORTED;
   }
   PRTGS_CHECK_LAUNCH();
@@ -435,10 +585,11 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_dL_partial(int64_t 
   __shared__ float sW[kDLBatch][3 * 8];  // dc * rho / pi for up to 8 lights per pass
   const int outs_per_light = 3 * C;
   const int64_t i0 = (int64_t)blockIdx.x * kDLChunk;
-  for (int l0 = 0; l0 < k; l0 += 8) {
-    const int nl = min(8, k - l0);
+  constexpr int LPP = 512 / (3 * C) < 8 ? 512 / (3 * C) : 8;  // lights per pass: <= 512 outputs
+  for (int l0 = 0; l0 < k; l0 += LPP) {
+    const int nl = min(LPP, k - l0);
     const int nout = nl * outs_per_light;
-    float acc[2] = {0.f, 0.f};  // outputs tid and tid + 256 (nout <= 8*48 = 384)
+    float acc[2] = {0.f, 0.f};  // outputs tid and tid + 256 (nout <= 512)
     for (int64_t b = i0; b < i0 + kDLChunk && b < n; b += kDLBatch) {
       __syncthreads();
       for (int e = threadIdx.x; e < kDLBatch * TCH * C; e += blockDim.x) {
@@ -498,13 +649,17 @@ static void launch_relight_bwd(int64_t n, const float* T, int tch, const float* 
   size_t smem = sizeof(float) * k * 3 * C;
   unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
   int64_t nb = (n + kDLChunk - 1) / kDLChunk;
-  if (tch == 3) {
+  if constexpr (C > kMaxC)
+    k_relight_bwd_local_hi<C, false><<<grid, kRelightThreads, 0, counted(stream)>>>(n, tch, T, albedo, nullptr, 1, L, k,
+                                                                                   dcol, d_albedo, dT);
+  else if (tch == 3)
     k_relight_bwd_local<C, 3><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
-    k_relight_dL_partial<C, 3><<<(unsigned)nb, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, k, dcol, partial);
-  } else {
+  else
     k_relight_bwd_local<C, 1><<<grid, kRelightThreads, smem, counted(stream)>>>(n, T, albedo, L, k, dcol, d_albedo, dT);
+  if (tch == 3)
+    k_relight_dL_partial<C, 3><<<(unsigned)nb, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, k, dcol, partial);
+  else
     k_relight_dL_partial<C, 1><<<(unsigned)nb, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, k, dcol, partial);
-  }
   int nout = k * 3 * C;
   k_sum_partials<<<(nout + 255) / 256, 256, 0, counted(stream)>>>(partial, nb, nout, dL);
 }
@@ -578,8 +733,9 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_dL_partial_batched(
   const float* dc = dcol + 3 * (int64_t)k * o;
   const int outs_per_light = 3 * C;
   const int64_t slot = o / kDLChunk + b + blockIdx.x;
-  for (int l0 = 0; l0 < k; l0 += 8) {
-    const int nl = min(8, k - l0);
+  constexpr int LPP = 512 / (3 * C) < 8 ? 512 / (3 * C) : 8;  // lights per pass: <= 512 outputs
+  for (int l0 = 0; l0 < k; l0 += LPP) {
+    const int nl = min(LPP, k - l0);
     const int nout = nl * outs_per_light;
     float acc[2] = {0.f, 0.f};
     for (int64_t bb = i0; bb < i1; bb += kDLBatch) {
@@ -646,15 +802,19 @@ static void launch_relight_bwd_batched(int64_t n, const float* T, int tch, const
                                        float* dL, float* partial, cudaStream_t stream) {
   const unsigned grid = (unsigned)((n + kRelightThreads - 1) / kRelightThreads);
   const dim3 pgrid((unsigned)((n + kDLChunk - 1) / kDLChunk), (unsigned)B);
-  if (tch == 3) {
+  if constexpr (C > kMaxC)
+    k_relight_bwd_local_hi<C, true><<<grid, kRelightThreads, 0, counted(stream)>>>(n, tch, T, albedo, offs, B, L, k,
+                                                                                  dcol, d_albedo, dT);
+  else if (tch == 3)
     k_relight_bwd_local_batched<C, 3><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offs, B, L, k, dcol,
-                                                                            d_albedo, dT);
-    k_relight_dL_partial_batched<C, 3><<<pgrid, kRelightThreads, 0, counted(stream)>>>(offs, T, albedo, k, dcol, partial);
-  } else {
+                                                                                    d_albedo, dT);
+  else
     k_relight_bwd_local_batched<C, 1><<<grid, kRelightThreads, 0, counted(stream)>>>(n, T, albedo, offs, B, L, k, dcol,
-                                                                            d_albedo, dT);
+                                                                                    d_albedo, dT);
+  if (tch == 3)
+    k_relight_dL_partial_batched<C, 3><<<pgrid, kRelightThreads, 0, counted(stream)>>>(offs, T, albedo, k, dcol, partial);
+  else
     k_relight_dL_partial_batched<C, 1><<<pgrid, kRelightThreads, 0, counted(stream)>>>(offs, T, albedo, k, dcol, partial);
-  }
   const int nout = k * 3 * C;
   k_sum_partials_batched<<<dim3((unsigned)((nout + 255) / 256), (unsigned)B), 256, 0, counted(stream)>>>(partial, offs, nout,
                                                                                                  dL);
@@ -674,6 +834,9 @@ int relight_backward_batched(int64_t n, int32_t order, const float* T, int32_t t
     case 1: launch_relight_bwd_batched<4>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     case 2: launch_relight_bwd_batched<9>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     case 3: launch_relight_bwd_batched<16>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 4: launch_relight_bwd_batched<25>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 5: launch_relight_bwd_batched<36>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 6: launch_relight_bwd_batched<49>(n, T, t_channels, albedo, offsets, n_scenes, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     default: return PRTGS_ERR_UNSUPPORTED;
   }
   PRTGS_CHECK_LAUNCH();
@@ -694,6 +857,9 @@ int relight_backward(int64_t n, int32_t order, const float* T, int32_t t_channel
     case 1: launch_relight_bwd<4>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     case 2: launch_relight_bwd<9>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     case 3: launch_relight_bwd<16>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 4: launch_relight_bwd<25>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 5: launch_relight_bwd<36>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
+    case 6: launch_relight_bwd<49>(n, T, t_channels, albedo, L, k, dcolors, d_albedo, dT, dL, partial, stream); break;
     default: return PRTGS_ERR_UNSUPPORTED;
   }
   PRTGS_CHECK_LAUNCH();

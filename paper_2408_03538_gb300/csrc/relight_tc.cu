@@ -3,7 +3,10 @@
 //   RGB T [n,3,C]:    D_c[i, l]  = sum_m T[i,c,m] L[l,c,m]     (three MMAs, N = k each)
 //   colors[l,i,c] = (rho_i[c] / pi) D
 // per tile of 128 Gaussians, N padded to a multiple of 16 (<= 256), accumulated in FP32 in
-// tensor memory.
+// tensor memory. K = C is padded to 16 per K block: one block for orders 1-3 (C <= 16), two to
+// four for orders 4-6 (C = 25, 36, 49 -> K = 32, 48, 64). The lights of every K block stay in
+// shared memory; the A operand is staged one K block at a time, each block's MMAs accumulating
+// onto the previous ones after the mbarrier has signalled that they are done reading it.
 //
 // Precision. PRTGS_PREC_BF16 feeds bf16(T) and bf16(L) (one K = 16 slab). PRTGS_PREC_BF16X3
 // splits both operands into three BF16 terms, x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1),
@@ -84,22 +87,27 @@ __device__ __forceinline__ int b_term(int slab) { return slab == 1 || slab == 4 
 
 // B operand (the split light SH of one scene) into shared memory: for scalar T one group
 // whose row o = 3l + c is L[l][c][:]; for RGB T group c whose row l is L[l][c][:].
+// Slab (g, kb, slab) of B sits at ((g * KB + kb) * slabs + slab) * n_pad * 32 bytes.
 template <int C, int TCH>
 __device__ __forceinline__ void load_lights(unsigned char* sB, const float* __restrict__ L, int k, int n_pad,
                                             int slabs) {
+  constexpr int KB = (C + 15) / 16;
   const int rows = TCH == 1 ? 3 * k : k;
-  const int per_group = slabs * n_pad * 16;
+  const int per_slab = n_pad * 16;
+  const int per_group = KB * slabs * per_slab;
   for (int e = threadIdx.x; e < TCH * per_group; e += kTcThreads) {
     const int g = e / per_group, rem0 = e % per_group;
-    const int slab = rem0 / (n_pad * 16), rem = rem0 % (n_pad * 16);
+    const int kbs = rem0 / per_slab, rem = rem0 % per_slab;  // kbs = kb * slabs + slab
+    const int kb = kbs / slabs, slab = kbs % slabs;
     const int row = rem / 16, kk = rem % 16;
+    const int m = 16 * kb + kk;
     float v = 0.f;
-    if (row < rows && kk < C) v = TCH == 1 ? L[(int64_t)row * C + kk] : L[((int64_t)row * 3 + g) * C + kk];
+    if (row < rows && m < C) v = TCH == 1 ? L[(int64_t)row * C + m] : L[((int64_t)row * 3 + g) * C + m];
     __nv_bfloat16 t1, t2, t3;
     split3(v, t1, t2, t3);
     const int term = slabs == 1 ? 0 : b_term(slab);
     const __nv_bfloat16 sel = term == 0 ? t1 : (term == 1 ? t2 : t3);
-    *reinterpret_cast<__nv_bfloat16*>(sB + (g * slabs + slab) * n_pad * 32 + kmajor_offset(row, kk)) = sel;
+    *reinterpret_cast<__nv_bfloat16*>(sB + ((g * KB + kb) * slabs + slab) * n_pad * 32 + kmajor_offset(row, kk)) = sel;
   }
 }
 
@@ -156,7 +164,8 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
                                                            const float* __restrict__ bgv, int32_t* status,
                                                            unsigned wait_polls) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // layout: [A groups x slabs][B groups x slabs]
+  constexpr int KB = (C + 15) / 16;  // K blocks of 16
+  // layout: [A: groups x slabs of one K block][B: groups x K blocks x slabs]
   unsigned char* sA = smem_raw;
   unsigned char* sB = smem_raw + TCH * slabs * kSlabBytesA;
   __shared__ uint64_t mbar;
@@ -189,36 +198,6 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
     const int b_first = offsets ? find_scene(offsets, n_scenes, row0) : 0;
     const int b_last = offsets ? find_scene(offsets, n_scenes, row_end - 1) : 0;
     const int64_t gi = row0 + row;
-    float tv[TCH][kKW];  // this thread's part of the row's K = 16
-    if (PIXEL) {
-#pragma unroll
-      for (int g = 0; g < TCH; ++g)
-#pragma unroll
-        for (int j = 0; j < kKW; ++j) {
-          const int m = kKW * khalf + j;
-          tv[g][j] = (gi < n && m < C) ? __ldg(T + ((int64_t)m * 3 + g) * n + gi) : 0.f;
-        }
-    } else if (C == 16 && t_vec && gi < n) {
-      const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + kKW * khalf);
-#pragma unroll
-      for (int g = 0; g < TCH; ++g)
-#pragma unroll
-        for (int q = 0; q < kKW / 4; ++q) {
-          const float4 v = __ldg(src + 4 * g + q);
-          tv[g][4 * q] = v.x;
-          tv[g][4 * q + 1] = v.y;
-          tv[g][4 * q + 2] = v.z;
-          tv[g][4 * q + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-      for (int g = 0; g < TCH; ++g)
-#pragma unroll
-        for (int j = 0; j < kKW; ++j) {
-          const int m = kKW * khalf + j;
-          tv[g][j] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
-        }
-    }
     float rho[3] = {0.f, 0.f, 0.f}, add[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
       if (PIXEL) {
@@ -250,61 +229,95 @@ __global__ void __launch_bounds__(kTcThreads) k_relight_tc(int64_t n, const floa
       const int64_t ob = offsets ? offsets[b] : 0;
       const int64_t nb = offsets ? offsets[b + 1] - ob : n;
       float* cb = colors + 3 * (int64_t)k * ob;
-      // A operand: this thread's part of the row, split into BF16 terms (zero outside the
-      // scene). In the K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte
-      // runs: one 16-byte (or 8-byte) store per slab.
+      for (int kb = 0; kb < KB; ++kb) {
+        float tv[TCH][kKW];  // this thread's part of the row's K block kb
+        if (PIXEL) {
 #pragma unroll
-      for (int g = 0; g < TCH; ++g) {
-        uint32_t pk[3][kKW / 2];  // term x (pairs of K)
+          for (int g = 0; g < TCH; ++g)
 #pragma unroll
-        for (int j = 0; j < kKW; j += 2) {
-          __nv_bfloat16 a1, a2, a3, b1, b2, b3;
-          split3(mine ? tv[g][j] : 0.f, a1, a2, a3);
-          split3(mine ? tv[g][j + 1] : 0.f, b1, b2, b3);
-          pk[0][j / 2] = pack_bf16x2(a1, b1);
-          pk[1][j / 2] = pack_bf16x2(a2, b2);
-          pk[2][j / 2] = pack_bf16x2(a3, b3);
+            for (int j = 0; j < kKW; ++j) {
+              const int m = 16 * kb + kKW * khalf + j;
+              tv[g][j] = (gi < n && m < C) ? __ldg(T + ((int64_t)m * 3 + g) * n + gi) : 0.f;
+            }
+        } else if (C == 16 && t_vec && gi < n) {
+          const float4* src = reinterpret_cast<const float4*>(T + gi * TCH * C + kKW * khalf);
+#pragma unroll
+          for (int g = 0; g < TCH; ++g)
+#pragma unroll
+            for (int q = 0; q < kKW / 4; ++q) {
+              const float4 v = __ldg(src + 4 * g + q);
+              tv[g][4 * q] = v.x;
+              tv[g][4 * q + 1] = v.y;
+              tv[g][4 * q + 2] = v.z;
+              tv[g][4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+          for (int g = 0; g < TCH; ++g)
+#pragma unroll
+            for (int j = 0; j < kKW; ++j) {
+              const int m = 16 * kb + kKW * khalf + j;
+              tv[g][j] = (gi < n && m < C) ? __ldg(T + (gi * TCH + g) * C + m) : 0.f;
+            }
         }
-        for (int slab = 0; slab < slabs; ++slab) {
-          const int term = slabs == 1 ? 0 : a_term(slab);
-          unsigned char* base = sA + (g * slabs + slab) * kSlabBytesA;
-          const uint32_t* q = term == 0 ? pk[0] : (term == 1 ? pk[1] : pk[2]);
-          if constexpr (kKW == 8)
-            *reinterpret_cast<uint4*>(base + kmajor_offset(row, 8 * khalf)) = make_uint4(q[0], q[1], q[2], q[3]);
-          else
-            *reinterpret_cast<uint2*>(base + kmajor_offset(row, kKW * khalf)) = make_uint2(q[0], q[1]);
-        }
-      }
-      // make the generic-proxy stores visible to the tensor core's async proxy
-      asm volatile("fence.proxy.async.shared::cta;");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int g = 0; g < TCH; ++g)
-          for (int slab = 0; slab < slabs; ++slab) {
-            const uint64_t da = smem_desc(smem_u32(sA + (g * slabs + slab) * kSlabBytesA), 128, 256);
-            const uint64_t db = smem_desc(smem_u32(sB + (g * slabs + slab) * n_pad * 32), 128, 256);
-            const uint32_t acc = slab > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(g * n_pad)),
-                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        // A operand: this thread's part of the row, split into BF16 terms (zero outside the
+        // scene). In the K-major layout a row's K = 0..7 and 8..15 are two contiguous 16-byte
+        // runs: one 16-byte (or 8-byte) store per slab.
+#pragma unroll
+        for (int g = 0; g < TCH; ++g) {
+          uint32_t pk[3][kKW / 2];  // term x (pairs of K)
+#pragma unroll
+          for (int j = 0; j < kKW; j += 2) {
+            __nv_bfloat16 a1, a2, a3, b1, b2, b3;
+            split3(mine ? tv[g][j] : 0.f, a1, a2, a3);
+            split3(mine ? tv[g][j + 1] : 0.f, b1, b2, b3);
+            pk[0][j / 2] = pack_bf16x2(a1, b1);
+            pk[1][j / 2] = pack_bf16x2(a2, b2);
+            pk[2][j / 2] = pack_bf16x2(a3, b3);
           }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mbar)));
+          for (int slab = 0; slab < slabs; ++slab) {
+            const int term = slabs == 1 ? 0 : a_term(slab);
+            unsigned char* base = sA + (g * slabs + slab) * kSlabBytesA;
+            const uint32_t* q = term == 0 ? pk[0] : (term == 1 ? pk[1] : pk[2]);
+            if constexpr (kKW == 8)
+              *reinterpret_cast<uint4*>(base + kmajor_offset(row, 8 * khalf)) = make_uint4(q[0], q[1], q[2], q[3]);
+            else
+              *reinterpret_cast<uint2*>(base + kmajor_offset(row, kKW * khalf)) = make_uint2(q[0], q[1]);
+          }
+        }
+        // make the generic-proxy stores visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int g = 0; g < TCH; ++g)
+            for (int slab = 0; slab < slabs; ++slab) {
+              const uint64_t da = smem_desc(smem_u32(sA + (g * slabs + slab) * kSlabBytesA), 128, 256);
+              const uint64_t db = smem_desc(smem_u32(sB + ((g * KB + kb) * slabs + slab) * n_pad * 32), 128, 256);
+              const uint32_t acc = (kb > 0 || slab > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(g * n_pad)),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar)));
+        }
+        // bounded wait for this K block's MMA chain (after it, the A operand may be restaged). If
+        // any thread gives up, the whole CTA treats the tile as failed: it reports
+        // PRTGS_STATUS_TIMEOUT and waits again with the full limit so that the chain has finished
+        // reading the operands and writing the accumulator before anything reuses them (or the
+        // tensor memory is freed); the tile's outputs become NaN.
+        bool done = bounded_wait(smem_u32(&mbar), phase, wait_polls);
+        if (__syncthreads_or(!done)) {
+          if (tid == 0) set_status(status, PRTGS_STATUS_TIMEOUT);
+          bounded_wait(smem_u32(&mbar), phase, kWaitLimit);
+          failed = true;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (failed) break;  // CTA-uniform
       }
-      // bounded wait for the MMA chain. If any thread gives up, the whole CTA treats the tile as
-      // failed: it reports PRTGS_STATUS_TIMEOUT and waits again with the full limit so that the
-      // chain has finished reading the operands and writing the accumulator before anything
-      // reuses them (or the tensor memory is freed); the tile's outputs become NaN.
-      bool done = bounded_wait(smem_u32(&mbar), phase, wait_polls);
-      if (__syncthreads_or(!done)) {
-        if (tid == 0) set_status(status, PRTGS_STATUS_TIMEOUT);
-        bounded_wait(smem_u32(&mbar), phase, kWaitLimit);
-        failed = true;
-      }
-      phase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;");
       if (failed) {
         write_nan<PIXEL>(mine, k, n, gi, ob, nb, colors);
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -369,6 +382,21 @@ static void launch_tc(int grid, size_t smem, cudaStream_t stream, int64_t n, con
                                                             n_scenes, colors, nullptr, status, wait_polls);
 }
 
+// Dynamic shared memory of one CTA: the A slabs of one K block and the B slabs of every K block.
+static size_t tc_smem(int order, int tch, int slabs, int n_pad) {
+  const int kb = (sh_count(order) + 15) / 16;
+  return (size_t)tch * slabs * kSlabBytesA + (size_t)tch * kb * slabs * n_pad * 32 + 1024;
+}
+
+// Whether a tensor-core relight of this shape fits one MMA's N, the TMEM columns and one CTA's
+// shared memory.
+int relight_tc_fits(int32_t order, int32_t k, int32_t t_channels, int32_t precision) {
+  int n_pad = 0, cols = 0;
+  if (order < 1 || order > 6 || !relight_tc_shape(k, t_channels, &n_pad, &cols)) return 0;
+  const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
+  return tc_smem(order, t_channels, slabs, n_pad) <= (size_t)227 * 1024 ? 1 : 0;
+}
+
 // Tensor-core shape of a relight: N of each MMA and the TMEM columns (a power of two >= 32
 // holding every group and the 24 columns the epilogue reads per eight lights), or 0 when the
 // shape does not fit one MMA (N <= 256) or the 512 TMEM columns.
@@ -394,7 +422,7 @@ int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float
   int n_pad = 0, tmem_cols = 0;
   if (!relight_tc_shape(k, 3, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
   const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
-  const size_t smem = (size_t)3 * slabs * kSlabBytesA + (size_t)3 * slabs * n_pad * 32 + 1024;
+  const size_t smem = tc_smem(order, 3, slabs, n_pad);
   if (smem > 227 * 1024) return PRTGS_ERR_UNSUPPORTED;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -414,7 +442,11 @@ int relight_tc_pixels(int64_t n_pix, int32_t order, const float* TI, const float
   switch (order) {
     case 1: PRTGS_PIX_LAUNCH(4); break;
     case 2: PRTGS_PIX_LAUNCH(9); break;
-    default: PRTGS_PIX_LAUNCH(16); break;
+    case 3: PRTGS_PIX_LAUNCH(16); break;
+    case 4: PRTGS_PIX_LAUNCH(25); break;
+    case 5: PRTGS_PIX_LAUNCH(36); break;
+    case 6: PRTGS_PIX_LAUNCH(49); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
   }
 #undef PRTGS_PIX_LAUNCH
   PRTGS_CHECK_LAUNCH();
@@ -429,7 +461,7 @@ int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, con
   if (!relight_tc_shape(k, t_channels, &n_pad, &tmem_cols)) return PRTGS_ERR_UNSUPPORTED;
   const int slabs = precision == PRTGS_PREC_BF16X3 ? 6 : 1;
   const int tch = t_channels;
-  const size_t smem = (size_t)tch * slabs * kSlabBytesA + (size_t)tch * slabs * n_pad * 32 + 1024;
+  const size_t smem = tc_smem(order, tch, slabs, n_pad);
   if (smem > 227 * 1024) return PRTGS_ERR_UNSUPPORTED;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -446,20 +478,21 @@ int relight_tc(int64_t n, int32_t order, const float* T, int32_t t_channels, con
   const int64_t want = (int64_t)sms * per_sm;
   const int grid = (int)(tiles < want ? tiles : want);
   const bool rgb = tch == 3;
+#define PRTGS_TC_LAUNCH(CC)                                                                                       \
+  if (rgb) launch_tc<CC, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes,     \
+                            colors, status, wait_polls);                                                           \
+  else launch_tc<CC, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, \
+                        status, wait_polls)
   switch (order) {
-    case 1:
-      if (rgb) launch_tc<4, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      else launch_tc<4, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      break;
-    case 2:
-      if (rgb) launch_tc<9, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      else launch_tc<9, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      break;
-    default:
-      if (rgb) launch_tc<16, 3>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      else launch_tc<16, 1>(grid, smem, stream, n, T, albedo, L, k, n_pad, slabs, tmem_cols, offsets, n_scenes, colors, status, wait_polls);
-      break;
+    case 1: PRTGS_TC_LAUNCH(4); break;
+    case 2: PRTGS_TC_LAUNCH(9); break;
+    case 3: PRTGS_TC_LAUNCH(16); break;
+    case 4: PRTGS_TC_LAUNCH(25); break;
+    case 5: PRTGS_TC_LAUNCH(36); break;
+    case 6: PRTGS_TC_LAUNCH(49); break;
+    default: return PRTGS_ERR_UNSUPPORTED;
   }
+#undef PRTGS_TC_LAUNCH
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
 }

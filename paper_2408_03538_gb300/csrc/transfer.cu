@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(T
       dP[k] = k < C ? g.dP[(int64_t)gid * C + k] : 0.f;
       any |= dP[k] != 0.0f;
     }
+    for (int k = kMaxC; k < C; ++k) any |= g.dP[(int64_t)gid * C + k] != 0.0f;  // orders 4-6
     if (!any) continue;  // a receiver with dP_i = 0 contributes nothing (warp-uniform)
     int cnt = 0;
     for (int base = 0; base < a.S; base += 32) {
@@ -547,12 +548,18 @@ __global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(T
       const int s = list[t];
       const float* d = sdir + 3 * s;
       const float c = ray_cos(q3.y, q3.z, q3.w, d);
-      float Y[kMaxC];
-      sh_eval_dyn(a.sh_order, d[0], d[1], d[2], Y);
       float gsum = 0.f;  // w * sum_k dP_k Y_k
+      if (C <= kMaxC) {
+        float Y[kMaxC];
+        sh_eval_dyn(a.sh_order, d[0], d[1], d[2], Y);
 #pragma unroll
-      for (int k = 0; k < kMaxC; ++k)
-        if (k < C) gsum = fmaf(dP[k], Y[k], gsum);  // Y holds only the first C values
+        for (int k = 0; k < kMaxC; ++k)
+          if (k < C) gsum = fmaf(dP[k], Y[k], gsum);  // Y holds only the first C values
+      } else {  // orders 4-6: the direction set's SH table
+        const float* dPi = g.dP + (int64_t)gid * C;
+        const float* Ys = a.Ytab + (int64_t)s * C;
+        for (int k = 0; k < C; ++k) gsum = fmaf(__ldg(dPi + k), __ldg(Ys + k), gsum);
+      }
       gsum *= wq;
       Ray r;
       make_ray(r, q0.x, q0.y, q0.z, d[0], d[1], d[2]);
@@ -610,8 +617,15 @@ int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh
   if (n == 0) return PRTGS_OK;
   Carver c(ws);
   unsigned int* work = c.take<unsigned int>(1);
+  const int C = sh_count(p->sh_order);
+  float* ytab = C > kMaxC ? c.take<float>((size_t)p->n_dirs * C) : nullptr;
   cudaMemsetAsync(work, 0, sizeof(unsigned int), stream);
+  if (ytab) {
+    const int rc = sh_table(p->n_dirs, p->sh_order, p->dirs, ytab, stream);
+    if (rc != PRTGS_OK) return rc;
+  }
   TraceArgs a{};
+  a.Ytab = ytab;
   a.nodes = reinterpret_cast<const float4*>(bvh->nodes);
   a.recs = reinterpret_cast<const float4*>(bvh->records);
   a.order = bvh->order;
@@ -640,7 +654,10 @@ int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh
   return PRTGS_OK;
 }
 
-size_t transfer_backward_workspace(int64_t, const prtgs_transfer_params*) { return align_up(sizeof(unsigned int)); }
+size_t transfer_backward_workspace(int64_t, const prtgs_transfer_params* p) {
+  const int C = sh_count(p->sh_order);
+  return align_up(sizeof(unsigned int)) + (C > kMaxC ? align_up(sizeof(float) * (size_t)p->n_dirs * C) : 0);
+}
 
 // ---- self-transfer bounces (Eq. 33; n bounces Eq. 34-35) ----------------------------------------
 // One bounce k: T^k_i = sum_s w (n_i.w_s)^+ (rho_j / pi) T^{k-1}_j over the index matrix, per
@@ -720,24 +737,30 @@ __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs
 constexpr int kGlossyThreads = 128;
 
 
+// C coefficients (orders 1-6); for C > 16 the SH of the direction set come from the table Ytab.
+template <int C>
 __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, const int32_t* __restrict__ glossy_ids,
                                                            int S, int order, const float* __restrict__ dirs,
+                                                           const float* __restrict__ Ytab,
                                                            const float* __restrict__ normals,
                                                            const float* __restrict__ roughness,
                                                            const float* __restrict__ metallic,
                                                            const float* __restrict__ Vg, float* __restrict__ M) {
   extern __shared__ float smem[];
-  const int C = sh_count(order);
   float* sdir = smem;              // [S*3]
   float* sY = sdir + 3 * S;        // [S][C]
   float* sU = sY + S * C;          // [S][C]   w^2 (n.w_s)^+ V_s Y(w_s)
   float* sB = sU + S * C;          // [S][C]   sum_o k(s,o) Y(w_o)
   for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sdir[i] = dirs[i];
   __syncthreads();
-  for (int s = threadIdx.x; s < S; s += blockDim.x) {
-    float Y[kMaxC];
-    sh_eval_dyn(order, sdir[3 * s], sdir[3 * s + 1], sdir[3 * s + 2], Y);
-    for (int k = 0; k < C; ++k) sY[s * C + k] = Y[k];
+  if (C > kMaxC) {
+    for (int e = threadIdx.x; e < S * C; e += blockDim.x) sY[e] = Ytab[e];
+  } else {
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      float Y[kMaxC];
+      sh_eval_dyn(order, sdir[3 * s], sdir[3 * s + 1], sdir[3 * s + 2], Y);
+      for (int k = 0; k < C && k < kMaxC; ++k) sY[s * C + k] = Y[k];
+    }
   }
   __syncthreads();
   const float wq = 4.0f * kPi / (float)S;
@@ -750,9 +773,9 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, con
       const float* wi = sdir + 3 * s;
       float ni = fmaf(nx, wi[0], fmaf(ny, wi[1], nz * wi[2]));
       float v = Vg[g * S + s];
-      float Bs[kMaxC];
+      float Bs[C];
 #pragma unroll
-      for (int k = 0; k < kMaxC; ++k) Bs[k] = 0.f;
+      for (int k = 0; k < C; ++k) Bs[k] = 0.f;
       float u = 0.f;
       if (ni > 0.0f && v > 0.0f) {
         u = wq * wq * ni * v;
@@ -762,16 +785,13 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, con
           if (!(no > 0.0f)) continue;
           float kv = brdf_kernel(nx, ny, nz, wi, wo, ni, no, alpha, metal);
 #pragma unroll
-          for (int k = 0; k < kMaxC; ++k)
-            if (k < C) Bs[k] = fmaf(kv, sY[o * C + k], Bs[k]);
+          for (int k = 0; k < C; ++k) Bs[k] = fmaf(kv, sY[o * C + k], Bs[k]);
         }
       }
 #pragma unroll
-      for (int k = 0; k < kMaxC; ++k) {
-        if (k < C) {
-          sB[s * C + k] = Bs[k];
-          sU[s * C + k] = u * sY[s * C + k];
-        }
+      for (int k = 0; k < C; ++k) {
+        sB[s * C + k] = Bs[k];
+        sU[s * C + k] = u * sY[s * C + k];
       }
     }
     __syncthreads();
@@ -810,6 +830,26 @@ __global__ void k_mask_u32(int64_t n, const uint8_t* __restrict__ mask, uint32_t
 
 static size_t trace_smem(int S) { return sizeof(float) * 3 * S + kTraceWarps * S * (sizeof(float) + 2); }
 static size_t glossy_smem(int S, int C) { return sizeof(float) * (3 * S + 3 * (size_t)S * C); }
+
+// The glossy matrices' shared memory (directions and three [S][C] tables) must fit one block.
+bool glossy_fits(int S, int order) { return glossy_smem(S, sh_count(order)) <= (size_t)227 * 1024; }
+
+template <int C>
+static int launch_glossy(int64_t n_glossy, const int32_t* gids, int S, const prtgs_transfer_params* p,
+                         const float* ytab, const prtgs_gaussians* g, const float* Vg, float* M, int sms,
+                         cudaStream_t stream) {
+  const size_t gsm = glossy_smem(S, C);
+  if (gsm > (size_t)227 * 1024) return PRTGS_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_glossy<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  int gper = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_glossy<C>, kGlossyThreads, gsm);
+  int64_t blocks = (int64_t)sms * (gper > 0 ? gper : 1);
+  if (blocks > n_glossy) blocks = n_glossy;
+  k_glossy<C><<<(unsigned)blocks, kGlossyThreads, gsm, counted(stream)>>>(n_glossy, gids, S, p->sh_order, p->dirs, ytab,
+                                                                          g->normals, g->roughness, g->metallic, Vg, M);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
 
 // Receivers per batch: the resolve queue holds at most batch * S rays.
 static int64_t trace_batch(int64_t n, int S) {
@@ -1014,15 +1054,17 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
     PRTGS_CHECK_LAUNCH();
   }
   if (glossy) {
-    size_t gsm = glossy_smem(S, C);
-    cudaFuncSetAttribute(k_glossy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-    int gper = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_glossy, kGlossyThreads, gsm);
-    int64_t blocks = (int64_t)sms * (gper > 0 ? gper : 1);
-    if (blocks > n_glossy) blocks = n_glossy;
-    k_glossy<<<(unsigned)blocks, kGlossyThreads, gsm, counted(stream)>>>(n_glossy, gids, S, p->sh_order, p->dirs, g->normals,
-                                                               g->roughness, g->metallic, Vg, M);
-    PRTGS_CHECK_LAUNCH();
+    int rc = PRTGS_ERR_UNSUPPORTED;
+    switch (C) {
+      case 4: rc = launch_glossy<4>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      case 9: rc = launch_glossy<9>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      case 16: rc = launch_glossy<16>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      case 25: rc = launch_glossy<25>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      case 36: rc = launch_glossy<36>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      case 49: rc = launch_glossy<49>(n_glossy, gids, S, p, ytab, g, Vg, M, sms, stream); break;
+      default: break;
+    }
+    if (rc != PRTGS_OK) return rc;
   }
   return PRTGS_OK;
 }

@@ -68,13 +68,14 @@ def test_host_side_validation_without_gpu():
     p = L.TransferParams(7, 64, ctypes.c_void_p(1), 0.0, 1.0, L.SHADOW, 0)
     # null Gaussian arrays
     assert lib.prtgs_build_bvh(ctypes.byref(g), ctypes.byref(bvh), None, None, 0, None) == L.ERR_INVALID_ARG
-    # SH order outside 1..6, and orders above 3 with glossy matrices
+    # SH order outside 1..6
     fake = ctypes.c_void_p(256)
     g2 = L.Gaussians(10, fake, fake, fake, fake, fake, fake, None, None, None)
     bvh.n = 10
     assert lib.prtgs_precompute_transfer(ctypes.byref(g2), ctypes.byref(bvh), ctypes.byref(p), fake, None, None, None,
                                          0, None, None, 0, None) == L.ERR_UNSUPPORTED
-    p5 = L.TransferParams(5, 64, fake, 0.0, 1.0, L.SHADOW | L.GLOSSY, 0)
+    # glossy matrices whose block would need more than 227 KB of shared memory (order 6, S = 1024)
+    p5 = L.TransferParams(6, 1024, fake, 0.0, 1.0, L.SHADOW | L.GLOSSY, 0)
     assert lib.prtgs_precompute_transfer(ctypes.byref(g2), ctypes.byref(bvh), ctypes.byref(p5), fake, fake, fake, None,
                                          0, None, None, 0, None) == L.ERR_UNSUPPORTED
     # too many directions

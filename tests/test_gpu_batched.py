@@ -37,17 +37,17 @@ def test_batched_transfer_equals_per_scene():
     assert np.all(err <= lim)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_relight_batched_equals_per_scene(precision):
-    rng = np.random.default_rng(3)
+@pytest.mark.parametrize("precision,order", [(0, 3), (1, 3), (0, 5), (1, 6)])
+def test_relight_batched_equals_per_scene(precision, order):
+    rng = np.random.default_rng(3 + order)
     sizes = [129, 1000, 1, 257, 0, 64]
     offs = np.zeros(len(sizes) + 1, np.int64)
     offs[1:] = np.cumsum(sizes)
-    n, C, k = int(offs[-1]), 16, 8
+    n, C, k = int(offs[-1]), (order + 1) ** 2, 8
     T = torch.from_numpy(rng.standard_normal((n, C)).astype(np.float32)).cuda()
     alb = torch.from_numpy(rng.uniform(0, 1, (n, 3)).astype(np.float32)).cuda()
     Lsh = torch.from_numpy(rng.standard_normal((len(sizes), k, 3, C)).astype(np.float32)).cuda()
-    flat = api.relight_batched(T, alb, torch.from_numpy(offs).cuda(), Lsh, 3, precision)
+    flat = api.relight_batched(T, alb, torch.from_numpy(offs).cuda(), Lsh, order, precision)
     for b in range(len(sizes)):
         if sizes[b] == 0:
             continue
@@ -108,26 +108,28 @@ def test_render_batched_forward_and_backward_equal_per_scene():
     assert OR.psnr(images[b].cpu().numpy(), ref, peak=1.0) >= 50.0
 
 
-def test_relight_backward_and_loss_batched_equal_per_scene():
-    rng = np.random.default_rng(7)
+@pytest.mark.parametrize("order", [3, 6])
+def test_relight_backward_and_loss_batched_equal_per_scene(order):
+    rng = np.random.default_rng(7 + order)
     sizes = [129, 1000, 1, 2100, 0, 64]
     offs = np.zeros(len(sizes) + 1, np.int64)
     offs[1:] = np.cumsum(sizes)
-    n, C, k = int(offs[-1]), 16, 8
+    n, C, k = int(offs[-1]), (order + 1) ** 2, 8
     for tch in (1, 3):
         T = torch.from_numpy(rng.standard_normal((n, C) if tch == 1 else (n, 3, C)).astype(np.float32)).cuda()
         alb = torch.from_numpy(rng.uniform(0, 1, (n, 3)).astype(np.float32)).cuda()
         Lsh = torch.from_numpy(rng.standard_normal((len(sizes), k, 3, C)).astype(np.float32)).cuda()
         dcol = torch.from_numpy(rng.standard_normal(3 * k * n).astype(np.float32)).cuda()
-        da, dT, dL = api.relight_backward_batched(T, alb, torch.from_numpy(offs).cuda(), Lsh, 3, dcol, need_dT=True)
+        da, dT, dL = api.relight_backward_batched(T, alb, torch.from_numpy(offs).cuda(), Lsh, order, dcol,
+                                                  need_dT=True)
         for b in range(len(sizes)):
             o0, o1 = int(offs[b]), int(offs[b + 1])
             if o1 == o0:
                 assert float(dL[b].abs().max()) == 0.0
                 continue
             db = dcol[3 * k * o0:3 * k * o1].view(k, o1 - o0, 3).contiguous()
-            ra, rT, rL = api.relight_backward(T[o0:o1].contiguous(), alb[o0:o1].contiguous(), Lsh[b].contiguous(), 3,
-                                              db, need_dT=True)
+            ra, rT, rL = api.relight_backward(T[o0:o1].contiguous(), alb[o0:o1].contiguous(), Lsh[b].contiguous(),
+                                              order, db, need_dT=True)
             torch.testing.assert_close(da[o0:o1], ra, rtol=1e-6, atol=1e-6)
             torch.testing.assert_close(dT[o0:o1], rT, rtol=1e-6, atol=1e-6)
             torch.testing.assert_close(dL[b], rL, rtol=1e-5, atol=1e-5)

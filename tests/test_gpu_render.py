@@ -24,7 +24,8 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("order,tch,k", [(2, 1, 1), (3, 1, 5), (3, 3, 1), (3, 3, 64), (1, 1, 3)])
+@pytest.mark.parametrize("order,tch,k", [(2, 1, 1), (3, 1, 5), (3, 3, 1), (3, 3, 64), (1, 1, 3), (5, 3, 7),
+                                         (6, 1, 4)])
 def test_relight_fp32(order, tch, k):
     rng = np.random.default_rng(order * 10 + tch + k)
     n, C = 5003, (order + 1) ** 2
@@ -37,9 +38,11 @@ def test_relight_fp32(order, tch, k):
     assert err.max() < 1e-4
 
 
-def test_relight_glossy_fp32():
-    rng = np.random.default_rng(3)
-    n, C, k = 2000, 16, 4
+@pytest.mark.parametrize("order", [3, 5, 6])
+def test_relight_glossy_fp32(order):
+    """Glossy rows t_eff = M Y(v) (Eq. 41); orders 4-6 evaluate Y(v) by the Legendre recurrence."""
+    rng = np.random.default_rng(3 + order)
+    n, C, k = 2000, (order + 1) ** 2, 4
     T = rng.standard_normal((n, 3, C)).astype(np.float32)
     alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
     L = rng.standard_normal((k, 3, C)).astype(np.float32)
@@ -47,18 +50,19 @@ def test_relight_glossy_fp32():
     M = rng.standard_normal((600, C, C)).astype(np.float32)
     means = rng.standard_normal((n, 3)).astype(np.float32)
     cam = np.array([2.0, -5.0, 1.5], np.float32)
-    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), 3, glossy_ids=_cuda(gids, torch.int32), M=_cuda(M),
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), order, glossy_ids=_cuda(gids, torch.int32), M=_cuda(M),
                       means=_cuda(means), cam_pos=_cuda(cam)).cpu().numpy()
-    ref = oracle.relight(T, alb, L, glossy_ids=gids, M=M, means=means, cam_pos=cam, order=3)
+    ref = oracle.relight(T, alb, L, glossy_ids=gids, M=M, means=means, cam_pos=cam, order=order)
     err = oracle.norm_err(col.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-6)
     assert err.max() < 1e-4
 
 
-@pytest.mark.parametrize("tch,k", [(1, 1), (3, 2), (1, 9)])
-def test_relight_backward(tch, k):
-    rng = np.random.default_rng(11 + k)
-    n, order = 3001, 3
-    C = 16
+@pytest.mark.parametrize("tch,k,order", [(1, 1, 3), (3, 2, 3), (1, 9, 3), (3, 5, 4), (1, 3, 5), (3, 9, 6),
+                                         (1, 4, 6)])
+def test_relight_backward(tch, k, order):
+    rng = np.random.default_rng(11 + k + order)
+    n = 3001
+    C = (order + 1) ** 2
     T = rng.standard_normal((n, C) if tch == 1 else (n, 3, C)).astype(np.float32)
     alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
     L = rng.standard_normal((k, 3, C)).astype(np.float32)
@@ -189,7 +193,9 @@ def test_relit_render_autograd_end_to_end():
 
 @pytest.mark.parametrize("order,k,n,tch", [(3, 1, 5003, 1), (3, 64, 20000, 1), (2, 4, 129, 1), (1, 2, 128, 1),
                                            (3, 85, 777, 1), (3, 64, 20000, 3), (2, 5, 777, 3), (1, 1, 129, 3),
-                                           (3, 160, 3001, 3), (3, 10, 4099, 1)])
+                                           (3, 160, 3001, 3), (3, 10, 4099, 1),
+                                           (4, 8, 3001, 3), (4, 85, 1025, 1), (5, 64, 2049, 1), (5, 80, 999, 3),
+                                           (6, 64, 5003, 3), (6, 85, 777, 1), (6, 1, 129, 1), (6, 13, 20000, 3)])
 def test_relight_tensor_core_bf16x3(order, k, n, tch):
     """tcgen05 relight with the 3-term BF16 split meets the FP32 bar (1e-4 norm-wise), for
     scalar and RGB transfer, ragged row tails and light counts that are not multiples of 8."""
@@ -217,10 +223,11 @@ def test_relight_tensor_core_plain_bf16_error_is_bf16_sized():
     assert 1e-5 < np.median(err) < 2e-2  # plain BF16 operands: about 2^-8 relative
 
 
-def test_relight_tensor_core_with_glossy_rows():
+@pytest.mark.parametrize("order,k", [(3, 64), (6, 32)])
+def test_relight_tensor_core_with_glossy_rows(order, k):
     """BF16x3 tensor cores for every row, then the glossy rows rewritten in FP32 (Eq. 41)."""
-    rng = np.random.default_rng(17)
-    n, C, k = 6000, 16, 64
+    rng = np.random.default_rng(17 + order)
+    n, C = 6000, (order + 1) ** 2
     T = rng.standard_normal((n, 3, C)).astype(np.float32)
     alb = rng.uniform(0, 1, (n, 3)).astype(np.float32)
     L = rng.standard_normal((k, 3, C)).astype(np.float32)
@@ -228,9 +235,9 @@ def test_relight_tensor_core_with_glossy_rows():
     M = rng.standard_normal((gids.size, C, C)).astype(np.float32) * 0.2
     means = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
     cam = np.array([0.5, -3.0, 1.0], np.float32)
-    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), 3, precision=1, glossy_ids=_cuda(gids, torch.int32),
+    col = api.relight(_cuda(T), _cuda(alb), _cuda(L), order, precision=1, glossy_ids=_cuda(gids, torch.int32),
                       M=_cuda(M), means=_cuda(means), cam_pos=_cuda(cam)).cpu().numpy()
-    ref = oracle.relight(T, alb, L, glossy_ids=gids, M=M, means=means, cam_pos=cam, order=3)
+    ref = oracle.relight(T, alb, L, glossy_ids=gids, M=M, means=means, cam_pos=cam, order=order)
     err = oracle.norm_err(col.transpose(1, 0, 2), ref.transpose(1, 0, 2), 1e-3)
     assert err.max() < 1e-4, err.max()
 
@@ -242,6 +249,9 @@ def test_relight_tensor_core_rejects_unsupported():
     with pytest.raises(Exception):  # more lights than one launch holds
         api.relight(torch.zeros((10, 3, 16), device="cuda"), torch.zeros((10, 3), device="cuda"),
                     torch.zeros((300, 3, 16), device="cuda"), 3, precision=1)
+    with pytest.raises(Exception):  # order 6, RGB transfer: the lights of four K blocks exceed shared memory
+        api.relight(torch.zeros((10, 3, 49), device="cuda"), torch.zeros((10, 3), device="cuda"),
+                    torch.zeros((65, 3, 49), device="cuda"), 6, precision=1)
 
 
 def test_relit_render_through_transfer_end_to_end():
@@ -368,11 +378,13 @@ def test_relight_1m_64_lights_tensor_cores_full_size():
 
 # ---- pixel-space relight of many lights ----------------------------------------------------
 @pytest.mark.parametrize("precision,bar,order,tch", [(0, 50.0, 3, 3), (1, 50.0, 3, 3), (2, 30.0, 3, 3),
-                                                     (1, 50.0, 2, 1), (0, 50.0, 1, 3), (1, 50.0, 1, 1)])
+                                                     (1, 50.0, 2, 1), (0, 50.0, 1, 3), (1, 50.0, 1, 1),
+                                                     (0, 50.0, 6, 3), (1, 50.0, 6, 3), (1, 50.0, 5, 1),
+                                                     (0, 50.0, 4, 1)])
 def test_render_relit_matches_oracle(precision, bar, order, tch):
     """Composite the splats' (rho/pi) T once, contract per pixel with 12 lights: equals the FP64
     oracle's relight + composite of each light (30 % glossy splats, background; RGB or scalar
-    transfer, SH orders 1-3)."""
+    transfer, SH orders 1-6)."""
     sc = S.surface_scene(1500, 44)
     sc.means *= 0.5
     rng = np.random.default_rng(44)

@@ -284,7 +284,8 @@ def _check_grads(gpu, ref, tol=2e-3):
         np.testing.assert_allclose(a, b, rtol=0, atol=tol * max(np.abs(b).max(), 1e-3 * top_el), err_msg=f)
 
 
-@pytest.mark.parametrize("n,order,nd,t_min", [(300, 3, 64, 0.0), (600, 2, 48, api.DEFAULT_T_MIN), (257, 1, 33, 0.0)])
+@pytest.mark.parametrize("n,order,nd,t_min", [(300, 3, 64, 0.0), (600, 2, 48, api.DEFAULT_T_MIN), (257, 1, 33, 0.0),
+                                               (280, 5, 48, 0.0), (200, 6, 40, api.DEFAULT_T_MIN)])
 def test_transfer_backward_matches_autograd(n, order, nd, t_min):
     """dL/d(Gaussians) for L = sum(wP * P) against FP64 autograd through the brute-force P."""
     sc = _crowded(n, 11 + n)
@@ -448,16 +449,33 @@ def test_high_order_transfer_and_relight_match_oracle(order):
 
 def test_high_order_rejects_what_it_does_not_cover():
     sc = S.isotropic_scene(50, 3)
+    sc.glossy_mask[:10] = 1
     g = _gt(sc)
     bvh = api.build_bvh(g)
     d = torch.from_numpy(S.direction_set(32, 1)).cuda()
-    with pytest.raises(Exception):
-        api.precompute_transfer(g, bvh, d, 6, glossy=True)
-    with pytest.raises(Exception):
-        api.relight(torch.zeros((50, 49), device="cuda"), g.albedo, torch.zeros((1, 3, 49), device="cuda"), 6,
-                    precision=1)
+    with pytest.raises(Exception):  # order 6 glossy matrices of 1024 directions: 614 KB of shared memory
+        api.precompute_transfer(g, bvh, torch.from_numpy(S.direction_set(1024, 1)).cuda(), 6, glossy=True)
     with pytest.raises(Exception):
         api.precompute_transfer(g, bvh, d, 7)
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_high_order_glossy_matrices(order):
+    """The C x C glossy matrices (Eq. 40) at orders 4 and 6 (25 x 25, 49 x 49) against the oracle."""
+    sc = S.surface_scene(900, 70 + order)
+    rng = np.random.default_rng(order)
+    sc.glossy_mask = (rng.random(sc.n) < 0.2).astype(np.uint8)
+    sc.roughness = rng.uniform(0.2, 0.8, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    dirs = S.direction_set(64, 8)
+    out = _transfer_gpu(sc, dirs, order, glossy=True)
+    gids = np.nonzero(sc.glossy_mask)[0]
+    assert out["n_glossy"] == gids.size and out["M"].shape[1:] == ((order + 1) ** 2, (order + 1) ** 2)
+    tr = oracle.transfer(sc, dirs, order, gids)
+    Vallow = tr["dV"] + np.where((tr["flags"] & oracle.RF_TRACED) != 0, api.DEFAULT_T_MIN, 0.0)
+    M, allow = oracle.glossy(sc, dirs, order, gids, tr["V"], Vallow)
+    floor = 1e-3 * np.median(np.linalg.norm(M.reshape(len(M), -1), axis=1))
+    _check_norm(out["M"], M, allow, floor)
 
 
 @pytest.mark.parametrize("nb", [1, 3])
