@@ -669,17 +669,20 @@ def run_sh_orders():
         e1.synchronize()
         t_ms = e0.elapsed_time(e1)
         Lsh = torch.from_numpy(S.env_lights(1, order, 5)).cuda()
-        frames = []
-        for _ in range(23):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            colors = api.relight(tr["P"], g.albedo, Lsh, order)
-            api.render(g, colors, cam, bg, state=state)
-            b.record()
-            b.synchronize()
-            frames.append(a.elapsed_time(b))
-        res[str(order)] = {"coefficients": C, "relight_render_ms": float(np.median(frames[3:])),
+        med = {}
+        for prec in (0, 1):  # FP32 CUDA cores, BF16x3 tensor cores (K = C padded to 16 per K block)
+            frames = []
+            for _ in range(23):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                colors = api.relight(tr["P"], g.albedo, Lsh, order, precision=prec)
+                api.render(g, colors, cam, bg, state=state)
+                b.record()
+                b.synchronize()
+                frames.append(a.elapsed_time(b))
+            med[prec] = float(np.median(frames[3:]))
+        res[str(order)] = {"coefficients": C, "relight_render_ms": med[0], "relight_render_ms_bf16x3": med[1],
                            "transfer_ms": t_ms}
     print(json.dumps({"case": "sh-orders", "workload": SURFACE, "image": f"{cam.width}x{cam.height}",
                       "by_order": res}))
@@ -710,29 +713,38 @@ def run_batched(args):
     for _ in range(args.warmup):
         pipe.step()
     pipe.capture()
+    pipe.capture(transfer=False)
     for _ in range(args.warmup):
         pipe.replay()
+        pipe.replay(transfer=False)
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    graph_ms = eager_ms = 0.0
-    for mode in ("graph", "eager"):
-        for _ in range(args.steps):
+    ms = {}
+    # the full step (transfer included) and the frame part (relight, render, loss, backward on
+    # the frozen transfer), each as one graph replay and as eager calls
+    for mode in ("graph", "eager", "frame_graph", "frame_eager"):
+        reps = args.steps if mode in ("graph", "eager") else 10 * args.steps
+        tot = 0.0
+        for _ in range(reps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if mode == "graph":
                 pipe.replay()
-            else:
+            elif mode == "eager":
                 pipe.step()
+            elif mode == "frame_graph":
+                pipe.replay(transfer=False)
+            else:
+                pipe.step(transfer=False)
             e1.record(stream)
             e1.synchronize()
-            if mode == "graph":
-                graph_ms += e0.elapsed_time(e1)
-            else:
-                eager_ms += e0.elapsed_time(e1)
+            tot += e0.elapsed_time(e1)
+        ms[mode] = tot / reps
+    graph_ms, eager_ms = ms["graph"] * args.steps, ms["eager"] * args.steps
     clocks = sampler.stop()
     # the same step as one call per scene and stage (no batching)
     gts = [pipe.scene(b) for b in range(pipe.B)]
@@ -745,11 +757,15 @@ def run_batched(args):
         del st0
     tgt = pipe.targets
 
-    def per_scene_step():
+    Ps = [None] * len(gts)
+
+    def per_scene_step(transfer=True):
         for b, gb in enumerate(gts):
-            bvh = api.build_bvh(gb)
-            P = api.precompute_transfer(gb, bvh, pipe.dirs, w["order"], packet_dirs=pipe.packet_dirs,
-                                        walk=pipe.walk)["P"]
+            if transfer or Ps[b] is None:
+                bvh = api.build_bvh(gb)
+                Ps[b] = api.precompute_transfer(gb, bvh, pipe.dirs, w["order"], packet_dirs=pipe.packet_dirs,
+                                                walk=pipe.walk)["P"]
+            P = Ps[b]
             col = api.relight(P, gb.albedo, pipe.L[b], w["order"], precision=pipe.precision)
             img, _ = api.render(gb, col, cams[b], pipe.bg, state=states[b])
             loss, dimg = api.l2_loss(img, tgt[b])
@@ -765,7 +781,16 @@ def run_batched(args):
     e1.record(stream)
     e1.synchronize()
     per_scene_ms = e0.elapsed_time(e1)
+    frame_per_scene = []
+    for _ in range(5):
+        flush.zero_()
+        e0.record(stream)
+        per_scene_step(transfer=False)
+        e1.record(stream)
+        e1.synchronize()
+        frame_per_scene.append(e0.elapsed_time(e1))
     launches = count_launches(pipe.step)
+    frame_launches = count_launches(lambda: pipe.step(transfer=False))
     n_total = sum(p.n for p in parts)
     rays = n_total * int(dirs.shape[0])
     frames = len(parts) * w["lights"]
@@ -781,6 +806,10 @@ def run_batched(args):
             "frames_per_s": frames * args.steps / (graph_ms / 1e3),
             "eager_ms_per_step": eager_ms / args.steps, "graph_ms_per_step": graph_ms / args.steps,
             "per_scene_calls_ms_per_step": per_scene_ms,
+            "frame": {"what": "relight + render + L2 loss + render backward + relight backward of all 32 scenes on "
+                              "the frozen transfer", "graph_ms": ms["frame_graph"], "eager_ms": ms["frame_eager"],
+                      "per_scene_calls_ms": float(np.median(frame_per_scene)),
+                      "frames_per_s_graph": frames / (ms["frame_graph"] / 1e3), "gpu_launches": frame_launches},
             "gpu_launches_per_step": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)

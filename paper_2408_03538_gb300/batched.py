@@ -57,6 +57,7 @@ class BatchedPipeline:
             targets = torch.zeros_like(self.images)
         self.targets = torch.as_tensor(targets).to(device).reshape(self.images.shape).contiguous()
         self.graph = None
+        self.frame_graph = None
         self.out = {}
 
     def scene(self, b) -> api.GaussianTensors:
@@ -91,10 +92,17 @@ class BatchedPipeline:
         del probe
         self.state = api.RenderState(self.n, W, H, int(pairs * 1.25) + 4096, device, n_scenes=self.B)
 
-    def step(self):
-        """One pass of the whole path (forward and backward) over every scene: one call per stage."""
-        bvh = api.build_bvh(self.g, self.offs_d)
-        Tt = self._transfer_out(bvh)
+    def step(self, transfer: bool = True):
+        """One pass of the whole path (forward and backward) over every scene: one call per stage.
+        ``transfer=False`` runs the frame part only (relight, render, loss and both backward
+        passes) on the transfer of the last full step: the geometry is frozen after the ray
+        tracing (Sec. 4.4), so a training or serving loop repeats this part."""
+        if transfer:
+            bvh = api.build_bvh(self.g, self.offs_d)
+            Tt = self._transfer_out(bvh)
+        else:
+            bvh = self.out.get("bvh")
+            Tt = self.T if self.bounce else self.P
         api.relight_batched(Tt, self.g.albedo, self.offs_d, self.L, self.order, self.precision, out=self.colors)
         api.render_batched(self.g, self.offs_d, self.colors, self.k, self.cams, self.bg, self.state, out=self.images)
         losses, dimg = api.l2_loss_batched(self.images, self.targets)
@@ -104,20 +112,28 @@ class BatchedPipeline:
         self.out = {"losses": losses, "dL": dL, "grads": (dm, ds, dq, do, da), "bvh": bvh}
         return self.out
 
-    def capture(self):
-        """Capture step() into a CUDA graph (after one eager warm-up on the capture stream)."""
+    def capture(self, transfer: bool = True):
+        """Capture step(transfer) into a CUDA graph (after one eager warm-up on the capture stream);
+        the full step and the frame part are kept as separate graphs."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            self.step()
+            self.step(transfer)
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self.captured = self.step()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            captured = self.step(transfer)
         torch.cuda.synchronize()
-        return self.graph
+        if transfer:
+            self.graph, self.captured = graph, captured
+        else:
+            self.frame_graph, self.frame_captured = graph, captured
+        return graph
 
-    def replay(self):
-        self.graph.replay()
-        return self.captured
+    def replay(self, transfer: bool = True):
+        if transfer:
+            self.graph.replay()
+            return self.captured
+        self.frame_graph.replay()
+        return self.frame_captured
