@@ -288,6 +288,9 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, in
 // is no index-matrix candidate). It keeps the nearest front-facing hit (by key). After the cut-off
 // the walk goes on pruned to the nearer of the horizon and that hit, so that it ends as the
 // nearest front-facing hit of the whole ray within the horizon: the first index-matrix candidate.
+// It also sums log(1 - alpha) over the hits in front of the current candidate (lpre). That sum
+// stays exact while no hit it holds lies behind a nearer candidate found later (checked with the
+// largest key summed); when it holds, the index search needs no walk in front of the candidate.
 struct BounceVis {
   const TraceArgs& a;
   const Ray& r;
@@ -299,6 +302,10 @@ struct BounceVis {
   float tf;  // nearest front-facing hit: t*, position
   int pf;
   float amax;  // largest alpha m of the front-facing hits multiplied into T
+  float lpre;  // sum of log(1 - alpha) of the hits with key below (tf, pf)
+  float ts;    // largest key summed into lpre: t*, position
+  int ps;
+  bool pre_ok;  // lpre is the prefix of (tf, pf)
   __device__ float t_hi() const { return T < a.t_min ? fminf(slack_hi(t_hor), slack_hi(tf)) : FLT_MAX; }
   __device__ bool stop() const { return false; }
   __device__ void hit(int pos, float t, float al, float m) {
@@ -311,8 +318,15 @@ struct BounceVis {
       return;
     }
     if (m > 0.f && key_less(t, pos, tf, pf)) {
+      if (ps != INT32_MIN && !key_less(ts, ps, t, pos)) pre_ok = false;  // a summed hit lies behind it
       tf = t;
       pf = pos;
+    } else if (key_less(t, pos, tf, pf)) {
+      lpre += log1pf(-al);
+      if (ps == INT32_MIN || key_less(ts, ps, t, pos)) {
+        ts = t;
+        ps = pos;
+      }
     }
   }
   __device__ void leaf(int pos) {
@@ -482,7 +496,7 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
             packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
             if (mine) vis = sv.T;
           } else {
-            BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f};
+            BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f, 0.0f, 0.0f, INT32_MIN, true};
             packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
             if (mine) vis = bv.T;
             // index matrix (Sec. 4.4): argmax of W_j = alpha_j T_j m_j over the hits in key order,
@@ -495,6 +509,12 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
             bool searching = mine && bv.tf != FLT_MAX;
             float t_last = -FLT_MAX, lt = 0.0f, lw_best = -FLT_MAX;
             int p_last = INT32_MIN;
+            // with an exact prefix of the first candidate, the first round starts at the candidate
+            const bool pre = bv.pre_ok && bv.pf > INT32_MIN;
+            if (pre) {
+              t_last = bv.tf;
+              p_last = bv.pf - 1;
+            }
             for (int64_t round = 0; __any_sync(0xffffffffu, searching); ++round) {
               if (round > a.n / kPacketRoundHits + 1) {
                 if (searching) set_status(a.status, PRTGS_STATUS_BAD_INDEX);
@@ -506,7 +526,7 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
               packet_walk(a, f, r, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
                           rs.search_nodes);
               if (searching) {
-                if (round == 0) lt = sv.lbase;
+                if (round == 0) lt = pre ? bv.lpre : sv.lbase;
                 const int nh = sv.count;
                 bool decided = false;
                 for (int k = 0; k < nh && !decided; ++k) {
