@@ -1,4 +1,4 @@
-"""FP64 PyTorch restatement of the shadowed transfer P -- TEST INFRASTRUCTURE ONLY.
+"""FP64 PyTorch restatement of the shadowed transfer P and of the bounces -- TEST INFRASTRUCTURE ONLY.
 
 Differentiable counterpart of oracle_trace's P (Eq. 29 projected by Eq. 9, visibility from
 Eq. 27 read as the Gaussian's maximum along the ray, Eq. 4 along a ray), for the gradients of
@@ -77,3 +77,26 @@ def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
         V = torch.prod(one_m, dim=0)  # [S]
         rows.append(torch.where(up, w * V * c, torch.zeros_like(c)))
     return torch.stack(rows) @ Y
+
+
+def bounce_T(P, idx, dirs, normals, albedo, n_bounces: int = 1):
+    """T [N,3,C] = P + T^1 + ... + T^n (Eq. 33-35) over a fixed index matrix idx [N,S] (-1 = no
+    hit), FP64 and differentiable in P, normals and albedo: T^0_i = P_i for the three channels,
+    T^k_i[c] = sum_s w max(0, n_i.w_s) (rho_j[c]/pi) T^{k-1}_j[c], j = idx[i,s], w = 4 pi/S.
+    The index matrix is a discrete decision and carries no gradient; the clamp of the cosine
+    has the derivative of max (zero below the horizon)."""
+    idx = torch.as_tensor(np.asarray(idx), dtype=torch.int64)
+    N, S = idx.shape
+    d = torch.as_tensor(np.asarray(dirs, dtype=np.float64))
+    w = 4.0 * math.pi / S
+    valid = idx >= 0
+    jj = torch.where(valid, idx, torch.zeros_like(idx))
+    coef = w * torch.clamp(normals @ d.T, min=0.0) * valid  # [N,S]
+    rho = albedo / math.pi  # [N,3]
+    prev = P[:, None, :].expand(N, 3, P.shape[1])
+    total = prev
+    for _ in range(n_bounces):
+        G = rho[jj][:, :, :, None] * prev[jj]  # [N,S,3,C]
+        prev = (coef[:, :, None, None] * G).sum(dim=1)
+        total = total + prev
+    return total

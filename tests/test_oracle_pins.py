@@ -650,3 +650,39 @@ def test_multi_bounce_allowance_covers_switching_a_flagged_ray(oracle_mod):
                 T2, _ = oracle_mod.multi_bounce(sc, dirs, 1, dict(tr, idx=idx2, flags=np.zeros_like(flags)), nb)
                 # a single switch moves receiver i directly and, through later bounces, others
                 assert np.all(np.linalg.norm(T2 - T, axis=2)[i] <= allow[i] + 1e-12), (nb, i, alt)
+
+
+@pytest.mark.parametrize("nb", [1, 3])
+def test_torch_bounce_equals_the_recursion_and_central_differences(oracle_mod, nb):
+    """The differentiable bounce restatement equals the numpy recursion (itself pinned to Eq. 33
+    and the closed forms above) on a traced index matrix, and its autograd gradients with respect
+    to P, albedo and normals equal central differences."""
+    import torch
+
+    from oracle import transfer_torch as TT
+
+    sc = _crowd(90, 12)
+    dirs = S.direction_set(40, 5)
+    tr = oracle_mod.transfer(sc, dirs, 2, np.arange(sc.n), bounce=True)
+    Tref, _ = oracle_mod.multi_bounce(sc, dirs, 2, tr, nb)
+    t = lambda a, rg=False: torch.tensor(np.asarray(a, np.float64), requires_grad=rg)
+    P, rho, nrm = t(tr["P"], True), t(sc.albedo, True), t(sc.normals, True)
+    T = TT.bounce_T(P, tr["idx"], dirs, nrm, rho, nb)
+    np.testing.assert_allclose(T.detach().numpy(), Tref, rtol=0, atol=1e-12)
+    assert (tr["idx"] >= 0).sum() > 100
+    rng = np.random.default_rng(nb)
+    W = torch.as_tensor(rng.standard_normal(tuple(T.shape)))
+    f = lambda p, r, n: (TT.bounce_T(p, tr["idx"], dirs, n, r, nb) * W).sum()
+    grads = torch.autograd.grad(f(P, rho, nrm), (P, rho, nrm))
+    h = 1e-7
+    for gi, base in enumerate((P, rho, nrm)):
+        for k in rng.choice(base.numel(), size=8, replace=False):
+            args_p = [q.detach().clone() for q in (P, rho, nrm)]
+            args_m = [q.detach().clone() for q in (P, rho, nrm)]
+            args_p[gi].reshape(-1)[k] += h
+            args_m[gi].reshape(-1)[k] -= h
+            with torch.no_grad():
+                fd = (f(*args_p) - f(*args_m)).item() / (2 * h)
+            g = grads[gi].reshape(-1)[k].item()
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(fd)), (gi, k, fd, g)
+    assert all(float(g.abs().sum()) > 0 for g in grads)
