@@ -240,6 +240,28 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                        size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Backward of the self-transfer bounces (Eq. 33-35) with the index matrix held fixed (its argmax
+ * is a discrete decision). Forward, per channel c: T = T^0 + ... + T^n, T^0_i = P_i,
+ * T^k_i[c] = sum_s (4 pi/S) max(0, n_i.w_s) (albedo_j[c]/pi) T^{k-1}_j[c], j = idx[i,s]; the call
+ * takes G = dLoss/dT back through it:
+ *   dP[n,C]         out: dLoss/dP (feed it to prtgs_precompute_transfer_backward for the geometry)
+ *   d_albedo[n,3]   out: through the hit splats' albedo in every bounce
+ *   d_normals[n,3]  out: through the receivers' cosines max(0, n_i.w_s) (raw normals; add the
+ *                   transfer backward's own d_normals for the total)
+ * Inputs (device): dirs[S,3], normals[n,3], albedo[n,3], P[n,C] and idx[n,S] of the forward call,
+ * dT[n,3,C]; n_bounces as the forward's (0 or 1 = one bounce, at most 64). The intermediate bounces
+ * are recomputed. Outputs are overwritten; the scatters use float atomics, so the last bits vary
+ * from run to run. sh_order 1..6. Workspace: prtgs_bounce_backward_workspace_size
+ * ((max(n_bounces, 1) + 2) n 3 C floats, one fewer for one bounce). idx entries >= n set
+ * PRTGS_STATUS_BAD_INDEX and are skipped.
+ */
+size_t prtgs_bounce_backward_workspace_size(int64_t n, int32_t sh_order, int32_t n_bounces);
+int prtgs_bounce_backward(int64_t n, int32_t sh_order, int32_t n_dirs, const float* dirs, const float* normals,
+                          const float* albedo, const float* P, const int32_t* idx, int32_t n_bounces, const float* dT,
+                          float* dP, float* d_albedo, float* d_normals, int32_t* status, void* workspace,
+                          size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
  * Visibility cache for training (Sec. 4.4-4.5): the same walk as prtgs_precompute_transfer with
  * flags = PRTGS_SHADOW, keeping every ray's visibility.
  *  V[n,S]   out (device): V_is, the transmittance of the ray from mu_i along w_s as in P below;

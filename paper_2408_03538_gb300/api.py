@@ -618,3 +618,53 @@ class ShadowedTransfer(torch.autograd.Function):
 
 def shadowed_transfer(means, scales, quats, opacity, normals, albedo, dirs, order, t_min=DEFAULT_T_MIN):
     return ShadowedTransfer.apply(means, scales, quats, opacity, normals, albedo, dirs, order, t_min)
+
+
+def bounce_backward(g: GaussianTensors, dirs: torch.Tensor, order: int, P: torch.Tensor, idx: torch.Tensor,
+                    dT: torch.Tensor, n_bounces: int = 1, status: Status | None = None):
+    """Backward of the self-transfer bounces (Eq. 33-35) with the index matrix fixed: from
+    dT = dLoss/dT [n,3,C] to dP [n,C], d_albedo [n,3] and d_normals [n,3] (the receivers' cosines)."""
+    lib = L.load()
+    dev = g.means.device
+    n = g.n
+    C = sh_count(order)
+    dP = torch.empty((n, C), dtype=torch.float32, device=dev)
+    da = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    dn = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    dT = dT.contiguous()
+    ws, nb = _ws(lib.prtgs_bounce_backward_workspace_size(n, order, n_bounces), dev)
+    L.check(lib.prtgs_bounce_backward(n, order, int(dirs.shape[0]), _ptr(dirs), _ptr(g.normals), _ptr(g.albedo),
+                                      _ptr(P), _ptr(idx), int(n_bounces), _ptr(dT), _ptr(dP), _ptr(da), _ptr(dn),
+                                      status.ptr() if status else None, _ptr(ws), nb, _stream()),
+            "prtgs_bounce_backward")
+    return dP, da, dn
+
+
+class BounceTransfer(torch.autograd.Function):
+    """T = shadowed transfer with n self-transfer bounces over the index matrix (Eq. 29, Eq. 33-35)
+    with the hand-written backward: the bounces' adjoint (index matrix fixed) gives dP, the albedo
+    and the receivers' cosine gradients, then the transfer backward takes dP to the geometry.
+    Differentiable in means, scales, quats, opacity, normals and albedo."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, normals, albedo, dirs, order, n_bounces, t_min):
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                            normals.contiguous(), albedo.contiguous())
+        st = Status()
+        bvh = build_bvh(g, status=st)
+        out = precompute_transfer(g, bvh, dirs, order, bounce=True, n_bounces=n_bounces, t_min=t_min, status=st)
+        ctx.g, ctx.bvh, ctx.st, ctx.dirs, ctx.order, ctx.t_min, ctx.nb = g, bvh, st, dirs, order, t_min, n_bounces
+        ctx.P, ctx.idx = out["P"], out["idx"]
+        return out["T"]
+
+    @staticmethod
+    def backward(ctx, dT):
+        dP, da, dn = bounce_backward(ctx.g, ctx.dirs, ctx.order, ctx.P, ctx.idx, dT, ctx.nb, status=ctx.st)
+        gr = precompute_transfer_backward(ctx.g, ctx.bvh, ctx.dirs, ctx.order, dP, t_min=ctx.t_min, status=ctx.st)
+        return (gr["d_means"], gr["d_scales"], gr["d_quats"], gr["d_opacity"], gr["d_normals"] + dn, da, None, None,
+                None, None)
+
+
+def bounce_transfer(means, scales, quats, opacity, normals, albedo, dirs, order, n_bounces=1, t_min=DEFAULT_T_MIN):
+    return BounceTransfer.apply(means, scales, quats, opacity, normals, albedo, dirs, order, n_bounces, t_min)
+

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libprtgs.so")
 SOURCES = ["api.cu", "sort.cu", "bvh.cu", "transfer.cu", "packet.cu", "relight.cu", "relight_tc.cu", "relight_noalloc.cu", "render.cu",
-           "autotune.cu", "training.cu"]
+           "autotune.cu", "training.cu", "bounce_bwd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -171,6 +171,31 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                              workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+// ---- backward of the self-transfer bounces ----
+
+size_t prtgs_bounce_backward_workspace_size(int64_t n, int32_t sh_order, int32_t n_bounces) {
+  if (n < 0 || check_order_high(sh_order) || n_bounces < 0 || n_bounces > 64) return 0;
+  return bounce_backward_workspace(n, sh_order, n_bounces);
+}
+
+int prtgs_bounce_backward(int64_t n, int32_t sh_order, int32_t n_dirs, const float* dirs, const float* normals,
+                          const float* albedo, const float* P, const int32_t* idx, int32_t n_bounces, const float* dT,
+                          float* dP, float* d_albedo, float* d_normals, int32_t* status, void* workspace,
+                          size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc;
+  if (n < 0) return PRTGS_ERR_SHAPE;
+  if ((rc = check_order_high(sh_order))) return rc;
+  if (prtgs::transfer_check_dirs(n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (n_bounces < 0 || n_bounces > 64) return PRTGS_ERR_INVALID_ARG;
+  if (n == 0) return PRTGS_OK;
+  if (!dirs || !normals || !albedo || !P || !idx || !dT || !dP || !d_albedo || !d_normals)
+    return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, bounce_backward_workspace(n, sh_order, n_bounces));
+  if (rc) return rc;
+  return finish(bounce_backward(n, sh_order, n_dirs, dirs, normals, albedo, P, idx, n_bounces, dT, dP, d_albedo,
+                                d_normals, status, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // ---- visibility cache, training-stage transfer, pseudo-normal, normal loss ----
 
 size_t prtgs_visibility_workspace_size(int64_t n, const prtgs_transfer_params* p) {

@@ -32,6 +32,16 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
                         cudaStream_t stream, float* V_out = nullptr);
 // whether the glossy matrices of S directions at this order fit one block's shared memory
 bool glossy_fits(int S, int order);
+// one bounce of the self-transfer (Eq. 33-35): Tcur = B(Tprev), or B(P) when Tprev is NULL
+// (Tscratch receives the forward's running sum and is not read afterwards)
+int bounce_step(int64_t n, int C, int S, const float* dirs, const float* normals, const float* albedo, const float* P,
+                const float* Tprev, const int32_t* idx, float* Tscratch, float* Tcur, int32_t* status,
+                cudaStream_t stream);
+// bounce_bwd.cu: backward of the bounces with the index matrix fixed
+size_t bounce_backward_workspace(int64_t n, int32_t order, int32_t n_bounces);
+int bounce_backward(int64_t n, int32_t order, int32_t S, const float* dirs, const float* normals,
+                    const float* albedo, const float* P, const int32_t* idx, int32_t n_bounces, const float* dT,
+                    float* dP, float* d_albedo, float* d_normals, int32_t* status, void* ws, cudaStream_t stream);
 // Y[S, (order+1)^2] of the direction set, orders 1..6 (FP64, rounded once)
 int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream);
 

@@ -1069,6 +1069,21 @@ int precompute_transfer(const prtgs_gaussians* g, const prtgs_bvh* bvh, const pr
   return PRTGS_OK;
 }
 
+int bounce_step(int64_t n, int C, int S, const float* dirs, const float* normals, const float* albedo, const float* P,
+                const float* Tprev, const int32_t* idx, float* Tscratch, float* Tcur, int32_t* status,
+                cudaStream_t stream) {
+  if (n == 0) return PRTGS_OK;
+  const unsigned blocks = (unsigned)((n + 7) / 8);
+  if (!Tprev)
+    k_bounce<true><<<blocks, 256, 0, counted(stream)>>>(n, C, S, dirs, normals, albedo, P, nullptr, idx, Tscratch, Tcur,
+                                                        status);
+  else
+    k_bounce<false><<<blocks, 256, 0, counted(stream)>>>(n, C, S, dirs, normals, albedo, P, Tprev, idx, Tscratch, Tcur,
+                                                         status);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
 int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream) {
   if (S <= 0) return PRTGS_OK;
   k_sh_table<<<(unsigned)((S + 127) / 128), 128, 0, counted(stream)>>>(S, order, dirs, Y);

@@ -494,3 +494,70 @@ def test_high_order_bounce_matches_oracle(nb):
     tr = oracle.transfer(sc, dirs, 6, np.arange(sc.n), bounce=True)
     Tref, allow = oracle.multi_bounce(sc, dirs, 6, tr, nb)
     _check_norm(T, Tref, allow.max(axis=1), 1e-3 * oracle.unoccluded_norm(6))
+
+
+# ---- backward of the bounces (Eq. 33-35, index matrix fixed) -------------------------------
+@pytest.mark.parametrize("order,nb", [(3, 1), (2, 3), (6, 2)])
+def test_bounce_backward_matches_autograd(order, nb):
+    """dT -> dP, d_albedo, d_normals through the bounces against FP64 autograd of the
+    bounce restatement on the GPU's own P and index matrix."""
+    from oracle import transfer_torch as TT
+
+    sc = _crowded(1200, 40 + order)
+    dirs = S.direction_set(64, 6)
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    d = torch.from_numpy(dirs).cuda()
+    out = api.precompute_transfer(g, bvh, d, order, bounce=True, n_bounces=nb, status=st)
+    C = (order + 1) ** 2
+    dT = np.random.default_rng(order + nb).standard_normal((sc.n, 3, C)).astype(np.float32)
+    dP, da, dn = api.bounce_backward(g, d, order, out["P"], out["idx"], torch.from_numpy(dT).cuda(), nb, status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    idx = out["idx"].cpu().numpy()
+    assert (idx >= 0).mean() > 0.1
+    t = lambda a, rg=False: torch.tensor(np.asarray(a, np.float64), requires_grad=rg)
+    P, rho, nrm = t(out["P"].cpu().numpy(), True), t(sc.albedo, True), t(sc.normals, True)
+    T = TT.bounce_T(P, idx, dirs, nrm, rho, nb)
+    np.testing.assert_allclose(out["T"].cpu().numpy(), T.detach().numpy(), rtol=0,
+                               atol=2e-6 * float(T.detach().abs().max()))
+    ref = torch.autograd.grad((T * torch.as_tensor(dT.astype(np.float64))).sum(), (P, rho, nrm))
+    for got, r, name in zip((dP, da, dn), ref, ("dP", "d_albedo", "d_normals")):
+        got = got.cpu().numpy().astype(np.float64)
+        r = r.numpy()
+        assert np.linalg.norm(got - r) <= 1e-5 * np.linalg.norm(r), (name, np.linalg.norm(got - r) / np.linalg.norm(r))
+        assert np.linalg.norm(r) > 0
+
+
+def test_bounce_transfer_gradient_to_the_gaussians():
+    """L = sum(W * T) for the one-bounce T: the geometry, normal and albedo gradients of
+    BounceTransfer (bounce backward, then the transfer backward) against FP64 autograd of the
+    brute-force P chained into the bounce restatement, with the GPU's index matrix held fixed."""
+    from oracle import transfer_torch as TT
+
+    sc = _crowded(260, 17)
+    dirs = S.direction_set(40, 5)
+    order = 2
+    C = (order + 1) ** 2
+    fields = ("means", "scales", "quats", "opacity", "normals", "albedo")
+    gp = [torch.tensor(np.asarray(getattr(sc, f), np.float32), device="cuda", requires_grad=True) for f in fields]
+    d = torch.from_numpy(dirs).cuda()
+    T = api.bounce_transfer(*gp, d, order, 1, 0.0)
+    W = np.random.default_rng(3).standard_normal((sc.n, 3, C))
+    (T * torch.as_tensor(W, dtype=torch.float32, device="cuda")).sum().backward()
+    gpu = {f: p.grad.cpu().numpy().astype(np.float64) for f, p in zip(fields, gp)}
+    # the index matrix of the same forward, held fixed in the reference
+    g = _gt(sc)
+    idx = api.precompute_transfer(g, api.build_bvh(g), d, order, bounce=True, t_min=0.0)["idx"].cpu().numpy()
+    ps = [torch.tensor(np.asarray(getattr(sc, f), np.float64), requires_grad=True) for f in fields]
+    P = TT.transfer_P(*ps[:5], dirs, oracle.sh(order, dirs))
+    Tr = TT.bounce_T(P, idx, dirs, ps[4], ps[5], 1)
+    np.testing.assert_allclose(T.detach().cpu().numpy(), Tr.detach().numpy(), rtol=0, atol=1e-4)
+    ref = torch.autograd.grad((Tr * torch.as_tensor(W)).sum(), ps)
+    top = max(np.linalg.norm(r.numpy()) for r in ref)
+    for f, r in zip(fields, ref):
+        r = r.numpy()
+        nb = max(np.linalg.norm(r), 1e-3 * top)
+        assert np.linalg.norm(gpu[f] - r) <= 2e-3 * nb, (f, np.linalg.norm(gpu[f] - r) / nb)
+    assert np.linalg.norm(ref[5].numpy()) > 0 and np.linalg.norm(ref[3].numpy()) > 0
