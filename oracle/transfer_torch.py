@@ -32,14 +32,27 @@ def _hit_test(means, Sinv, recv_means, d, j0, j1):
 
 def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
     """P [len(recv),C] for the receivers ``recv`` (default: all, in index order); every Gaussian
-    is an occluder. dirs [S,3] and Y [S,C] (SH table) are constants.
+    is an occluder. dirs [S,3] and Y [S,C] (SH table) are constants: P = (w V (n.w)^+) Y with V
+    from ``transfer_V``."""
+    d = torch.as_tensor(np.asarray(dirs, np.float64))
+    Y = torch.as_tensor(np.asarray(Y, np.float64))
+    n = means.shape[0]
+    recv = torch.arange(n) if recv is None else torch.as_tensor(np.asarray(recv), dtype=torch.long)
+    V = transfer_V(means, scales, quats, opacity, normals, dirs, recv)
+    c = normals[recv] @ d.T
+    w = 4.0 * math.pi / d.shape[0]
+    return torch.where((c > 0).detach(), w * V * c, torch.zeros_like(c)) @ Y
+
+
+def transfer_V(means, scales, quats, opacity, normals, dirs, recv=None):
+    """Visibility V [len(recv),S] of the receivers' rays (0 on the rays with n.w <= 0, which are
+    not traced); every Gaussian is an occluder.
 
     A Gaussian that no traced ray (n.w > 0) of receiver i hits contributes a factor 1 to each of
-    the visibility products that reach P_i, and nothing to the gradient, so after the (detached)
+    the visibility products of receiver i, and nothing to the gradient, so after the (detached)
     hit test over all Gaussians the differentiable product of receiver i runs over the ones its
     traced rays hit."""
     d = torch.as_tensor(np.asarray(dirs, np.float64))
-    Y = torch.as_tensor(np.asarray(Y, np.float64))
     n = means.shape[0]
     S = d.shape[0]
     recv = torch.arange(n) if recv is None else torch.as_tensor(np.asarray(recv), dtype=torch.long)
@@ -54,14 +67,12 @@ def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
             h = _hit_test(means.detach(), Sinv.detach(), means.detach()[recv], d, j0, j1)
             occ_mask[:, j0:j1] = (h & traced[:, None, :]).any(dim=2)
         occ_mask[torch.arange(len(recv)), recv] = False  # the receiver itself is no occluder
-    w = 4.0 * math.pi / S
     rows = []
     for r, i in enumerate(recv.tolist()):
         occ = torch.nonzero(occ_mask[r]).flatten()
-        c = normals[i] @ d.T  # [S]
-        up = (c > 0).detach()
+        up = traced[r]
         if occ.numel() == 0:  # nothing hit: V = 1 on every traced ray
-            rows.append(torch.where(up, w * c, torch.zeros_like(c)))
+            rows.append(torch.where(up, torch.ones(S, dtype=means.dtype), torch.zeros(S, dtype=means.dtype)))
             continue
         u = means[i][None, :] - means[occ]  # [No,3] = o - mu_j
         So = Sinv[occ]
@@ -75,8 +86,8 @@ def transfer_P(means, scales, quats, opacity, normals, dirs, Y, recv=None):
         alpha = opacity[occ][:, None] * torch.exp(-0.5 * D2)
         one_m = torch.where(hit, 1.0 - alpha, torch.ones_like(alpha))
         V = torch.prod(one_m, dim=0)  # [S]
-        rows.append(torch.where(up, w * V * c, torch.zeros_like(c)))
-    return torch.stack(rows) @ Y
+        rows.append(torch.where(up, V, torch.zeros_like(V)))
+    return torch.stack(rows)
 
 
 def bounce_T(P, idx, dirs, normals, albedo, n_bounces: int = 1):
@@ -100,3 +111,48 @@ def bounce_T(P, idx, dirs, normals, albedo, n_bounces: int = 1):
         prev = (coef[:, :, None, None] * G).sum(dim=1)
         total = total + prev
     return total
+
+
+def brdf_kernel(n, wi, wo, roughness, metallic):
+    """k(w_i, w_o) = (1-m) + pi D F G / (4 (n.w_i)(n.w_o)) for the unit normal n/|n| (the glossy
+    kernel of Eq. 15, with GGX D, Schlick F (F0 = 0.04) on w_o.h and Smith-Schlick G, k = alpha/2,
+    alpha = r^2), zero unless n.w_i > 0 and n.w_o > 0 (held fixed). n [3]; wi [S,1,3], wo [1,S,3]
+    broadcast; differentiable in n, roughness, metallic."""
+    nu = n / torch.linalg.norm(n)
+    ni = (wi * nu).sum(-1)
+    no = (wo * nu).sum(-1)
+    h = wi + wo
+    hn = torch.linalg.norm(h, dim=-1, keepdim=True)
+    h = h / torch.where(hn > 0, hn, torch.ones_like(hn))
+    nh = (h * nu).sum(-1)
+    oh = torch.clamp((wo * h).sum(-1), 0.0, 1.0)
+    a = roughness * roughness
+    a2 = a * a
+    D = a2 / (math.pi * (nh * nh * (a2 - 1.0) + 1.0) ** 2)
+    F = 0.04 + 0.96 * (1.0 - oh) ** 5
+    kk = a / 2.0
+    g = lambda x: 1.0 / (x * (1.0 - kk) + kk)  # G1(x) / x
+    on = ((ni > 0) & (no > 0)).detach()
+    k = (1.0 - metallic) + math.pi * 0.25 * D * F * g(torch.where(on, ni, torch.ones_like(ni))) * \
+        g(torch.where(on, no, torch.ones_like(no)))
+    return torch.where(on, k, torch.zeros_like(k))
+
+
+def glossy_M(V, normals, roughness, metallic, dirs, Y):
+    """M [R,C,C] = sum_s sum_o w^2 Y(w_s) k(w_s,w_o) (n.w_s)^+ V_s Y(w_o)^T (Eq. 40 with the in/out
+    double sum over the direction set), differentiable in V [R,S], normals [R,3] (raw: the cosine
+    takes n, the kernel n/|n|), roughness [R], metallic [R]."""
+    d = torch.as_tensor(np.asarray(dirs, np.float64))
+    Y = torch.as_tensor(np.asarray(Y, np.float64))
+    S = d.shape[0]
+    w = 4.0 * math.pi / S
+    out = []
+    for r in range(V.shape[0]):
+        n = normals[r]
+        K = brdf_kernel(n, d[:, None, :], d[None, :, :], roughness[r], metallic[r])  # [S_in,S_out]
+        c = torch.clamp(d @ n, min=0.0)
+        B = w * (K @ Y)  # [S,C]
+        a = w * c * V[r]
+        out.append((Y * a[:, None]).T @ B)
+    return torch.stack(out)
+
