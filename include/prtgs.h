@@ -240,6 +240,36 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                        size_t workspace_bytes, prtgs_stream_t stream);
 
 /*
+ * Backward of the glossy transfer matrices (Eq. 40): from dM = dLoss/dM [n_glossy,C,C] (the glossy
+ * splats in increasing Gaussian order, as prtgs_precompute_transfer returns M) to
+ *   dV[n,S]         out: dLoss/dV_is of each glossy receiver's rays (0 for the others); pass it to
+ *                   prtgs_precompute_transfer_backward_v to reach the occluders' geometry
+ *   d_roughness[n], d_metallic[n]  out: through the BRDF kernel k (GGX with alpha = r^2; k = 1 - m + ...)
+ *   d_normals[n,3]  out: through the cosine max(0, n.w_s) (raw normal) and the kernel (n / |n|)
+ * With U_so = Y(w_s)^T dM Y(w_o): dLoss/dV_s = w^2 (n.w_s)^+ sum_o k(s,o) U_so, and the others as
+ * the derivatives of sum_s sum_o w^2 (n.w_s)^+ V_s k(s,o) U_so. The cut-offs n.w > 0 are held
+ * fixed. V[n,S] is the visibility of prtgs_precompute_visibility (same walk as the forward).
+ * Outputs are overwritten (deterministic). Workspace: prtgs_glossy_backward_workspace_size;
+ * PRTGS_ERR_UNSUPPORTED when the block's shared memory (3S + 2SC + C^2 floats) exceeds 227 KB.
+ */
+size_t prtgs_glossy_backward_workspace_size(int64_t n, const prtgs_transfer_params* p);
+int prtgs_glossy_backward(const prtgs_gaussians* g, const prtgs_transfer_params* p, const float* V, const float* dM,
+                          int64_t n_glossy, float* dV, float* d_roughness, float* d_metallic, float* d_normals,
+                          int32_t* status, void* workspace, size_t workspace_bytes, prtgs_stream_t stream);
+
+/*
+ * prtgs_precompute_transfer_backward with an additional per-ray visibility gradient: dV[n,S]
+ * (nullable) is added to the dLoss/dV_is that dP implies (w (n_i.w_s)^+ Y(w_s) . dP_i) before the
+ * walk pushes it to the occluders; dP (nullable) as before. Receivers whose dP and dV rows are
+ * zero are skipped. Same workspace and errors as prtgs_precompute_transfer_backward.
+ */
+int prtgs_precompute_transfer_backward_v(const prtgs_gaussians* g, const prtgs_bvh* bvh,
+                                         const prtgs_transfer_params* p, const float* dP, const float* dV,
+                                         float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                                         float* d_normals, int32_t* status, void* workspace, size_t workspace_bytes,
+                                         prtgs_stream_t stream);
+
+/*
  * Backward of the self-transfer bounces (Eq. 33-35) with the index matrix held fixed (its argmax
  * is a discrete decision). Forward, per channel c: T = T^0 + ... + T^n, T^0_i = P_i,
  * T^k_i[c] = sum_s (4 pi/S) max(0, n_i.w_s) (albedo_j[c]/pi) T^{k-1}_j[c], j = idx[i,s]; the call

@@ -131,6 +131,12 @@ _SIGS = {
     "prtgs_relight_backward_batched": (c_int32, [c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                                  c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                                  c_size_t, c_void_p]),
+    "prtgs_glossy_backward_workspace_size": (c_size_t, [c_int64, P(TransferParams)]),
+    "prtgs_glossy_backward": (c_int32, [P(Gaussians), P(TransferParams), c_void_p, c_void_p, c_int64, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "prtgs_precompute_transfer_backward_v": (c_int32, [P(Gaussians), P(BVH), P(TransferParams), c_void_p, c_void_p,
+                                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                       c_void_p, c_size_t, c_void_p]),
     "prtgs_bounce_backward_workspace_size": (c_size_t, [c_int64, c_int32, c_int32]),
     "prtgs_bounce_backward": (c_int32, [c_int64, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,

@@ -170,9 +170,10 @@ def precompute_transfer(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order:
 
 def precompute_transfer_backward(g: GaussianTensors, bvh: Bvh, dirs: torch.Tensor, order: int, dP: torch.Tensor,
                                  shadow: bool = True, t_min: float = DEFAULT_T_MIN, status: Status | None = None,
-                                 stats: torch.Tensor | None = None):
-    """Gradients of a loss through P [n,C] (shadowed diffuse transfer) to the Gaussians:
-    dict of d_means [n,3], d_scales [n,3], d_quats [n,4], d_opacity [n], d_normals [n,3]."""
+                                 stats: torch.Tensor | None = None, dV: torch.Tensor | None = None):
+    """Gradients of a loss through P [n,C] (shadowed diffuse transfer) and, optionally, through the
+    rays' visibility directly (dV [n,S], e.g. from the glossy matrices) to the Gaussians: dict of
+    d_means [n,3], d_scales [n,3], d_quats [n,4], d_opacity [n], d_normals [n,3]."""
     lib = L.load()
     dev = g.means.device
     n = g.n
@@ -180,15 +181,22 @@ def precompute_transfer_backward(g: GaussianTensors, bvh: Bvh, dirs: torch.Tenso
     grads = {"d_means": torch.empty((n, 3), **f32), "d_scales": torch.empty((n, 3), **f32),
              "d_quats": torch.empty((n, 4), **f32), "d_opacity": torch.empty((n,), **f32),
              "d_normals": torch.empty((n, 3), **f32)}
-    dP = dP.contiguous()
+    dP = dP.contiguous() if dP is not None else None
     p = L.TransferParams(order, int(dirs.shape[0]), _ptr(dirs), float(t_min), 1.0, L.SHADOW if shadow else 0, 0,
                          _ptr(stats))
     ws, nb = _ws(lib.prtgs_transfer_backward_workspace_size(n, ctypes.byref(p)), dev)
     gs = g.struct()
-    L.check(lib.prtgs_precompute_transfer_backward(
-        ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(dP), _ptr(grads["d_means"]),
-        _ptr(grads["d_scales"]), _ptr(grads["d_quats"]), _ptr(grads["d_opacity"]), _ptr(grads["d_normals"]),
-        status.ptr() if status else None, _ptr(ws), nb, _stream()), "prtgs_precompute_transfer_backward")
+    if dV is None:
+        L.check(lib.prtgs_precompute_transfer_backward(
+            ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(dP), _ptr(grads["d_means"]),
+            _ptr(grads["d_scales"]), _ptr(grads["d_quats"]), _ptr(grads["d_opacity"]), _ptr(grads["d_normals"]),
+            status.ptr() if status else None, _ptr(ws), nb, _stream()), "prtgs_precompute_transfer_backward")
+    else:
+        L.check(lib.prtgs_precompute_transfer_backward_v(
+            ctypes.byref(gs), ctypes.byref(bvh.s), ctypes.byref(p), _ptr(dP), _ptr(dV.contiguous()),
+            _ptr(grads["d_means"]), _ptr(grads["d_scales"]), _ptr(grads["d_quats"]), _ptr(grads["d_opacity"]),
+            _ptr(grads["d_normals"]), status.ptr() if status else None, _ptr(ws), nb, _stream()),
+            "prtgs_precompute_transfer_backward_v")
     grads["_ws"] = ws
     return grads
 
@@ -667,4 +675,63 @@ class BounceTransfer(torch.autograd.Function):
 
 def bounce_transfer(means, scales, quats, opacity, normals, albedo, dirs, order, n_bounces=1, t_min=DEFAULT_T_MIN):
     return BounceTransfer.apply(means, scales, quats, opacity, normals, albedo, dirs, order, n_bounces, t_min)
+
+
+def glossy_backward(g: GaussianTensors, dirs: torch.Tensor, order: int, V: torch.Tensor, dM: torch.Tensor,
+                    status: Status | None = None):
+    """Backward of the glossy matrices (Eq. 40): dM [n_glossy,C,C] -> dV [n,S] (for
+    precompute_transfer_backward's dV), d_roughness [n], d_metallic [n], d_normals [n,3]."""
+    lib = L.load()
+    dev = g.means.device
+    n = g.n
+    S = int(dirs.shape[0])
+    n_glossy = int(dM.shape[0])
+    f32 = dict(dtype=torch.float32, device=dev)
+    dV = torch.empty((n, S), **f32)
+    dr, dm, dn = torch.empty(n, **f32), torch.empty(n, **f32), torch.empty((n, 3), **f32)
+    p = L.TransferParams(order, S, _ptr(dirs), float(DEFAULT_T_MIN), 1.0, L.SHADOW | L.GLOSSY, 0, None)
+    ws, nb = _ws(lib.prtgs_glossy_backward_workspace_size(n, ctypes.byref(p)), dev)
+    gs = g.struct()
+    L.check(lib.prtgs_glossy_backward(ctypes.byref(gs), ctypes.byref(p), _ptr(V), _ptr(dM.contiguous()), n_glossy,
+                                      _ptr(dV), _ptr(dr), _ptr(dm), _ptr(dn), status.ptr() if status else None,
+                                      _ptr(ws), nb, _stream()), "prtgs_glossy_backward")
+    return dV, dr, dm, dn
+
+
+class GlossyTransfer(torch.autograd.Function):
+    """(P, M): the shadowed diffuse transfer of every Gaussian (Eq. 29) and the glossy matrices of the
+    glossy ones (Eq. 40), with the hand-written backward: the glossy backward turns dM into a
+    visibility gradient per ray (and roughness, metallic, normal gradients), and the transfer
+    backward takes dP and that visibility gradient to the geometry. Differentiable in means,
+    scales, quats, opacity, normals, roughness and metallic; the glossy mask is fixed."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, normals, roughness, metallic, glossy_mask, albedo, dirs, order,
+                t_min):
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), opacity.contiguous(),
+                            normals.contiguous(), albedo.contiguous(), roughness.contiguous(), metallic.contiguous(),
+                            glossy_mask.contiguous())
+        st = Status()
+        bvh = build_bvh(g, status=st)
+        out = precompute_transfer(g, bvh, dirs, order, glossy=True, t_min=t_min, status=st)
+        ctx.g, ctx.bvh, ctx.st, ctx.dirs, ctx.order, ctx.t_min = g, bvh, st, dirs, order, t_min
+        return out["P"], out["M"]
+
+    @staticmethod
+    def backward(ctx, dP, dM):
+        g = ctx.g
+        V = precompute_visibility(g, ctx.bvh, ctx.dirs, ctx.order, t_min=ctx.t_min, status=ctx.st)["V"]
+        if dM is None:
+            dM = torch.zeros((int(g.glossy_mask.sum().item()), sh_count(ctx.order), sh_count(ctx.order)),
+                             dtype=torch.float32, device=g.means.device)
+        dV, dr, dm, dn = glossy_backward(g, ctx.dirs, ctx.order, V, dM, status=ctx.st)
+        gr = precompute_transfer_backward(g, ctx.bvh, ctx.dirs, ctx.order, dP, t_min=ctx.t_min, status=ctx.st, dV=dV)
+        return (gr["d_means"], gr["d_scales"], gr["d_quats"], gr["d_opacity"], gr["d_normals"] + dn, dr, dm, None,
+                None, None, None, None)
+
+
+def glossy_transfer(means, scales, quats, opacity, normals, roughness, metallic, glossy_mask, albedo, dirs, order,
+                    t_min=DEFAULT_T_MIN):
+    return GlossyTransfer.apply(means, scales, quats, opacity, normals, roughness, metallic, glossy_mask, albedo, dirs,
+                                order, t_min)
 

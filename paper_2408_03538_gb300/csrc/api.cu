@@ -171,6 +171,53 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
                                              workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+// ---- backward of the glossy matrices, and the transfer backward with a visibility gradient ----
+
+size_t prtgs_glossy_backward_workspace_size(int64_t n, const prtgs_transfer_params* p) {
+  if (!p || n < 0 || check_order_high(p->sh_order)) return 0;
+  return glossy_backward_workspace(n, p);
+}
+
+int prtgs_glossy_backward(const prtgs_gaussians* g, const prtgs_transfer_params* p, const float* V, const float* dM,
+                          int64_t n_glossy, float* dV, float* d_roughness, float* d_metallic, float* d_normals,
+                          int32_t* status, void* workspace, size_t workspace_bytes, prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!p) return PRTGS_ERR_INVALID_ARG;
+  if ((rc = check_order_high(p->sh_order))) return rc;
+  if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!prtgs::glossy_backward_fits(p->n_dirs, p->sh_order)) return PRTGS_ERR_UNSUPPORTED;
+  if (n_glossy < 0 || n_glossy > g->n) return PRTGS_ERR_SHAPE;
+  if (g->n == 0) return PRTGS_OK;
+  if (!p->dirs || !dV || !d_roughness || !d_metallic || !d_normals || !g->normals) return PRTGS_ERR_INVALID_ARG;
+  if (n_glossy > 0 && (!V || !dM || !g->glossy_mask || !g->roughness || !g->metallic)) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, glossy_backward_workspace(g->n, p));
+  if (rc) return rc;
+  return finish(glossy_backward(g, p, V, dM, n_glossy, dV, d_roughness, d_metallic, d_normals, status, workspace,
+                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int prtgs_precompute_transfer_backward_v(const prtgs_gaussians* g, const prtgs_bvh* bvh,
+                                         const prtgs_transfer_params* p, const float* dP, const float* dV,
+                                         float* d_means, float* d_scales, float* d_quats, float* d_opacity,
+                                         float* d_normals, int32_t* status, void* workspace, size_t workspace_bytes,
+                                         prtgs_stream_t stream) {
+  int rc = check_gaussians(g);
+  if (rc) return rc;
+  if (!p || !bvh) return PRTGS_ERR_INVALID_ARG;
+  if ((rc = check_order_high(p->sh_order))) return rc;
+  if (p->flags & ~PRTGS_SHADOW) return PRTGS_ERR_UNSUPPORTED;
+  if (prtgs::transfer_check_dirs(p->n_dirs) != PRTGS_OK) return PRTGS_ERR_UNSUPPORTED;
+  if (!p->dirs || !(p->t_min >= 0.f)) return PRTGS_ERR_INVALID_ARG;
+  if (bvh->n != g->n) return PRTGS_ERR_SHAPE;
+  if (g->n == 0) return PRTGS_OK;
+  if (!g->normals || !d_means || !d_scales || !d_quats || !d_opacity || !d_normals) return PRTGS_ERR_INVALID_ARG;
+  rc = check_ws(workspace, workspace_bytes, transfer_backward_workspace(g->n, p));
+  if (rc) return rc;
+  return finish(precompute_transfer_backward(g, bvh, p, dP, d_means, d_scales, d_quats, d_opacity, d_normals, status,
+                                             workspace, reinterpret_cast<cudaStream_t>(stream), dV));
+}
+
 // ---- backward of the self-transfer bounces ----
 
 size_t prtgs_bounce_backward_workspace_size(int64_t n, int32_t sh_order, int32_t n_bounces) {

@@ -89,4 +89,46 @@ __device__ __forceinline__ float brdf_kernel_dr(float nx, float ny, float nz, co
   return q * (dD * 4.0f * alpha * r - D * r * ((1.0f - xi) * gi + (1.0f - xo) * go));
 }
 
+// dk/dn for the raw normal n (the kernel depends on n / |n|; the metallic term does not depend on
+// it): with u = n/|n|, h = (w_i + w_o)/|w_i + w_o| and x_h = u.h, x_i = u.w_i, x_o = u.w_o,
+//   dk/du = pi/4 F [D'(x_h) g_i g_o h + D g_o g'(x_i) w_i + D g_i g'(x_o) w_o],
+//   D'(x) = -4 a2 x (a2 - 1) / (pi den^3), den = x^2 (a2 - 1) + 1,  g'(x) = -(1 - kk) g(x)^2,
+// and dk/dn = (dk/du - u (u . dk/du)) / |n|. For gradients; the value of k comes from brdf_kernel.
+__device__ __forceinline__ void brdf_kernel_dn(float nx, float ny, float nz, const float* wi, const float* wo, float r,
+                                               float* dkdn) {
+  const float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+  const float rn = rsqrtf(nn);
+  const float ux = nx * rn, uy = ny * rn, uz = nz * rn;
+  float hx = wi[0] + wo[0], hy = wi[1] + wo[1], hz = wi[2] + wo[2];
+  const float hl = rsqrtf(fmaf(hx, hx, fmaf(hy, hy, hz * hz)));
+  hx *= hl;
+  hy *= hl;
+  hz *= hl;
+  const float xh = fmaf(ux, hx, fmaf(uy, hy, uz * hz));
+  const float xi = fmaf(ux, wi[0], fmaf(uy, wi[1], uz * wi[2]));
+  const float xo = fmaf(ux, wo[0], fmaf(uy, wo[1], uz * wo[2]));
+  const float oh = fminf(fmaxf(fmaf(wo[0], hx, fmaf(wo[1], hy, wo[2] * hz)), 0.f), 1.f);
+  const float alpha = r * r, a2 = alpha * alpha;
+  const float den = fmaf(xh * xh, a2 - 1.0f, 1.0f);
+  const float pden = __fdividef(1.0f, kPi * den * den);
+  const float D = a2 * pden;
+  const float dD = __fdividef(-4.0f * a2 * xh * (a2 - 1.0f) * pden, den);
+  const float x = 1.0f - oh, x2 = x * x;
+  const float F = fmaf(0.96f, x2 * x2 * x, 0.04f);
+  const float kk = 0.5f * alpha;
+  const float gi = __fdividef(1.0f, fmaf(xi, 1.0f - kk, kk));
+  const float go = __fdividef(1.0f, fmaf(xo, 1.0f - kk, kk));
+  const float q = kPi * 0.25f * F;
+  const float ch = q * dD * gi * go;
+  const float ci = -q * D * go * (1.0f - kk) * gi * gi;
+  const float co = -q * D * gi * (1.0f - kk) * go * go;
+  const float gx = ch * hx + ci * wi[0] + co * wo[0];
+  const float gy = ch * hy + ci * wi[1] + co * wo[1];
+  const float gz = ch * hz + ci * wi[2] + co * wo[2];
+  const float d = fmaf(ux, gx, fmaf(uy, gy, uz * gz));
+  dkdn[0] = (gx - ux * d) * rn;
+  dkdn[1] = (gy - uy * d) * rn;
+  dkdn[2] = (gz - uz * d) * rn;
+}
+
 }  // namespace prtgs

@@ -50,9 +50,17 @@ struct TraceArgs;
 int launch_packet(const TraceArgs& a, float* V, bool bounce, int sms, cudaStream_t stream);
 
 size_t transfer_backward_workspace(int64_t n, const prtgs_transfer_params* p);
+// dP [n,C] and dV [n,S] (extra dLoss/dV per ray, e.g. from the glossy matrices) are both nullable
 int precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
                                  const float* dP, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
-                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream);
+                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream,
+                                 const float* dV = nullptr);
+// glossy-matrix backward (Eq. 40): dM -> dV [n,S] (to the transfer backward), roughness, metallic, normals
+size_t glossy_backward_workspace(int64_t n, const prtgs_transfer_params* p);
+int glossy_backward(const prtgs_gaussians* g, const prtgs_transfer_params* p, const float* V, const float* dM,
+                    int64_t n_glossy, float* dV, float* d_roughness, float* d_metallic, float* d_normals,
+                    int32_t* status, void* ws, cudaStream_t stream);
+bool glossy_backward_fits(int S, int order);
 
 // relight.cu
 size_t relight_workspace(int64_t n, int32_t order, int32_t k, int32_t precision);

@@ -438,7 +438,8 @@ __device__ __forceinline__ bool gauss_hit_geom(const float4* __restrict__ recs, 
 
 struct GradArgs {
   const float* quats;
-  const float* dP;
+  const float* dP;  // [n,C], nullable (zero)
+  const float* dV;  // [n,S] dLoss/dV of each ray beyond what P carries (the glossy matrices), nullable
   float* d_means;
   float* d_scales;
   float* d_quats;
@@ -525,11 +526,16 @@ __global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(T
     bool any = false;
 #pragma unroll
     for (int k = 0; k < kMaxC; ++k) {
-      dP[k] = k < C ? g.dP[(int64_t)gid * C + k] : 0.f;
+      dP[k] = (g.dP && k < C) ? g.dP[(int64_t)gid * C + k] : 0.f;
       any |= dP[k] != 0.0f;
     }
-    for (int k = kMaxC; k < C; ++k) any |= g.dP[(int64_t)gid * C + k] != 0.0f;  // orders 4-6
-    if (!any) continue;  // a receiver with dP_i = 0 contributes nothing (warp-uniform)
+    if (g.dP)
+      for (int k = kMaxC; k < C; ++k) any |= g.dP[(int64_t)gid * C + k] != 0.0f;  // orders 4-6
+    bool any_v = false;
+    if (g.dV)
+      for (int s = lane; s < a.S; s += 32) any_v |= g.dV[(int64_t)gid * a.S + s] != 0.0f;
+    any = any || __any_sync(0xffffffffu, any_v);
+    if (!any) continue;  // a receiver with dP_i = 0 (and dV_i = 0) contributes nothing (warp-uniform)
     int cnt = 0;
     for (int base = 0; base < a.S; base += 32) {
       const int s = base + lane;
@@ -573,7 +579,7 @@ __global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(T
       gn[0] += gsum * V * d[0];
       gn[1] += gsum * V * d[1];
       gn[2] += gsum * V * d[2];
-      const float gV = gsum * c;
+      const float gV = gsum * c + (g.dV ? g.dV[(int64_t)gid * a.S + s] : 0.0f);
       if ((a.flags & PRTGS_SHADOW) && gV != 0.0f) {
         BwdVis bv{a, g, r, self, rs, 1.0f, gV * V, {0.f, 0.f, 0.f}};
         traverse(a, r, root, 0.0f, bv, rs, rs.search_nodes);
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__(kTraceThreads, kRoundsMinBlocks) k_trace_bwd(T
 
 int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh, const prtgs_transfer_params* p,
                                  const float* dP, float* d_means, float* d_scales, float* d_quats, float* d_opacity,
-                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream) {
+                                 float* d_normals, int32_t* status, void* ws, cudaStream_t stream, const float* dV) {
   const int64_t n = gs->n;
   cudaMemsetAsync(d_means, 0, sizeof(float) * 3 * n, stream);
   cudaMemsetAsync(d_scales, 0, sizeof(float) * 3 * n, stream);
@@ -644,7 +650,7 @@ int precompute_transfer_backward(const prtgs_gaussians* gs, const prtgs_bvh* bvh
   a.stats = p->stats;
   a.r0 = 0;
   a.r1 = n;
-  GradArgs g{gs->quats, dP, d_means, d_scales, d_quats, d_opacity, d_normals};
+  GradArgs g{gs->quats, dP, dV, d_means, d_scales, d_quats, d_opacity, d_normals};
   const size_t smem = sizeof(float) * 3 * p->n_dirs + kTraceWarps * (size_t)p->n_dirs * 2;
   int per_sm = 0;
   cudaFuncSetAttribute(k_trace_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -800,6 +806,120 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, con
       float acc = 0.f;
       for (int s = 0; s < S; ++s) acc = fmaf(sU[s * C + ra], sB[s * C + cb], acc);
       M[(g * C + ra) * C + cb] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Backward of the glossy matrices (Eq. 40). With U_so = Y(w_s)^T dM Y(w_o) and c_s = n.w_s:
+//   L = sum_s sum_o w^2 c_s V_s k(s,o) U_so,
+//   dL/dV_s = w^2 c_s sum_o k(s,o) U_so,  dL/dr = sum_s w^2 c_s V_s sum_o U_so dk/dr,
+//   dL/dm = -sum_s w^2 c_s V_s sum_o U_so,  dL/dn = sum_s w^2 V_s sum_o U_so (k w_s + c_s dk/dn)
+// (the cosine takes the raw normal, the kernel n / |n|; the cut-offs n.w > 0 are held fixed).
+// One block per glossy splat; Q_o = dM Y(w_o) staged per splat, the threads over s.
+template <int C>
+__global__ void __launch_bounds__(kGlossyThreads) k_glossy_bwd(int64_t n_glossy, const int32_t* __restrict__ glossy_ids,
+                                                               int S, int order, const float* __restrict__ dirs,
+                                                               const float* __restrict__ Ytab,
+                                                               const float* __restrict__ normals,
+                                                               const float* __restrict__ roughness,
+                                                               const float* __restrict__ metallic,
+                                                               const float* __restrict__ V, const float* __restrict__ dM,
+                                                               float* __restrict__ dV, float* __restrict__ d_rough,
+                                                               float* __restrict__ d_metal, float* __restrict__ d_normals) {
+  extern __shared__ float smem[];
+  float* sdir = smem;         // [S*3]
+  float* sY = sdir + 3 * S;   // [S][C]
+  float* sQ = sY + S * C;     // [S][C]  dM Y(w_o)
+  float* sdM = sQ + S * C;    // [C*C]
+  __shared__ float red[5][kGlossyThreads / 32];
+  for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sdir[i] = dirs[i];
+  __syncthreads();
+  if (C > kMaxC) {
+    for (int e = threadIdx.x; e < S * C; e += blockDim.x) sY[e] = Ytab[e];
+  } else {
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      float Y[kMaxC];
+      sh_eval_dyn(order, sdir[3 * s], sdir[3 * s + 1], sdir[3 * s + 2], Y);
+      for (int k = 0; k < C && k < kMaxC; ++k) sY[s * C + k] = Y[k];
+    }
+  }
+  __syncthreads();
+  const float wq = 4.0f * kPi / (float)S;
+  const float w2 = wq * wq;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t g = blockIdx.x; g < n_glossy; g += gridDim.x) {
+    const int64_t i = glossy_ids[g];
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) sdM[e] = dM[g * C * C + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < S * C; e += blockDim.x) {
+      const int o = e / C, a = e % C;
+      float q = 0.f;
+      for (int b = 0; b < C; ++b) q = fmaf(sdM[a * C + b], sY[o * C + b], q);
+      sQ[e] = q;
+    }
+    __syncthreads();
+    const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
+    const float r = roughness[i], metal = metallic[i];
+    float gr = 0.f, gm = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      const float* wi = sdir + 3 * s;
+      const float c = fmaf(nx, wi[0], fmaf(ny, wi[1], nz * wi[2]));
+      float dv = 0.f;
+      if (c > 0.0f) {
+        const float v = V[i * S + s];
+        float Ys[C];
+#pragma unroll
+        for (int a = 0; a < C; ++a) Ys[a] = sY[s * C + a];
+        float kU = 0.f, rU = 0.f, mU = 0.f, nU[3] = {0.f, 0.f, 0.f};
+        for (int o = 0; o < S; ++o) {
+          const float* wo = sdir + 3 * o;
+          const float no = fmaf(nx, wo[0], fmaf(ny, wo[1], nz * wo[2]));
+          if (!(no > 0.0f)) continue;
+          float U = 0.f;
+#pragma unroll
+          for (int a = 0; a < C; ++a) U = fmaf(Ys[a], sQ[o * C + a], U);
+          float kv;
+          const float dkdr = brdf_kernel_dr(nx, ny, nz, wi, wo, c, no, r, metal, kv);
+          kU = fmaf(kv, U, kU);
+          if (v != 0.0f) {
+            rU = fmaf(U, dkdr, rU);
+            mU -= U;
+            float dn[3];
+            brdf_kernel_dn(nx, ny, nz, wi, wo, r, dn);
+            nU[0] = fmaf(U, dn[0], nU[0]);
+            nU[1] = fmaf(U, dn[1], nU[1]);
+            nU[2] = fmaf(U, dn[2], nU[2]);
+          }
+        }
+        dv = w2 * c * kU;
+        gr = fmaf(w2 * c * v, rU, gr);
+        gm = fmaf(w2 * c * v, mU, gm);
+        gnx = fmaf(w2 * v, fmaf(kU, wi[0], c * nU[0]), gnx);
+        gny = fmaf(w2 * v, fmaf(kU, wi[1], c * nU[1]), gny);
+        gnz = fmaf(w2 * v, fmaf(kU, wi[2], c * nU[2]), gnz);
+      }
+      dV[i * S + s] = dv;
+    }
+    gr = warp_sum(gr);
+    gm = warp_sum(gm);
+    gnx = warp_sum(gnx);
+    gny = warp_sum(gny);
+    gnz = warp_sum(gnz);
+    if (lane == 0) {
+      red[0][warp] = gr;
+      red[1][warp] = gm;
+      red[2][warp] = gnx;
+      red[3][warp] = gny;
+      red[4][warp] = gnz;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      float t = 0.f;
+      for (int w = 0; w < kGlossyThreads / 32; ++w) t += red[threadIdx.x][w];
+      if (threadIdx.x == 0) d_rough[i] = t;
+      else if (threadIdx.x == 1) d_metal[i] = t;
+      else d_normals[3 * i + threadIdx.x - 2] = t;
     }
     __syncthreads();
   }
@@ -1082,6 +1202,74 @@ int bounce_step(int64_t n, int C, int S, const float* dirs, const float* normals
                                                          status);
   PRTGS_CHECK_LAUNCH();
   return PRTGS_OK;
+}
+
+size_t glossy_backward_workspace(int64_t n, const prtgs_transfer_params* p) {
+  const int C = sh_count(p->sh_order);
+  return 2 * align_up(sizeof(int32_t) * n) + align_up(sizeof(uint32_t) * n) + scan_workspace(n) +
+         align_up(sizeof(uint32_t)) + (C > kMaxC ? align_up(sizeof(float) * (size_t)p->n_dirs * C) : 0);
+}
+
+static size_t glossy_bwd_smem(int S, int C) { return sizeof(float) * (3 * S + 2 * (size_t)S * C + (size_t)C * C); }
+
+bool glossy_backward_fits(int S, int order) {
+  return glossy_bwd_smem(S, sh_count(order)) <= (size_t)227 * 1024;
+}
+
+template <int C>
+static int launch_glossy_bwd(int64_t n_glossy, const int32_t* gids, int S, int order, const float* dirs,
+                             const float* ytab, const prtgs_gaussians* g, const float* V, const float* dM, float* dV,
+                             float* dr, float* dm, float* dn, cudaStream_t stream) {
+  const size_t sm = glossy_bwd_smem(S, C);
+  if (sm > (size_t)227 * 1024) return PRTGS_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_glossy_bwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_glossy_bwd<C>, kGlossyThreads, sm);
+  int64_t blocks = (int64_t)device_sms() * (per > 0 ? per : 1);
+  if (blocks > n_glossy) blocks = n_glossy;
+  k_glossy_bwd<C><<<(unsigned)blocks, kGlossyThreads, sm, counted(stream)>>>(n_glossy, gids, S, order, dirs, ytab,
+                                                                             g->normals, g->roughness, g->metallic, V,
+                                                                             dM, dV, dr, dm, dn);
+  PRTGS_CHECK_LAUNCH();
+  return PRTGS_OK;
+}
+
+int glossy_backward(const prtgs_gaussians* g, const prtgs_transfer_params* p, const float* V, const float* dM,
+                    int64_t n_glossy, float* dV, float* d_roughness, float* d_metallic, float* d_normals,
+                    int32_t* status, void* ws, cudaStream_t stream) {
+  const int64_t n = g->n;
+  const int S = p->n_dirs;
+  const int C = sh_count(p->sh_order);
+  cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)n * S, stream);
+  cudaMemsetAsync(d_roughness, 0, sizeof(float) * n, stream);
+  cudaMemsetAsync(d_metallic, 0, sizeof(float) * n, stream);
+  cudaMemsetAsync(d_normals, 0, sizeof(float) * 3 * n, stream);
+  if (n == 0 || n_glossy == 0) return PRTGS_OK;
+  Carver c(ws);
+  int32_t* slot = c.take<int32_t>(n);
+  int32_t* gids = c.take<int32_t>(n);
+  uint32_t* flags = c.take<uint32_t>(n);
+  void* sws = c.take<char>(scan_workspace(n));
+  uint32_t* total = c.take<uint32_t>(1);
+  float* ytab = C > kMaxC ? c.take<float>((size_t)S * C) : nullptr;
+  k_mask_u32<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, g->glossy_mask, flags);
+  int rc = scan_u32(flags, flags, n, false, total, sws, stream);
+  if (rc != PRTGS_OK) return rc;
+  k_glossy_slots<<<(unsigned)((n + 255) / 256), 256, 0, counted(stream)>>>(n, g->glossy_mask, flags, slot, gids);
+  if (ytab) {
+    rc = sh_table(S, p->sh_order, p->dirs, ytab, stream);
+    if (rc != PRTGS_OK) return rc;
+  }
+  PRTGS_CHECK_LAUNCH();
+  switch (C) {
+    case 4: return launch_glossy_bwd<4>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    case 9: return launch_glossy_bwd<9>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    case 16: return launch_glossy_bwd<16>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    case 25: return launch_glossy_bwd<25>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    case 36: return launch_glossy_bwd<36>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    case 49: return launch_glossy_bwd<49>(n_glossy, gids, S, p->sh_order, p->dirs, ytab, g, V, dM, dV, d_roughness, d_metallic, d_normals, stream);
+    default: return PRTGS_ERR_UNSUPPORTED;
+  }
 }
 
 int sh_table(int S, int order, const float* dirs, float* Y, cudaStream_t stream) {

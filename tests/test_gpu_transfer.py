@@ -561,3 +561,88 @@ def test_bounce_transfer_gradient_to_the_gaussians():
         nb = max(np.linalg.norm(r), 1e-3 * top)
         assert np.linalg.norm(gpu[f] - r) <= 2e-3 * nb, (f, np.linalg.norm(gpu[f] - r) / nb)
     assert np.linalg.norm(ref[5].numpy()) > 0 and np.linalg.norm(ref[3].numpy()) > 0
+
+
+# ---- backward of the glossy matrices (Eq. 40) ----------------------------------------------
+@pytest.mark.parametrize("order", [3, 5])
+def test_glossy_backward_matches_autograd(order):
+    """dM -> dV, d_roughness, d_metallic, d_normals against FP64 autograd of the glossy matrices on
+    the GPU's own visibility; non-glossy rows stay zero."""
+    from oracle import transfer_torch as TT
+
+    sc = S.surface_scene(900, 80 + order)
+    rng = np.random.default_rng(order)
+    sc.glossy_mask = (rng.random(sc.n) < 0.2).astype(np.uint8)
+    sc.roughness = rng.uniform(0.25, 0.9, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    dirs = S.direction_set(48, 9)
+    g = _gt(sc)
+    st = api.Status()
+    bvh = api.build_bvh(g, status=st)
+    d = torch.from_numpy(dirs).cuda()
+    V = api.precompute_visibility(g, bvh, d, order, status=st)["V"]
+    gids = np.nonzero(sc.glossy_mask)[0]
+    C = (order + 1) ** 2
+    dM = rng.standard_normal((gids.size, C, C)).astype(np.float32)
+    dV, dr, dm, dn = api.glossy_backward(g, d, order, V, torch.from_numpy(dM).cuda(), status=st)
+    torch.cuda.synchronize()
+    assert st.read() == 0
+    t = lambda a: torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+    Vg, ng, rg, mg = (t(V.cpu().numpy()[gids]), t(sc.normals[gids]), t(sc.roughness[gids]), t(sc.metallic[gids]))
+    M = TT.glossy_M(Vg, ng, rg, mg, dirs, oracle.sh(order, dirs))
+    ref = torch.autograd.grad((M * torch.as_tensor(dM.astype(np.float64))).sum(), (Vg, ng, rg, mg))
+    got = [x.cpu().numpy().astype(np.float64) for x in (dV, dn, dr, dm)]
+    other = np.ones(sc.n, bool)
+    other[gids] = False
+    for name, a, r, tol in zip(("dV", "d_normals", "d_roughness", "d_metallic"), got, ref, (2e-4, 2e-3, 5e-4, 2e-4)):
+        r = r.numpy()
+        assert np.all(a[other] == 0), name
+        a = a[gids]
+        assert np.linalg.norm(a - r) <= tol * np.linalg.norm(r), (name, np.linalg.norm(a - r) / np.linalg.norm(r))
+        assert np.linalg.norm(r) > 0, name
+
+
+def test_glossy_transfer_gradient_to_the_gaussians():
+    """L = sum(Wp * P) + sum(Wm * M): the geometry, normal, roughness and metallic gradients of
+    GlossyTransfer (glossy backward, then the transfer backward with its visibility gradient)
+    against FP64 autograd of the brute-force visibility chained into P and the glossy matrices."""
+    from oracle import transfer_torch as TT
+
+    sc = _crowded(220, 19)
+    rng = np.random.default_rng(19)
+    sc.glossy_mask = (rng.random(sc.n) < 0.3).astype(np.uint8)
+    sc.roughness = rng.uniform(0.3, 0.9, sc.n).astype(np.float32)
+    sc.metallic = rng.uniform(0.0, 1.0, sc.n).astype(np.float32)
+    dirs = S.direction_set(32, 5)
+    order = 2
+    C = (order + 1) ** 2
+    fields = ("means", "scales", "quats", "opacity", "normals", "roughness", "metallic")
+    gp = [torch.tensor(np.asarray(getattr(sc, f), np.float32), device="cuda", requires_grad=True) for f in fields]
+    mask = torch.from_numpy(sc.glossy_mask).cuda()
+    alb = torch.from_numpy(np.asarray(sc.albedo, np.float32)).cuda()
+    d = torch.from_numpy(dirs).cuda()
+    P, M = api.glossy_transfer(*gp, mask, alb, d, order, 0.0)
+    gids = np.nonzero(sc.glossy_mask)[0]
+    Wp = rng.standard_normal((sc.n, C))
+    Wm = rng.standard_normal((gids.size, C, C))
+    loss = (P * torch.as_tensor(Wp, dtype=torch.float32, device="cuda")).sum() + \
+        (M * torch.as_tensor(Wm, dtype=torch.float32, device="cuda")).sum()
+    loss.backward()
+    gpu = {f: p.grad.cpu().numpy().astype(np.float64) for f, p in zip(fields, gp)}
+    ps = [torch.tensor(np.asarray(getattr(sc, f), np.float64), requires_grad=True) for f in fields]
+    Y = oracle.sh(order, dirs)
+    V = TT.transfer_V(*ps[:5], dirs)
+    dd = torch.as_tensor(np.asarray(dirs, np.float64))
+    c = ps[4] @ dd.T
+    Pr = torch.where((c > 0).detach(), 4.0 * math.pi / len(dirs) * V * c, torch.zeros_like(c)) @ torch.as_tensor(Y)
+    gi = torch.as_tensor(gids)
+    Mr = TT.glossy_M(V[gi], ps[4][gi], ps[5][gi], ps[6][gi], dirs, Y)
+    np.testing.assert_allclose(M.detach().cpu().numpy(), Mr.detach().numpy(), rtol=0,
+                               atol=1e-4 * float(Mr.detach().abs().max()))
+    ref = torch.autograd.grad((Pr * torch.as_tensor(Wp)).sum() + (Mr * torch.as_tensor(Wm)).sum(), ps)
+    top = max(np.linalg.norm(r.numpy()) for r in ref)
+    for f, r in zip(fields, ref):
+        r = r.numpy()
+        nb = max(np.linalg.norm(r), 1e-3 * top)
+        assert np.linalg.norm(gpu[f] - r) <= 2e-3 * nb, (f, np.linalg.norm(gpu[f] - r) / nb)
+    assert all(np.linalg.norm(ref[k].numpy()) > 0 for k in (0, 3, 4, 5, 6))
