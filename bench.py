@@ -53,13 +53,15 @@ def parse():
                          "graph-captured step (measurement of batching); diff-300k: differentiable relight + "
                          "1080p render of 300k isotropic splats")
     ap.add_argument("--case", default=None, choices=["kernels-small", "sh-orders", "transfer-traffic", "training",
-                                                       "training-small"],
+                                                       "training-small", "transfer-backward"],
                     help="kernels-small: the small profiling case of the ncu captures; sh-orders: relight + "
                          "render and transfer times at SH orders 1-6; transfer-traffic: two transfer calls of "
                          "the workload for a DRAM-traffic capture; training: the training-stage calls (visibility "
                          "cache, view transfer and its backward, pseudo-normal, normal loss) on the 1M workload; "
                          "training-small: one view transfer forward and backward on 200k surface splats (S = 256, "
-                         "V of 205 MB, larger than L2) for an ncu capture; each instead of the bench")
+                         "V of 205 MB, larger than L2) for an ncu capture; transfer-backward: the backward of the "
+                         "one- and three-bounce transfer and of the glossy matrices of the 1M workload; each instead "
+                         "of the bench")
     return ap.parse_args()
 
 
@@ -641,6 +643,53 @@ def run_training_small():
                       "d_roughness_abs_sum": float(dr.abs().sum())}))
 
 
+def run_transfer_backward(args):
+    """The backward passes of the transfer's bounce and glossy parts on the tiled 1M workload (order
+    3, S = 256): dT of the one- and three-bounce T back to dP, albedo and receiver normals (index
+    matrix fixed; float atomics), and dM of the 300k glossy splats' matrices back to per-ray
+    visibility, roughness, metallic and normal gradients. CUDA events, median of ``--steps``, L2
+    flushed before each."""
+    import torch
+
+    from paper_2408_03538_gb300 import api, scenes as S
+
+    w, sc, dirs_np, *_ = workload_inputs(WORKLOAD)
+    order = w["order"]
+    g = api.GaussianTensors.from_scene(sc)
+    dirs = torch.from_numpy(dirs_np).cuda()
+    bvh = api.build_bvh(g)
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(1)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(max(3, args.steps)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    res = {"case": "transfer-backward", "workload": WORKLOAD, "n": sc.n, "n_dirs": int(dirs_np.shape[0])}
+    for nb in (1, 3):
+        out = api.precompute_transfer(g, bvh, dirs, order, bounce=True, n_bounces=nb)
+        dT = torch.randn(out["T"].shape, device="cuda", generator=gen)
+        ms = timed(lambda: api.bounce_backward(g, dirs, order, out["P"], out["idx"], dT, nb))
+        res[f"bounce_backward_{nb}"] = {"ms": ms, "index_entries": int((out["idx"] >= 0).sum())}
+    n_glossy = int(g.glossy_mask.sum().item())
+    V = api.precompute_visibility(g, bvh, dirs, order)["V"]
+    C = (order + 1) ** 2
+    dM = torch.randn((n_glossy, C, C), device="cuda", generator=gen)
+    ms = timed(lambda: api.glossy_backward(g, dirs, order, V, dM))
+    res["glossy_backward"] = {"ms": ms, "n_glossy": n_glossy,
+                              "brdf_pairs": n_glossy * int(dirs_np.shape[0]) ** 2}
+    print(json.dumps(res))
+
+
 def run_sh_orders():
     """Relight + 1920x1080 render of the 100k surface scene under one light at SH orders 1-6
     (the render-time-against-order measurement of the paper's Table 4), and the shadowed
@@ -1148,6 +1197,8 @@ def main():
         run_training(args)
     elif args.case == "training-small":
         run_training_small()
+    elif args.case == "transfer-backward":
+        run_transfer_backward(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched-32":
