@@ -9,13 +9,6 @@
 
 namespace prtgs {
 
-// a b - c d without cancellation (Kahan's difference of products with an FMA: the rounding
-// error of c d is recovered exactly and added back).
-__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
-  const float w = c * d;
-  const float e = fmaf(-c, d, w);
-  return fmaf(a, b, -w) + e;
-}
 
 // k(w_i, w_o) of Eq. 15 times pi for the unit normal n / |n|. ni, no: n . w_i, n . w_o (> 0).
 // The GGX denominator (n.h)^2 (a^2 - 1) + 1 is evaluated as (a^2 (n.v)^2 + |n x v|^2) / (|n|^2 |v|^2)

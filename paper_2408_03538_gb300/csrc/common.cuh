@@ -150,6 +150,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// a b - c d without cancellation (Kahan's difference of products with an FMA: the rounding
+// error of c d is recovered exactly and added back).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+  const float w = c * d;
+  const float e = fmaf(-c, d, w);
+  return fmaf(a, b, -w) + e;
+}
+
 // Neumaier-style compensated accumulator.
 struct CompSum {
   float s, c;

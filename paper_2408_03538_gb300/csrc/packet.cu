@@ -45,9 +45,8 @@ constexpr int kPacketDirs = 1;
 
 struct PacketSmem {
   int stack[kPStack];
-  float4 la[kPLeaves];     // leaf box lo xyz, sorted position
-  float4 lb[kPLeaves];     // leaf box hi xyz, unused
-  float4 stage[32][5];     // a group of leaves, staged: q0, q1, q2, (a22, A d), (1/|A d|^2, sqrt, m, pos)
+  int lpos[kPLeaves];      // the chunk's leaves (sorted positions)
+  float4 stage[32][4];     // a group of leaves, staged: the exact-test terms of stage_leaf
   // the work item's window of 64 receivers: record row 0 (mean, opacity), scene root, Gaussian
   // index; and, per direction, the window slots of the receivers that face it
   float4 wq0[64];
@@ -109,6 +108,123 @@ __device__ __forceinline__ Beam make_beam(bool need, float xl, float yl, float z
   return b;
 }
 
+// The exact ray / Gaussian test of a packet. Every ray of the packet has the direction w, so the
+// whitened closest-approach distance depends only on the ray origin's offset from the Gaussian in
+// the plane (e1, e2): with u = o - mu = dx e1 + dy e2 + uz w and the rows of A = diag(1/s) R^T,
+//   D^2 = |A u x A w|^2 / |A w|^2 = |dx (A e1 x a) + dy (A e2 x a)|^2,  a = A w / |A w|,
+//   t*  = -(u^T A^T A w) / |A w|^2 = -uz - dx m1 - dy m2,  m_k = (A e_k . A w) / |A w|^2
+// (the component of u along w drops out exactly). The per-Gaussian terms are formed once per
+// staged leaf; a lane then needs two additions, six FMAs for the vector and three for its norm.
+// Offsets are taken against a reference point R of the packet (one of its ray origins). A leaf's
+// R - mu is moved along w to p, the reference ray's point nearest to the Gaussian (D^2 does not
+// change along w; the move keeps the frame's own rounding, w.e1 of a few ulp, from mixing the
+// distance along w into dx and dy), and p and the lane's o - R are projected on e1, e2 in twice the
+// working precision (exact products and sums, hi + lo), so dx = (o - R).e1 + p.e1 carries about one
+// rounding of itself: the role that the error-free o - mu and the refinement at the closest point
+// play in the per-ray test.
+struct Rel {
+  float Rx, Ry, Rz;        // reference point (warp-uniform)
+  float xr, xr_lo, yr, yr_lo;  // this lane's origin minus R on e1, e2, each as an unevaluated sum hi + lo
+  float zr;                // ... and on w
+};
+
+// a . b of three terms as an unevaluated sum hi + lo (error-free products by FMA, error-free sums
+// by TwoSum, their errors gathered in lo): twice the working precision.
+__device__ __forceinline__ void dot3_pair(float ax, float ay, float az, float bx, float by, float bz, float& hi,
+                                          float& lo) {
+  const float p = ax * bx, ep = fmaf(ax, bx, -p);
+  const float q = ay * by, eq = fmaf(ay, by, -q);
+  const float r = az * bz, er = fmaf(az, bz, -r);
+  float s, t, s2, t2;
+  two_sum(p, q, s, t);
+  two_sum(s, r, s2, t2);
+  hi = s2;
+  lo = ((ep + eq) + er) + (t + t2);
+}
+
+// The lane's offset o - R from the reference point R on the frame, e1 and e2 parts as hi + lo.
+// The frame is orthonormal only to a few ulp: its e1.w and e2.w (taken in twice the working
+// precision) times the offset along w are taken off, so that dx e1 + dy e2 is the part of o - R
+// across w (up to a multiple of w, which D^2 does not see) and not a few ulp of the packet's depth
+// off it, which 1/s_min of a thin Gaussian would magnify.
+__device__ __forceinline__ Rel make_rel(const Frame& f, float ox0, float oy0, float oz0, float Rx, float Ry,
+                                        float Rz) {
+  Rel rel;
+  rel.Rx = Rx;
+  rel.Ry = Ry;
+  rel.Rz = Rz;
+  float ox, oy, oz, lox, loy, loz;
+  two_sum(ox0, -Rx, ox, lox);
+  two_sum(oy0, -Ry, oy, loy);
+  two_sum(oz0, -Rz, oz, loz);
+  dot3_pair(f.e1x, f.e1y, f.e1z, ox, oy, oz, rel.xr, rel.xr_lo);
+  dot3_pair(f.e2x, f.e2y, f.e2z, ox, oy, oz, rel.yr, rel.yr_lo);
+  rel.zr = fmaf(f.wx, ox, fmaf(f.wy, oy, f.wz * oz)) + fmaf(f.wx, lox, fmaf(f.wy, loy, f.wz * loz));
+  float d1, d1l, d2, d2l;
+  dot3_pair(f.e1x, f.e1y, f.e1z, f.wx, f.wy, f.wz, d1, d1l);
+  dot3_pair(f.e2x, f.e2y, f.e2z, f.wx, f.wy, f.wz, d2, d2l);
+  rel.xr_lo += fmaf(f.e1x, lox, fmaf(f.e1y, loy, f.e1z * loz)) - rel.zr * (d1 + d1l);
+  rel.yr_lo += fmaf(f.e2x, lox, fmaf(f.e2y, loy, f.e2z * loz)) - rel.zr * (d2 + d2l);
+  return rel;
+}
+
+// Stage one leaf for the packet: (p on e1, e2 (high parts), R - mu on w; opacity), (A e1 x a; m1),
+// (A e2 x a; m2), (facing term max(-w.n_j, 0); sorted position; p on e1, e2 (low parts)).
+__device__ __forceinline__ void stage_leaf(const float4* __restrict__ recs, int pos, const Frame& f, const Rel& rel,
+                                           float4* out) {
+  const float4 q0 = __ldg(recs + 4 * pos), q1 = __ldg(recs + 4 * pos + 1), q2 = __ldg(recs + 4 * pos + 2),
+               q3 = __ldg(recs + 4 * pos + 3);
+  // R - mu = h + l exactly; p = R - mu + t_ref w, the offset of mu from the point of the reference
+  // ray nearest to it, formed with one rounding per component (the product t_ref w is exact inside
+  // the FMA): D^2 does not change along w, so the lanes use p in place of R - mu, and its projections
+  // on e1, e2 are small numbers, unaffected by the frame's own rounding (w.e1 of a few ulp times the
+  // distance to the Gaussian); uz keeps the distance along w as w.p - t_ref.
+  float hx, lx, hy, ly, hz, lz;
+  two_sum(rel.Rx, -q0.x, hx, lx);
+  two_sum(rel.Ry, -q0.y, hy, ly);
+  two_sum(rel.Rz, -q0.z, hz, lz);
+  const float t_ref = -fmaf(f.wx, hx, fmaf(f.wy, hy, f.wz * hz));
+  // p = h + l + t_ref w per component as hi + lo: the product exactly (FMA), the sum by TwoSum
+  float px, pxl, py, pyl, pz, pzl;
+  {
+    const float ax = t_ref * f.wx, ay = t_ref * f.wy, az = t_ref * f.wz;
+    const float eax = fmaf(t_ref, f.wx, -ax), eay = fmaf(t_ref, f.wy, -ay), eaz = fmaf(t_ref, f.wz, -az);
+    float e;
+    two_sum(hx, ax, px, e);
+    pxl = e + eax + lx;
+    two_sum(hy, ay, py, e);
+    pyl = e + eay + ly;
+    two_sum(hz, az, pz, e);
+    pzl = e + eaz + lz;
+  }
+  float cx, cxl, cy, cyl;
+  dot3_pair(f.e1x, f.e1y, f.e1z, px, py, pz, cx, cxl);
+  dot3_pair(f.e2x, f.e2y, f.e2z, px, py, pz, cy, cyl);
+  cxl += fmaf(f.e1x, pxl, fmaf(f.e1y, pyl, f.e1z * pzl));
+  cyl += fmaf(f.e2x, pxl, fmaf(f.e2y, pyl, f.e2z * pzl));
+  const float cz = fmaf(f.wx, hx, fmaf(f.wy, hy, f.wz * hz)) + fmaf(f.wx, lx, fmaf(f.wy, ly, f.wz * lz));
+  // rows of A: (q1.x q1.y q1.z), (q1.w q2.x q2.y), (q2.z q2.w q3.x)
+  const float b1x = fmaf(q1.x, f.e1x, fmaf(q1.y, f.e1y, q1.z * f.e1z));
+  const float b1y = fmaf(q1.w, f.e1x, fmaf(q2.x, f.e1y, q2.y * f.e1z));
+  const float b1z = fmaf(q2.z, f.e1x, fmaf(q2.w, f.e1y, q3.x * f.e1z));
+  const float b2x = fmaf(q1.x, f.e2x, fmaf(q1.y, f.e2y, q1.z * f.e2z));
+  const float b2y = fmaf(q1.w, f.e2x, fmaf(q2.x, f.e2y, q2.y * f.e2z));
+  const float b2z = fmaf(q2.z, f.e2x, fmaf(q2.w, f.e2y, q3.x * f.e2z));
+  const float adx = fmaf(q1.x, f.wx, fmaf(q1.y, f.wy, q1.z * f.wz));
+  const float ady = fmaf(q1.w, f.wx, fmaf(q2.x, f.wy, q2.y * f.wz));
+  const float adz = fmaf(q2.z, f.wx, fmaf(q2.w, f.wy, q3.x * f.wz));
+  const float dd = fmaf(adx, adx, fmaf(ady, ady, adz * adz));
+  const float id = 1.0f / sqrtf(dd);
+  const float ax = adx * id, ay = ady * id, az = adz * id;
+  const float idd = 1.0f / dd;
+  out[0] = make_float4(cx, cy, cz, q0.w);
+  out[1] = make_float4(diff_prod(b1y, az, b1z, ay), diff_prod(b1z, ax, b1x, az), diff_prod(b1x, ay, b1y, ax),
+                       fmaf(b1x, adx, fmaf(b1y, ady, b1z * adz)) * idd);
+  out[2] = make_float4(diff_prod(b2y, az, b2z, ay), diff_prod(b2z, ax, b2x, az), diff_prod(b2x, ay, b2y, ax),
+                       fmaf(b2x, adx, fmaf(b2y, ady, b2z * adz)) * idd);
+  out[3] = make_float4(fmaxf(-fmaf(f.wx, q3.y, fmaf(f.wy, q3.z, f.wz * q3.w)), 0.0f), __int_as_float(pos), cxl, cyl);
+}
+
 // Projection of a box [lo, hi] on the frame: centre and half-width along e1, e2 and w, widened
 // by a margin above the FP32 error of these sums and of a ray's drift off its projected origin
 // (|w.e1| of a few ulp times the distance travelled). Any point of the box -- in particular the
@@ -134,15 +250,16 @@ __device__ __forceinline__ bool beam_meets(const Beam& b, const float4& A, const
 }
 
 // One packet walk. Lane state: `active` (this lane's ray takes part), its projected origin
-// (xl, yl) and depth zl, the lower bound t_lo of the hits it wants (0: all hits ahead) and its
-// visitor, whose t_hi() bounds the hits it still wants and stop() ends its ray. The leaves of a
-// chunk are staged 32 at a time (one record load and one set of direction terms per lane), then
-// each lane whose ray meets a leaf's box (the slab test of the per-ray walk) evaluates the hit and
-// hands it to vis.hit(), in chunk order.
+// (xl, yl) and depth zl (for the beam), its offset from the packet's reference point (rel, for the
+// exact test), the lower bound t_lo of the hits it wants (0: all hits ahead) and its visitor, whose
+// t_hi() bounds the hits it still wants and stop() ends its ray. The leaves of a chunk are staged
+// 32 at a time (one record load and the per-Gaussian terms of the exact test per lane), then every
+// lane tests its ray against each of them (the test of Rel above) and hands the hits to
+// vis.hit(), in chunk order.
 template <class Vis>
-__device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, int self, int root, bool active,
-                            float xl, float yl, float zl, float t_lo, Vis& vis, PacketSmem& sm, RayStats& st,
-                            unsigned& node_count) {
+__device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, const Rel& rel, int self, int root,
+                            bool active, float xl, float yl, float zl, float t_lo, Vis& vis, PacketSmem& sm,
+                            RayStats& st, unsigned& node_count) {
   const int lane = threadIdx.x & 31;
   const float prune_lo = t_lo > 0.f ? t_lo * (1.0f - 1e-5f) - 1e-6f : -FLT_MAX;
   const unsigned above = lane == 31 ? 0u : (0xffffffffu << (lane + 1));  // lanes > lane
@@ -175,16 +292,10 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, in
       int c0 = 0, c1 = 0;
       float4 A0, A1;
       float2 Z0, Z1;
-      float4 bx0, bx1;  // child boxes: lo xyz + hi x
-      float2 by0, by1;  //              hi y, hi z
       bool near0 = true;
       if (node >= 0) {
         float4 n0, n1, n2;
         load_node(a.nodes, node, n0, n1, n2, c0, c1);
-        bx0 = n0;
-        by0 = make_float2(n1.x, n1.y);
-        bx1 = make_float4(n1.z, n1.w, n2.x, n2.y);
-        by1 = make_float2(n2.z, n2.w);
         project_box(f, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, A0, Z0);
         project_box(f, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, A1, Z1);
         const bool h0 = beam_meets(bm, A0, Z0) && child_ok(c0, a.n, a.status);
@@ -208,65 +319,38 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, in
         sm.stack[pos] = push0 ? c0 : c1;
       }
       sp = min(sp + __popc(b1) + __popc(b2), kPStack);
-      // leaves: appended to the chunk (their boxes; each lane tests its own ray against them)
+      // leaves: appended to the chunk (every lane tests its own ray against them)
       const int nlf = (int)leaf0 + (int)leaf1;
       const unsigned l1 = __ballot_sync(0xffffffffu, nlf >= 1), l2 = __ballot_sync(0xffffffffu, nlf == 2);
       int lp = nl + __popc(l1 & below) + __popc(l2 & below);
-      if (leaf0) {
-        sm.la[lp] = make_float4(bx0.x, bx0.y, bx0.z, __int_as_float(~c0));
-        sm.lb[lp] = make_float4(bx0.w, by0.x, by0.y, 0.f);
-        ++lp;
-      }
-      if (leaf1) {
-        sm.la[lp] = make_float4(bx1.x, bx1.y, bx1.z, __int_as_float(~c1));
-        sm.lb[lp] = make_float4(bx1.w, by1.x, by1.y, 0.f);
-      }
+      if (leaf0) sm.lpos[lp++] = ~c0;
+      if (leaf1) sm.lpos[lp] = ~c1;
       nl += __popc(l1) + __popc(l2);
       __syncwarp();
     }
     if (nl > kPLeaves - 64 || (sp == 0 && nl > 0)) {
       for (int g = 0; g < nl; g += 32) {
-        // stage: lane j loads the record of leaf g + j and its direction terms
-        if (g + lane < nl) {
-          const int pos = __float_as_int(sm.la[g + lane].w);
-          const float4 q0 = __ldg(a.recs + 4 * pos), q1 = __ldg(a.recs + 4 * pos + 1),
-                       q2 = __ldg(a.recs + 4 * pos + 2), q3 = __ldg(a.recs + 4 * pos + 3);
-          const DirTerms dt = dir_terms(q1, q2, q3, f.wx, f.wy, f.wz);
-          sm.stage[lane][0] = q0;
-          sm.stage[lane][1] = q1;
-          sm.stage[lane][2] = q2;
-          sm.stage[lane][3] = make_float4(q3.x, dt.dax, dt.day, dt.daz);
-          sm.stage[lane][4] = make_float4(dt.rdd, dt.srdd, dt.m, __int_as_float(pos));
-        }
+        // stage: lane j forms the exact-test terms of leaf g + j
+        if (g + lane < nl) stage_leaf(a.recs, sm.lpos[g + lane], f, rel, sm.stage[lane]);
         __syncwarp();
         const int cnt = min(32, nl - g);
+        if (lane == 0) st.entries += cnt;
         for (int j = 0; j < cnt; ++j) {
-          const float4 lo = sm.la[g + j];
-          const float4 hi = sm.lb[g + j];
-          const int pos = __float_as_int(lo.w);
+          const float4 s0 = sm.stage[j][0], s1 = sm.stage[j][1], s2 = sm.stage[j][2], s3 = sm.stage[j][3];
+          const int pos = __float_as_int(s3.y);
+          if (!need || pos == self) continue;
+          ++st.leaves;
+          // the high parts cancel without rounding error of their own beyond eps |dx| (and
+          // exactly where they nearly cancel), the low parts carry the roundings of both
+          const float dx = (rel.xr + s0.x) + (rel.xr_lo + s3.z), dy = (rel.yr + s0.y) + (rel.yr_lo + s3.w);
+          const float wx = fmaf(dx, s1.x, dy * s2.x), wy = fmaf(dx, s1.y, dy * s2.y), wz = fmaf(dx, s1.z, dy * s2.z);
+          const float d2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+          const float t = -(rel.zr + s0.z) - fmaf(dx, s1.w, dy * s2.w);
           th = vis.t_hi();
-          float tn, tf;
-          const bool cover = need && pos != self && slab(r, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, tn, tf) &&
-                             tf >= prune_lo && tn <= th;
-          if (!__any_sync(0xffffffffu, cover)) continue;
-          if (lane == 0) ++st.entries;
-          if (cover) {
-            ++st.leaves;
-            const float4 q0 = sm.stage[j][0], q1 = sm.stage[j][1], q2 = sm.stage[j][2], q3 = sm.stage[j][3],
-                         q4 = sm.stage[j][4];
-            DirTerms dt;
-            dt.dax = q3.y;
-            dt.day = q3.z;
-            dt.daz = q3.w;
-            dt.rdd = q4.x;
-            dt.srdd = q4.y;
-            dt.m = q4.z;
-            float t, al;
-            if (hit_eval(q0, q1, q2, q3.x, dt, r, t, al)) {
-              ++st.hits;
-              vis.hit(pos, t, al, dt.m);
-              need = !vis.stop();
-            }
+          if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th) {
+            ++st.hits;
+            vis.hit(pos, t, s0.w * expf(-0.5f * d2), s3.x);
+            need = !vis.stop();
           }
         }
         __syncwarp();
@@ -491,13 +575,16 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
           const unsigned grp = __ballot_sync(0xffffffffu, up && root == groot) & todo;
           const bool mine = (grp >> lane) & 1u;
           if (lane == 0) ++walks;
+          // reference point of the group's exact tests: its leader's ray origin
+          const Rel rel = make_rel(f, q0.x, q0.y, q0.z, __shfl_sync(0xffffffffu, q0.x, leader),
+                                   __shfl_sync(0xffffffffu, q0.y, leader), __shfl_sync(0xffffffffu, q0.z, leader));
           if (!BOUNCE) {
             ShadowVis sv{a, r, self, rs, 1.0f};
-            packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
+            packet_walk(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
             if (mine) vis = sv.T;
           } else {
             BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f, 0.0f, 0.0f, INT32_MIN, true};
-            packet_walk(a, f, r, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
+            packet_walk(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
             if (mine) vis = bv.T;
             // index matrix (Sec. 4.4): argmax of W_j = alpha_j T_j m_j over the hits in key order,
             // T_j the prefix transmittance; candidates need T_j >= t_min and T_j <= filter_t.
@@ -523,7 +610,7 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
               SearchVis<kPacketRoundHits> sv{a,     r,      self, rs,      t_last, p_last, bv.t_hor, bv.tf,
                                              bv.pf, 0.0f,   hbuf,   lane, 0,     FLT_MAX, INT32_MAX};
               if (searching) ++rs.rounds;
-              packet_walk(a, f, r, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
+              packet_walk(a, f, r, rel, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
                           rs.search_nodes);
               if (searching) {
                 if (round == 0) lt = pre ? bv.lpre : sv.lbase;

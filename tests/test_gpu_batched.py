@@ -23,12 +23,25 @@ def test_batched_transfer_equals_per_scene():
     g = api.GaussianTensors.from_scene(merged)
     bvh = api.build_bvh(g, torch.from_numpy(offs).cuda())
     P = api.precompute_transfer(g, bvh, dirs, 3)["P"].cpu().numpy()
+    dh = dirs.cpu().numpy()
+    floor = 1e-3 * oracle.unoccluded_norm(3)
     for b, sc in enumerate(parts):
         if sc.n == 0:
             continue
         gb = api.GaussianTensors.from_scene(sc)
         Pb = api.precompute_transfer(gb, api.build_bvh(gb), dirs, 3)["P"].cpu().numpy()
-        np.testing.assert_allclose(P[offs[b]:offs[b + 1]], Pb, rtol=0, atol=1e-6)
+        # the packets of the two launches differ (other windows, other reference points), so a
+        # hit decision inside the oracle's rounding band may go either way: such receivers are
+        # flagged by the oracle and both results lie within its allowance; all others agree
+        Pm = P[offs[b]:offs[b + 1]]
+        differ = np.nonzero(np.abs(Pm - Pb).max(axis=1) > 1e-6)[0]
+        assert differ.size <= max(2, sc.n // 200)
+        if differ.size:
+            ref = oracle.transfer(sc, dh, 3, differ)
+            assert np.all((ref["flags"] & oracle.RF_AMBIG_HIT).any(axis=1))
+            lim = 1e-4 * np.maximum(np.linalg.norm(ref["P"], axis=1), floor) + ref["allow_P"]
+            for got in (Pm[differ], Pb[differ]):
+                assert np.all(np.linalg.norm(got - ref["P"], axis=1) <= lim)
     # and one scene against the oracle (sampled receivers)
     recv = np.arange(offs[3], offs[4], 37)
     ref = oracle.transfer(merged.subset(np.arange(offs[3], offs[4])), dirs.cpu().numpy(), 3, recv - offs[3])

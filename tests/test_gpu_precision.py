@@ -58,7 +58,7 @@ def test_error_of_each_output_against_fp64():
     ref = oracle.transfer(sc, dirs, order, np.arange(sc.n), bounce=True)
     floor = 1e-3 * oracle.unoccluded_norm(order)
     okP, eP = _within(P, ref["P"], ref["allow_P"], floor)
-    okT, eT = _within(T, ref["T"], ref["allow_T"].max(axis=1), floor)
+    okT, eT = _within(T, ref["T"], np.linalg.norm(ref["allow_T"], axis=1), floor)
     rep["P (transfer vector, norm-wise per splat)"] = _stats(eP)
     rep["T (with one bounce, norm-wise per splat)"] = _stats(eT)
     flagged = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) != 0

@@ -68,11 +68,23 @@ def test_visibility_cache_matches_oracle(walk):
 
 
 def test_visibility_walks_agree():
+    """The packet walk and the per-ray walk take their hit decisions in different FP32
+    arithmetic, so they agree to 2e-6 on every ray except those with a decision inside the
+    oracle's rounding band (flagged): there each walk is within the oracle's allowance."""
     sc = _brdf_scene(2000, 22)
     dirs = S.direction_set(96, 4)
-    V0 = _visibility(sc, dirs, 2, 0)[3]["V"]
-    V1 = _visibility(sc, dirs, 2, 1)[3]["V"]
-    torch.testing.assert_close(V0, V1, rtol=0, atol=2e-6)
+    V0 = _visibility(sc, dirs, 2, 0)[3]["V"].cpu().numpy().astype(np.float64)
+    V1 = _visibility(sc, dirs, 2, 1)[3]["V"].cpu().numpy().astype(np.float64)
+    differ = np.abs(V0 - V1) > 2e-6
+    assert differ.mean() < 2e-3
+    rows = np.nonzero(differ.any(axis=1))[0]
+    if rows.size:
+        ref = oracle.transfer(sc, dirs, 2, rows)
+        flagged = (ref["flags"] & oracle.RF_AMBIG_HIT) != 0
+        assert np.all(flagged[differ[rows]])
+        lim = ref["dV"] + api.DEFAULT_T_MIN + 2e-6
+        for V in (V0, V1):
+            assert np.all(np.abs(V[rows] - ref["V"]) <= lim)
 
 
 def _tt_check(sc, dirs, order, recv, cam_pos, V):
