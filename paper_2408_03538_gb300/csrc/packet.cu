@@ -335,22 +335,26 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, co
         __syncwarp();
         const int cnt = min(32, nl - g);
         if (lane == 0) st.entries += cnt;
+        // per leaf only the test itself; the bookkeeping (the receiver's own Gaussian, the
+        // visitor's bound, whether the lane still wants hits) waits for a passing test, which
+        // is rare (a few percent of the leaves), and the visitor's bound th changes only there
+        if (need) st.leaves += cnt;  // leaf tests of the lane (its own Gaussian included)
         for (int j = 0; j < cnt; ++j) {
           const float4 s0 = sm.stage[j][0], s1 = sm.stage[j][1], s2 = sm.stage[j][2], s3 = sm.stage[j][3];
-          const int pos = __float_as_int(s3.y);
-          if (!need || pos == self) continue;
-          ++st.leaves;
           // the high parts cancel without rounding error of their own beyond eps |dx| (and
           // exactly where they nearly cancel), the low parts carry the roundings of both
           const float dx = (rel.xr + s0.x) + (rel.xr_lo + s3.z), dy = (rel.yr + s0.y) + (rel.yr_lo + s3.w);
           const float wx = fmaf(dx, s1.x, dy * s2.x), wy = fmaf(dx, s1.y, dy * s2.y), wz = fmaf(dx, s1.z, dy * s2.z);
           const float d2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
           const float t = -(rel.zr + s0.z) - fmaf(dx, s1.w, dy * s2.w);
-          th = vis.t_hi();
-          if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th) {
-            ++st.hits;
-            vis.hit(pos, t, s0.w * expf(-0.5f * d2), s3.x);
-            need = !vis.stop();
+          if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th && need) {
+            const int pos = __float_as_int(s3.y);
+            if (pos != self) {
+              ++st.hits;
+              vis.hit(pos, t, s0.w * expf(-0.5f * d2), s3.x);
+              need = !vis.stop();
+              th = vis.t_hi();
+            }
           }
         }
         __syncwarp();
