@@ -322,6 +322,27 @@ int oracle_trace(int64_t n, const float* means, const float* scales, const float
             double dt = fabs(hl[q + 1].t - hl[q].t);
             if (dt <= BAND_ORDER_REL * (fabs(hl[q].t) + 1e-3)) amb_arg = 1;
           }
+          /* further on, a front-facing hit within that band of the hits just in front of it may
+           * be ordered before them: its prefix then lacks their factors (1 - alpha), and if it
+           * could outweigh the winner that way the argmax is open too */
+          double lTq = 0.0;
+          for (int q = 0; q < nh; ++q) {
+            if (hl[q].ambiguous == 2) continue;
+            if (q > best_pos + 1 && hl[q].alpha > 0) {
+              const OG* gq = &g[hl[q].j];
+              double m = -(d[0] * gq->n[0] + d[1] * gq->n[1] + d[2] * gq->n[2]);
+              if (m > 0) {
+                double gain = 0.0;
+                for (int p = q - 1; p >= 0; --p) {
+                  if (hl[p].ambiguous == 2) continue;
+                  if (hl[q].t - hl[p].t > BAND_ORDER_REL * (fabs(hl[p].t) + 1e-3)) break;
+                  gain -= log1p(-hl[p].alpha);
+                }
+                if (gain > 0 && log(hl[q].alpha) + lTq + gain + log(m) >= lwbest - BAND_W_REL) amb_arg = 1;
+              }
+            }
+            lTq += log1p(-hl[q].alpha);
+          }
         }
         if (amb_arg) ray_flags[rs] |= RF_AMBIG_ARGMAX;
         if (cand)

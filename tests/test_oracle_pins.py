@@ -280,6 +280,21 @@ def test_index_matrix_weight_closed_form(oracle_mod):
     assert oracle_mod.trace(sc, up, 2, [0], bounce=True)["idx"][0, 0] == -1
 
 
+def test_index_matrix_flags_a_reorder_past_the_winner(oracle_mod):
+    """Hits A (front-facing, opacity 0.3, the winner: W = 0.3), B and X (back-facing) and Y
+    (front-facing, opacity 0.9) up the z axis. In order, W_Y = 0.9 (0.7)(0.8)(0.5) = 0.252 < W_A;
+    placed in front of X it would be 0.9 (0.7)(0.8) = 0.504 > W_A. With Y a rounding step behind
+    X the argmax is open (flagged); with Y well behind X it is not."""
+    up = np.array([[0, 0, 1.0]], np.float32)
+    for zy, flagged in ((2.0 + 1e-6, True), (2.5, False)):
+        sc = _sc([[0, 0, 0], [0, 0, 1], [0, 0, 1.5], [0, 0, 2], [0, 0, zy]], [[0.05] * 3] + [[0.1] * 3] * 4,
+                 [0.5, 0.3, 0.2, 0.5, 0.9], [[0, 0, 1], [0, 0, -1], [0, 0, 1], [0, 0, 1], [0, 0, -1]])
+        tr = oracle_mod.trace(sc, up, 1, [0], bounce=True)
+        assert tr["idx"][0, 0] == 1
+        assert bool(tr["flags"][0, 0] & oracle_mod.RF_AMBIG_ARGMAX) == flagged
+        assert not tr["flags"][0, 0] & oracle_mod.RF_AMBIG_HIT
+
+
 def test_bounce_against_closed_form_disc(oracle_mod):
     """Wide facing disc above the receiver: every ray within its 3-sigma footprint records it."""
     a, b, c, h, sig = 1.0, 0.8, 0.05, 1.0, 0.5
