@@ -35,6 +35,14 @@ constexpr int kPacketRoundHits = PRTGS_PACKET_ROUND_HITS;  // hits per index-mat
 #define PRTGS_PACKET_MIN_BLOCKS 4  // the visibility-only kernel fits 4 blocks per SM without spills
 #endif
 constexpr int kPLeaves = PRTGS_PACKET_LEAVES;  // leaf chunk of a warp (> 64; 96 and 128 measured alike)
+#ifndef PRTGS_PACKET_UNROLL
+#define PRTGS_PACKET_UNROLL 0
+#endif
+#ifndef PRTGS_PACKET_BOUNCE_UNROLL
+#define PRTGS_PACKET_BOUNCE_UNROLL 8
+#endif
+constexpr int kPUnrollVis = PRTGS_PACKET_UNROLL;            // leaves tested together (0: one by one): visibility walk
+constexpr int kPUnrollBounce = PRTGS_PACKET_BOUNCE_UNROLL;  // ... bounce and index-search walks
 // wide pops (32 nodes) only while the stack keeps room for their pushes plus a full one-node-
 // at-a-time descent of the deepest possible tree (64 levels)
 constexpr int kPHeadroom = 64 + 64 + 4;
@@ -249,6 +257,28 @@ __device__ __forceinline__ bool beam_meets(const Beam& b, const float4& A, const
          Z.x <= b.zhi;
 }
 
+// The exact test of one staged leaf for the lane: D^2 and t* (see Rel). The high parts of dx
+// cancel without rounding error of their own beyond eps |dx| (exactly where they nearly cancel);
+// the low parts carry the roundings of both.
+__device__ __forceinline__ void leaf_test(const Rel& rel, const float4* e, float& d2, float& t) {
+  const float4 s0 = e[0], s1 = e[1], s2 = e[2], s3 = e[3];
+  const float dx = (rel.xr + s0.x) + (rel.xr_lo + s3.z), dy = (rel.yr + s0.y) + (rel.yr_lo + s3.w);
+  const float wx = fmaf(dx, s1.x, dy * s2.x), wy = fmaf(dx, s1.y, dy * s2.y), wz = fmaf(dx, s1.z, dy * s2.z);
+  d2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+  t = -(rel.zr + s0.z) - fmaf(dx, s1.w, dy * s2.w);
+}
+
+// Hand one passing leaf test over to the visitor (the receiver's own Gaussian excepted).
+template <class Vis>
+__device__ __forceinline__ bool hand_over(const float4* e, int self, float d2, float t, Vis& vis, RayStats& st) {
+  const float4 s3 = e[3];
+  const int pos = __float_as_int(s3.y);
+  if (pos == self) return false;
+  ++st.hits;
+  vis.hit(pos, t, e[0].w * expf(-0.5f * d2), s3.x);
+  return true;
+}
+
 // One packet walk. Lane state: `active` (this lane's ray takes part), its projected origin
 // (xl, yl) and depth zl (for the beam), its offset from the packet's reference point (rel, for the
 // exact test), the lower bound t_lo of the hits it wants (0: all hits ahead) and its visitor, whose
@@ -256,7 +286,7 @@ __device__ __forceinline__ bool beam_meets(const Beam& b, const float4& A, const
 // 32 at a time (one record load and the per-Gaussian terms of the exact test per lane), then every
 // lane tests its ray against each of them (the test of Rel above) and hands the hits to
 // vis.hit(), in chunk order.
-template <class Vis>
+template <int UNROLL, class Vis>
 __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, const Rel& rel, int self, int root,
                             bool active, float xl, float yl, float zl, float t_lo, Vis& vis, PacketSmem& sm,
                             RayStats& st, unsigned& node_count) {
@@ -336,24 +366,44 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, co
         const int cnt = min(32, nl - g);
         if (lane == 0) st.entries += cnt;
         // per leaf only the test itself; the bookkeeping (the receiver's own Gaussian, the
-        // visitor's bound, whether the lane still wants hits) waits for a passing test, which
-        // is rare (a few percent of the leaves), and the visitor's bound th changes only there
+        // visitor's bound th, whether the lane still wants hits) waits for a passing test, which
+        // is rare (a few percent of the leaves); th only falls, and changes only at a hand-over.
+        // UNROLL > 0 tests UNROLL leaves at a time (independent chains) and hands the passing
+        // ones over in order, each test taken again by the same arithmetic (bit-identical)
+        // against the current th: one copy of the visitor's code serves the whole block, which
+        // pays where that code is long (the bounce and index-search visitors).
         if (need) st.leaves += cnt;  // leaf tests of the lane (its own Gaussian included)
-        for (int j = 0; j < cnt; ++j) {
-          const float4 s0 = sm.stage[j][0], s1 = sm.stage[j][1], s2 = sm.stage[j][2], s3 = sm.stage[j][3];
-          // the high parts cancel without rounding error of their own beyond eps |dx| (and
-          // exactly where they nearly cancel), the low parts carry the roundings of both
-          const float dx = (rel.xr + s0.x) + (rel.xr_lo + s3.z), dy = (rel.yr + s0.y) + (rel.yr_lo + s3.w);
-          const float wx = fmaf(dx, s1.x, dy * s2.x), wy = fmaf(dx, s1.y, dy * s2.y), wz = fmaf(dx, s1.z, dy * s2.z);
-          const float d2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-          const float t = -(rel.zr + s0.z) - fmaf(dx, s1.w, dy * s2.w);
-          if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th && need) {
-            const int pos = __float_as_int(s3.y);
-            if (pos != self) {
-              ++st.hits;
-              vis.hit(pos, t, s0.w * expf(-0.5f * d2), s3.x);
-              need = !vis.stop();
-              th = vis.t_hi();
+        if constexpr (UNROLL == 0) {
+          for (int j = 0; j < cnt; ++j) {
+            float d2, t;
+            leaf_test(rel, sm.stage[j], d2, t);
+            if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th && need) {
+              if (hand_over(sm.stage[j], self, d2, t, vis, st)) {
+                need = !vis.stop();
+                th = vis.t_hi();
+              }
+            }
+          }
+        } else {
+          for (int j0 = 0; j0 < cnt; j0 += UNROLL) {
+            unsigned pass = 0u;
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) {
+              float d2, t;
+              leaf_test(rel, sm.stage[min(j0 + k, 31)], d2, t);  // past cnt: a stale entry, masked below
+              if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th) pass |= 1u << k;
+            }
+            if (!need) pass = 0u;
+            if (cnt - j0 < UNROLL) pass &= (1u << (cnt - j0)) - 1u;
+            while (pass) {
+              const int j = j0 + __ffs(pass) - 1;
+              pass &= pass - 1u;
+              float d2, t;
+              leaf_test(rel, sm.stage[j], d2, t);
+              if (need && t <= th && hand_over(sm.stage[j], self, d2, t, vis, st)) {
+                need = !vis.stop();
+                th = vis.t_hi();
+              }
             }
           }
         }
@@ -584,11 +634,11 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
                                    __shfl_sync(0xffffffffu, q0.y, leader), __shfl_sync(0xffffffffu, q0.z, leader));
           if (!BOUNCE) {
             ShadowVis sv{a, r, self, rs, 1.0f};
-            packet_walk(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
+            packet_walk<kPUnrollVis>(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
             if (mine) vis = sv.T;
           } else {
             BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f, 0.0f, 0.0f, INT32_MIN, true};
-            packet_walk(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
+            packet_walk<kPUnrollBounce>(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
             if (mine) vis = bv.T;
             // index matrix (Sec. 4.4): argmax of W_j = alpha_j T_j m_j over the hits in key order,
             // T_j the prefix transmittance; candidates need T_j >= t_min and T_j <= filter_t.
@@ -614,7 +664,7 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
               SearchVis<kPacketRoundHits> sv{a,     r,      self, rs,      t_last, p_last, bv.t_hor, bv.tf,
                                              bv.pf, 0.0f,   hbuf,   lane, 0,     FLT_MAX, INT32_MAX};
               if (searching) ++rs.rounds;
-              packet_walk(a, f, r, rel, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
+              packet_walk<kPUnrollBounce>(a, f, r, rel, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
                           rs.search_nodes);
               if (searching) {
                 if (round == 0) lt = pre ? bv.lpre : sv.lbase;

@@ -89,12 +89,13 @@ def test_bvh_bit_exact(sizes):
             assert rr == r
 
 
-def _transfer_gpu(scene, dirs, order, bounce=False, glossy=False, t_min=api.DEFAULT_T_MIN):
+def _transfer_gpu(scene, dirs, order, bounce=False, glossy=False, t_min=api.DEFAULT_T_MIN, walk=0):
     g = _gt(scene)
     st = api.Status()
     bvh = api.build_bvh(g, status=st)
     d = torch.from_numpy(dirs).cuda()
-    out = api.precompute_transfer(g, bvh, d, order, bounce=bounce, glossy=glossy, t_min=t_min, status=st)
+    out = api.precompute_transfer(g, bvh, d, order, bounce=bounce, glossy=glossy, t_min=t_min, status=st,
+                                  walk=walk)
     torch.cuda.synchronize()
     assert st.read() == 0
     return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
@@ -380,6 +381,27 @@ def test_tiled_1m_glossy_full_size_sampled():
     assert np.all(np.isfinite(out["M"])) and np.all(np.isfinite(out["T"]))
 
 
+def test_walks_differ_only_inside_rounding_bands_full_size():
+    """The packet walk (a planar test per packet) and the per-ray walk take their hit decisions
+    in different FP32 arithmetic. At full size (1M Gaussians, S = 256, shadow + bounce) they
+    agree on almost every ray; on the receivers where they differ most, both lie within the
+    oracle's allowance and match its index matrix on every unflagged ray."""
+    sc = S.make_scene("tiled-1m-glossy")
+    dirs = S.direction_set(256, S.config_seed(2))
+    o0 = _transfer_gpu(sc, dirs, 3, bounce=True, walk=0)
+    o1 = _transfer_gpu(sc, dirs, 3, bounce=True, walk=1)
+    dP = np.linalg.norm(o0["P"] - o1["P"], axis=1)
+    didx = (o0["idx"] != o1["idx"]).sum(axis=1)
+    assert np.mean(o0["idx"] != o1["idx"]) < 1e-3
+    worst = np.unique(np.concatenate([np.argsort(dP)[-6:], np.argsort(didx)[-6:]]))
+    ref = oracle.transfer(sc, dirs, 3, worst, bounce=True, bounce_T=False)
+    floor = 1e-3 * oracle.unoccluded_norm(3)
+    clean = (ref["flags"] & (oracle.RF_AMBIG_HIT | oracle.RF_AMBIG_ARGMAX)) == 0
+    for o in (o0, o1):
+        _check_norm(o["P"][worst], ref["P"], ref["allow_P"], floor)
+        np.testing.assert_array_equal(o["idx"][worst][clean], ref["idx"][clean])
+
+
 # ---- n-bounce self-transfer (Eq. 34-35) -----------------------------------------------------
 @pytest.mark.parametrize("nb", [2, 3, 5])
 def test_multi_bounce_matches_oracle(nb):
@@ -396,7 +418,7 @@ def test_multi_bounce_matches_oracle(nb):
     assert st.read() == 0
     tr = oracle.transfer(sc, dirs, 2, np.arange(sc.n), bounce=True)
     Tref, allow = oracle.multi_bounce(sc, dirs, 2, tr, nb)
-    _check_norm(T, Tref, allow.max(axis=1), 1e-3 * oracle.unoccluded_norm(2))
+    _check_norm(T, Tref, np.linalg.norm(allow, axis=1), 1e-3 * oracle.unoccluded_norm(2))
     # the later bounces matter here: the n-bounce T differs from the one-bounce T
     assert np.linalg.norm(Tref - tr["T"]) > 1e-3 * np.linalg.norm(tr["T"])
 
