@@ -437,8 +437,9 @@ struct BounceVis {
   float T;
   float t_seen;
   float t_hor;
-  float tf;  // nearest front-facing hit: t*, position
+  float tf;  // nearest front-facing hit: t*, position, alpha, facing term
   int pf;
+  float af, mf;
   float amax;  // largest alpha m of the front-facing hits multiplied into T
   float lpre;  // sum of log(1 - alpha) of the hits with key below (tf, pf)
   float ts;    // largest key summed into lpre: t*, position
@@ -459,6 +460,8 @@ struct BounceVis {
       if (ps != INT32_MIN && !key_less(ts, ps, t, pos)) pre_ok = false;  // a summed hit lies behind it
       tf = t;
       pf = pos;
+      af = al;
+      mf = m;
     } else if (key_less(t, pos, tf, pf)) {
       lpre += log1pf(-al);
       if (ps == INT32_MIN || key_less(ts, ps, t, pos)) {
@@ -637,7 +640,8 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
             packet_walk<kPUnrollVis>(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, sv, sm, rs, rs.nodes);
             if (mine) vis = sv.T;
           } else {
-            BounceVis bv{a, r, self, rs, 1.0f, 0.0f, FLT_MAX, FLT_MAX, INT32_MAX, 0.0f, 0.0f, 0.0f, INT32_MIN, true};
+            BounceVis bv{a,    r,    self, rs,   1.0f, 0.0f,      FLT_MAX, FLT_MAX,
+                         INT32_MAX, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, INT32_MIN, true};
             packet_walk<kPUnrollBounce>(a, f, r, rel, self, groot, mine, xl, yl, zl, 0.0f, bv, sm, rs, rs.nodes);
             if (mine) vis = bv.T;
             // index matrix (Sec. 4.4): argmax of W_j = alpha_j T_j m_j over the hits in key order,
@@ -650,11 +654,27 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
             bool searching = mine && bv.tf != FLT_MAX;
             float t_last = -FLT_MAX, lt = 0.0f, lw_best = -FLT_MAX;
             int p_last = INT32_MIN;
-            // with an exact prefix of the first candidate, the first round starts at the candidate
+            // with an exact prefix of the first candidate, the candidate is taken here, as the
+            // rounds would take it (same arithmetic), and the rounds start behind it, if they are
+            // still needed: often its weight already settles the argmax
             const bool pre = bv.pre_ok && bv.pf > INT32_MIN;
-            if (pre) {
-              t_last = bv.tf;
-              p_last = bv.pf - 1;
+            if (pre && searching) {
+              lt = bv.lpre;
+              if (lt < lmin) {
+                searching = false;
+              } else {
+                if (lt <= lfilter) {
+                  const float lw = logf(bv.af * bv.mf) + lt;
+                  if (lw > lw_best) {
+                    lw_best = lw;
+                    best = bv.pf;
+                  }
+                }
+                lt += log1pf(-bv.af);
+                if (lt < lmin || lt + lamax <= lw_best) searching = false;
+                t_last = bv.tf;
+                p_last = bv.pf;
+              }
             }
             for (int64_t round = 0; __any_sync(0xffffffffu, searching); ++round) {
               if (round > a.n / kPacketRoundHits + 1) {
@@ -667,7 +687,7 @@ __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_M
               packet_walk<kPUnrollBounce>(a, f, r, rel, self, groot, searching, xl, yl, zl, t_last > 0.f ? t_last : 0.0f, sv, sm, rs,
                           rs.search_nodes);
               if (searching) {
-                if (round == 0) lt = pre ? bv.lpre : sv.lbase;
+                if (round == 0 && !pre) lt = sv.lbase;
                 const int nh = sv.count;
                 bool decided = false;
                 for (int k = 0; k < nh && !decided; ++k) {
