@@ -25,16 +25,18 @@ constexpr int kPacketWarps = 4;
 constexpr int kPacketThreads = 32 * kPacketWarps;
 constexpr int kPStack = 384;     // node stack of a warp (ints)
 #ifndef PRTGS_PACKET_ROUND_HITS
-#define PRTGS_PACKET_ROUND_HITS 16
+#define PRTGS_PACKET_ROUND_HITS 14  // 14 keeps the bounce kernel at 4 blocks per SM (16: 3 blocks)
 #endif
 constexpr int kPacketRoundHits = PRTGS_PACKET_ROUND_HITS;  // hits per index-matrix search round
 #ifndef PRTGS_PACKET_LEAVES
-#define PRTGS_PACKET_LEAVES 96
+#define PRTGS_PACKET_LEAVES 160
 #endif
 #ifndef PRTGS_PACKET_MIN_BLOCKS
 #define PRTGS_PACKET_MIN_BLOCKS 4  // the visibility-only kernel fits 4 blocks per SM without spills
 #endif
-constexpr int kPLeaves = PRTGS_PACKET_LEAVES;  // leaf chunk of a warp (> 64; 96 and 128 measured alike)
+// leaf chunk of a warp (> 64: a step appends up to 64 leaves; flushed past kPLeaves - 64). Longer
+// chunks flush less often: 1M bounce transfer 1.085 s at 96, 0.988 s at 128, 0.973 s at 160
+constexpr int kPLeaves = PRTGS_PACKET_LEAVES;
 #ifndef PRTGS_PACKET_UNROLL
 #define PRTGS_PACKET_UNROLL 0
 #endif
@@ -292,6 +294,8 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, co
                             RayStats& st, unsigned& node_count) {
   const int lane = threadIdx.x & 31;
   const float prune_lo = t_lo > 0.f ? t_lo * (1.0f - 1e-5f) - 1e-6f : -FLT_MAX;
+  // t > 0 && t >= prune_lo as one strict test against the float below prune_lo (or 0)
+  const float tlo = prune_lo > 0.f ? nextafterf(prune_lo, 0.0f) : 0.0f;
   const unsigned above = lane == 31 ? 0u : (0xffffffffu << (lane + 1));  // lanes > lane
   const unsigned below = (1u << lane) - 1u;                                // lanes < lane
   const float zlo_l = t_lo > 0.f ? zl + (t_lo * (1.0f - 1e-5f) - 1e-6f) : zl;
@@ -373,14 +377,16 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, co
         // against the current th: one copy of the visitor's code serves the whole block, which
         // pays where that code is long (the bounce and index-search visitors).
         if (need) st.leaves += cnt;  // leaf tests of the lane (its own Gaussian included)
+        float thn = need ? th : -FLT_MAX;  // a lane that wants no hits passes no test
         if constexpr (UNROLL == 0) {
           for (int j = 0; j < cnt; ++j) {
             float d2, t;
             leaf_test(rel, sm.stage[j], d2, t);
-            if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th && need) {
+            if (d2 <= 9.0f && t > tlo && t <= thn) {
               if (hand_over(sm.stage[j], self, d2, t, vis, st)) {
                 need = !vis.stop();
                 th = vis.t_hi();
+                thn = need ? th : -FLT_MAX;
               }
             }
           }
@@ -391,18 +397,18 @@ __device__ void packet_walk(const TraceArgs& a, const Frame& f, const Ray& r, co
             for (int k = 0; k < UNROLL; ++k) {
               float d2, t;
               leaf_test(rel, sm.stage[min(j0 + k, 31)], d2, t);  // past cnt: a stale entry, masked below
-              if (d2 <= 9.0f && t > 0.0f && t >= prune_lo && t <= th) pass |= 1u << k;
+              if (d2 <= 9.0f && t > tlo && t <= thn) pass |= 1u << k;
             }
-            if (!need) pass = 0u;
             if (cnt - j0 < UNROLL) pass &= (1u << (cnt - j0)) - 1u;
             while (pass) {
               const int j = j0 + __ffs(pass) - 1;
               pass &= pass - 1u;
               float d2, t;
               leaf_test(rel, sm.stage[j], d2, t);
-              if (need && t <= th && hand_over(sm.stage[j], self, d2, t, vis, st)) {
+              if (t <= thn && hand_over(sm.stage[j], self, d2, t, vis, st)) {
                 need = !vis.stop();
                 th = vis.t_hi();
+                thn = need ? th : -FLT_MAX;
               }
             }
           }
@@ -540,7 +546,7 @@ struct SearchVis {
 // Visibility (and with BOUNCE the index matrix) of the rays of receiver batch [r0, r1):
 // V[s * batch + (i - r0)] (0 where n.w <= 0), idx[gid * S + s].
 #ifndef PRTGS_PACKET_BOUNCE_MIN_BLOCKS
-#define PRTGS_PACKET_BOUNCE_MIN_BLOCKS 3
+#define PRTGS_PACKET_BOUNCE_MIN_BLOCKS 4  // 128 registers, no spills; 54.5 KB shared per block at S = 256
 #endif
 template <bool BOUNCE>
 __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_MIN_BLOCKS : PRTGS_PACKET_MIN_BLOCKS)
