@@ -146,8 +146,8 @@ int prtgs_build_bvh(const prtgs_gaussians* g, prtgs_bvh* bvh, int32_t* status, v
  * Transfer precompute parameters (Sec. 4.4-4.5).
  *   sh_order        1..6 (C = (order+1)^2 coefficients; for 4..6 the SH of the direction set
  *                   are tabulated per call). With PRTGS_GLOSSY the block of the glossy matrices
- *                   holds 3 S + 3 S C floats of shared memory: S x C above 227 KB of it (e.g.
- *                   S > 384 at order 6) -> PRTGS_ERR_UNSUPPORTED
+ *                   holds 3 S + 3 S C floats and 2 S ints of shared memory: above 227 KB of
+ *                   it (e.g. S > 382 at order 6) -> PRTGS_ERR_UNSUPPORTED
  *   n_dirs, dirs    S shared world-space directions [S,3] (device); weight 4 pi / S each
  *   t_min           a ray stops once its transmittance falls below t_min (bounded error
  *                   t_min per ray); 0 disables early exit. Suggested 2^-30.

@@ -743,7 +743,37 @@ __global__ void k_bounce(int64_t n, int C, int S, const float* __restrict__ dirs
 constexpr int kGlossyThreads = 128;
 
 
+// Ordered compaction of the directions s in [0, S) with pred(s) into list (increasing s), one
+// block of kGlossyThreads threads; returns the count (every thread). wt: kGlossyThreads / 32 ints.
+template <class Pred>
+__device__ __forceinline__ int glossy_compact(int S, Pred pred, int* list, int* wt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kW = kGlossyThreads / 32;
+  int count = 0;
+  for (int s0 = 0; s0 < S; s0 += kGlossyThreads) {
+    const int s = s0 + (int)threadIdx.x;
+    const bool p = s < S && pred(s);
+    const unsigned b = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) wt[warp] = __popc(b);
+    __syncthreads();
+    int off = count, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      off += w < warp ? wt[w] : 0;
+      tot += wt[w];
+    }
+    if (p) list[off + __popc(b & ((1u << lane) - 1u))] = s;
+    count += tot;
+    __syncthreads();
+  }
+  return count;
+}
+
 // C coefficients (orders 1-6); for C > 16 the SH of the direction set come from the table Ytab.
+// Per splat the directions with n.w > 0 (the kernel's outgoing side) and, among them, those with
+// V > 0 (the incoming side) are first compacted in increasing order, so that every thread of the
+// inner loops works on a live term; the sums run over the live terms in the order of the full
+// sums, whose other terms are exact zeros.
 template <int C>
 __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, const int32_t* __restrict__ glossy_ids,
                                                            int S, int order, const float* __restrict__ dirs,
@@ -755,8 +785,11 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, con
   extern __shared__ float smem[];
   float* sdir = smem;              // [S*3]
   float* sY = sdir + 3 * S;        // [S][C]
-  float* sU = sY + S * C;          // [S][C]   w^2 (n.w_s)^+ V_s Y(w_s)
-  float* sB = sU + S * C;          // [S][C]   sum_o k(s,o) Y(w_o)
+  float* sU = sY + S * C;          // [live][C]   w^2 (n.w_s)^+ V_s Y(w_s)
+  float* sB = sU + S * C;          // [live][C]   sum_o k(s,o) Y(w_o)
+  int* sin_list = reinterpret_cast<int*>(sB + S * C);  // [S] incoming live directions
+  int* sout_list = sin_list + S;                       // [S] outgoing directions (n.w_o > 0)
+  int* wt = sout_list + S;                             // [kGlossyThreads / 32] compaction counts
   for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sdir[i] = dirs[i];
   __syncthreads();
   if (C > kMaxC) {
@@ -775,36 +808,41 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy(int64_t n_glossy, con
     const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
     const float r = roughness[i];
     const float alpha = r * r, metal = metallic[i];
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    auto cosn = [&](int s) {
+      const float* w = sdir + 3 * s;
+      return fmaf(nx, w[0], fmaf(ny, w[1], nz * w[2]));
+    };
+    const int n_out = glossy_compact(S, [&](int s) { return cosn(s) > 0.0f; }, sout_list, wt);
+    const int n_in =
+        glossy_compact(S, [&](int s) { return cosn(s) > 0.0f && Vg[g * S + s] > 0.0f; }, sin_list, wt);
+    for (int l = threadIdx.x; l < n_in; l += blockDim.x) {
+      const int s = sin_list[l];
       const float* wi = sdir + 3 * s;
-      float ni = fmaf(nx, wi[0], fmaf(ny, wi[1], nz * wi[2]));
-      float v = Vg[g * S + s];
+      const float ni = cosn(s);
+      const float v = Vg[g * S + s];
+      const float u = wq * wq * ni * v;
       float Bs[C];
 #pragma unroll
       for (int k = 0; k < C; ++k) Bs[k] = 0.f;
-      float u = 0.f;
-      if (ni > 0.0f && v > 0.0f) {
-        u = wq * wq * ni * v;
-        for (int o = 0; o < S; ++o) {
-          const float* wo = sdir + 3 * o;
-          float no = fmaf(nx, wo[0], fmaf(ny, wo[1], nz * wo[2]));
-          if (!(no > 0.0f)) continue;
-          float kv = brdf_kernel(nx, ny, nz, wi, wo, ni, no, alpha, metal);
+      for (int q = 0; q < n_out; ++q) {
+        const int o = sout_list[q];
+        const float* wo = sdir + 3 * o;
+        const float no = cosn(o);
+        const float kv = brdf_kernel(nx, ny, nz, wi, wo, ni, no, alpha, metal);
 #pragma unroll
-          for (int k = 0; k < C; ++k) Bs[k] = fmaf(kv, sY[o * C + k], Bs[k]);
-        }
+        for (int k = 0; k < C; ++k) Bs[k] = fmaf(kv, sY[o * C + k], Bs[k]);
       }
 #pragma unroll
       for (int k = 0; k < C; ++k) {
-        sB[s * C + k] = Bs[k];
-        sU[s * C + k] = u * sY[s * C + k];
+        sB[l * C + k] = Bs[k];
+        sU[l * C + k] = u * sY[s * C + k];
       }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
       int ra = e / C, cb = e % C;
       float acc = 0.f;
-      for (int s = 0; s < S; ++s) acc = fmaf(sU[s * C + ra], sB[s * C + cb], acc);
+      for (int l = 0; l < n_in; ++l) acc = fmaf(sU[l * C + ra], sB[l * C + cb], acc);
       M[(g * C + ra) * C + cb] = acc;
     }
     __syncthreads();
@@ -949,9 +987,11 @@ __global__ void k_mask_u32(int64_t n, const uint8_t* __restrict__ mask, uint32_t
 }
 
 static size_t trace_smem(int S) { return sizeof(float) * 3 * S + kTraceWarps * S * (sizeof(float) + 2); }
-static size_t glossy_smem(int S, int C) { return sizeof(float) * (3 * S + 3 * (size_t)S * C); }
+static size_t glossy_smem(int S, int C) {
+  return sizeof(float) * (3 * S + 3 * (size_t)S * C) + sizeof(int) * (2 * (size_t)S + kGlossyThreads / 32);
+}
 
-// The glossy matrices' shared memory (directions and three [S][C] tables) must fit one block.
+// The glossy matrices' shared memory (directions, three [S][C] tables, two direction lists) must fit one block.
 bool glossy_fits(int S, int order) { return glossy_smem(S, sh_count(order)) <= (size_t)227 * 1024; }
 
 template <int C>

@@ -78,6 +78,10 @@ def test_host_side_validation_without_gpu():
     p5 = L.TransferParams(6, 1024, fake, 0.0, 1.0, L.SHADOW | L.GLOSSY, 0)
     assert lib.prtgs_precompute_transfer(ctypes.byref(g2), ctypes.byref(bvh), ctypes.byref(p5), fake, fake, fake, None,
                                          0, None, None, 0, None) == L.ERR_UNSUPPORTED
+    # ... and at the boundary: order 6 takes 608 B per direction, so S = 383 no longer fits
+    p6 = L.TransferParams(6, 383, fake, 0.0, 1.0, L.SHADOW | L.GLOSSY, 0)
+    assert lib.prtgs_precompute_transfer(ctypes.byref(g2), ctypes.byref(bvh), ctypes.byref(p6), fake, fake, fake, None,
+                                         0, None, None, 0, None) == L.ERR_UNSUPPORTED
     # too many directions
     p2 = L.TransferParams(2, 5000, fake, 0.0, 1.0, L.SHADOW, 0)
     assert lib.prtgs_precompute_transfer(ctypes.byref(g2), ctypes.byref(bvh), ctypes.byref(p2), fake, None, None, None,
