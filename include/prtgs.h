@@ -250,7 +250,7 @@ int prtgs_precompute_transfer_backward(const prtgs_gaussians* g, const prtgs_bvh
  * the derivatives of sum_s sum_o w^2 (n.w_s)^+ V_s k(s,o) U_so. The cut-offs n.w > 0 are held
  * fixed. V[n,S] is the visibility of prtgs_precompute_visibility (same walk as the forward).
  * Outputs are overwritten (deterministic). Workspace: prtgs_glossy_backward_workspace_size;
- * PRTGS_ERR_UNSUPPORTED when the block's shared memory (3S + 2SC + C^2 floats) exceeds 227 KB.
+ * PRTGS_ERR_UNSUPPORTED when the block's shared memory (3S + 2SC + C^2 floats, 2S ints) exceeds 227 KB.
  */
 size_t prtgs_glossy_backward_workspace_size(int64_t n, const prtgs_transfer_params* p);
 int prtgs_glossy_backward(const prtgs_gaussians* g, const prtgs_transfer_params* p, const float* V, const float* dM,

@@ -29,13 +29,14 @@ constexpr int kPStack = 384;     // node stack of a warp (ints)
 #endif
 constexpr int kPacketRoundHits = PRTGS_PACKET_ROUND_HITS;  // hits per index-matrix search round
 #ifndef PRTGS_PACKET_LEAVES
-#define PRTGS_PACKET_LEAVES 160
+#define PRTGS_PACKET_LEAVES 224
 #endif
 #ifndef PRTGS_PACKET_MIN_BLOCKS
 #define PRTGS_PACKET_MIN_BLOCKS 4  // the visibility-only kernel fits 4 blocks per SM without spills
 #endif
 // leaf chunk of a warp (> 64: a step appends up to 64 leaves; flushed past kPLeaves - 64). Longer
-// chunks flush less often: 1M bounce transfer 1.085 s at 96, 0.988 s at 128, 0.973 s at 160
+// chunks flush less often: 1M bounce transfer 1.085 s at 96, 0.988 s at 128, 0.970 s at 160,
+// 0.962 s at 192, 0.957 s at 224 (4 blocks per SM still fit at S = 256)
 constexpr int kPLeaves = PRTGS_PACKET_LEAVES;
 #ifndef PRTGS_PACKET_UNROLL
 #define PRTGS_PACKET_UNROLL 0
@@ -546,7 +547,7 @@ struct SearchVis {
 // Visibility (and with BOUNCE the index matrix) of the rays of receiver batch [r0, r1):
 // V[s * batch + (i - r0)] (0 where n.w <= 0), idx[gid * S + s].
 #ifndef PRTGS_PACKET_BOUNCE_MIN_BLOCKS
-#define PRTGS_PACKET_BOUNCE_MIN_BLOCKS 4  // 128 registers, no spills; 54.5 KB shared per block at S = 256
+#define PRTGS_PACKET_BOUNCE_MIN_BLOCKS 4  // 128 registers, no spills; 55.5 KB shared per block at S = 256
 #endif
 template <bool BOUNCE>
 __global__ void __launch_bounds__(kPacketThreads, BOUNCE ? PRTGS_PACKET_BOUNCE_MIN_BLOCKS : PRTGS_PACKET_MIN_BLOCKS)

@@ -868,8 +868,11 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy_bwd(int64_t n_glossy,
   extern __shared__ float smem[];
   float* sdir = smem;         // [S*3]
   float* sY = sdir + 3 * S;   // [S][C]
-  float* sQ = sY + S * C;     // [S][C]  dM Y(w_o)
+  float* sQ = sY + S * C;     // [S][C]  dM Y(w_o) (rows of the directions with n.w_o > 0)
   float* sdM = sQ + S * C;    // [C*C]
+  int* sout_list = reinterpret_cast<int*>(sdM + C * C);  // [S] directions with n.w > 0
+  int* sin_list = sout_list + S;                         // [S] the same, those with V != 0 first
+  int* wt = sin_list + S;                                // [kGlossyThreads / 32]
   __shared__ float red[5][kGlossyThreads / 32];
   for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sdir[i] = dirs[i];
   __syncthreads();
@@ -888,56 +891,65 @@ __global__ void __launch_bounds__(kGlossyThreads) k_glossy_bwd(int64_t n_glossy,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t g = blockIdx.x; g < n_glossy; g += gridDim.x) {
     const int64_t i = glossy_ids[g];
-    for (int e = threadIdx.x; e < C * C; e += blockDim.x) sdM[e] = dM[g * C * C + e];
-    __syncthreads();
-    for (int e = threadIdx.x; e < S * C; e += blockDim.x) {
-      const int o = e / C, a = e % C;
-      float q = 0.f;
-      for (int b = 0; b < C; ++b) q = fmaf(sdM[a * C + b], sY[o * C + b], q);
-      sQ[e] = q;
-    }
-    __syncthreads();
     const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
     const float r = roughness[i], metal = metallic[i];
+    auto cosn = [&](int s) {
+      const float* w = sdir + 3 * s;
+      return fmaf(nx, w[0], fmaf(ny, w[1], nz * w[2]));
+    };
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) sdM[e] = dM[g * C * C + e];
+    // the directions with n.w > 0 (increasing); as incoming directions, those with V != 0 (which
+    // take every derivative) before those with V = 0 (dV only), so that warps stay converged
+    const int n_out = glossy_compact(S, [&](int s) { return cosn(s) > 0.0f; }, sout_list, wt);
+    const int n_full =
+        glossy_compact(S, [&](int s) { return cosn(s) > 0.0f && V[i * S + s] != 0.0f; }, sin_list, wt);
+    const int n_in = n_full + glossy_compact(S, [&](int s) { return cosn(s) > 0.0f && V[i * S + s] == 0.0f; },
+                                             sin_list + n_full, wt);
+    for (int e = threadIdx.x; e < n_out * C; e += blockDim.x) {
+      const int o = sout_list[e / C], a = e % C;
+      float q = 0.f;
+      for (int b = 0; b < C; ++b) q = fmaf(sdM[a * C + b], sY[o * C + b], q);
+      sQ[o * C + a] = q;
+    }
+    for (int s = threadIdx.x; s < S; s += blockDim.x)
+      if (!(cosn(s) > 0.0f)) dV[i * S + s] = 0.f;
+    __syncthreads();
     float gr = 0.f, gm = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    for (int l = threadIdx.x; l < n_in; l += blockDim.x) {
+      const int s = sin_list[l];
       const float* wi = sdir + 3 * s;
-      const float c = fmaf(nx, wi[0], fmaf(ny, wi[1], nz * wi[2]));
-      float dv = 0.f;
-      if (c > 0.0f) {
-        const float v = V[i * S + s];
-        float Ys[C];
+      const float c = cosn(s);
+      const float v = V[i * S + s];
+      float Ys[C];
 #pragma unroll
-        for (int a = 0; a < C; ++a) Ys[a] = sY[s * C + a];
-        float kU = 0.f, rU = 0.f, mU = 0.f, nU[3] = {0.f, 0.f, 0.f};
-        for (int o = 0; o < S; ++o) {
-          const float* wo = sdir + 3 * o;
-          const float no = fmaf(nx, wo[0], fmaf(ny, wo[1], nz * wo[2]));
-          if (!(no > 0.0f)) continue;
-          float U = 0.f;
+      for (int a = 0; a < C; ++a) Ys[a] = sY[s * C + a];
+      float kU = 0.f, rU = 0.f, mU = 0.f, nU[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < n_out; ++q) {
+        const int o = sout_list[q];
+        const float* wo = sdir + 3 * o;
+        const float no = cosn(o);
+        float U = 0.f;
 #pragma unroll
-          for (int a = 0; a < C; ++a) U = fmaf(Ys[a], sQ[o * C + a], U);
-          float kv;
-          const float dkdr = brdf_kernel_dr(nx, ny, nz, wi, wo, c, no, r, metal, kv);
-          kU = fmaf(kv, U, kU);
-          if (v != 0.0f) {
-            rU = fmaf(U, dkdr, rU);
-            mU -= U;
-            float dn[3];
-            brdf_kernel_dn(nx, ny, nz, wi, wo, r, dn);
-            nU[0] = fmaf(U, dn[0], nU[0]);
-            nU[1] = fmaf(U, dn[1], nU[1]);
-            nU[2] = fmaf(U, dn[2], nU[2]);
-          }
+        for (int a = 0; a < C; ++a) U = fmaf(Ys[a], sQ[o * C + a], U);
+        float kv;
+        const float dkdr = brdf_kernel_dr(nx, ny, nz, wi, wo, c, no, r, metal, kv);
+        kU = fmaf(kv, U, kU);
+        if (v != 0.0f) {
+          rU = fmaf(U, dkdr, rU);
+          mU -= U;
+          float dn[3];
+          brdf_kernel_dn(nx, ny, nz, wi, wo, r, dn);
+          nU[0] = fmaf(U, dn[0], nU[0]);
+          nU[1] = fmaf(U, dn[1], nU[1]);
+          nU[2] = fmaf(U, dn[2], nU[2]);
         }
-        dv = w2 * c * kU;
-        gr = fmaf(w2 * c * v, rU, gr);
-        gm = fmaf(w2 * c * v, mU, gm);
-        gnx = fmaf(w2 * v, fmaf(kU, wi[0], c * nU[0]), gnx);
-        gny = fmaf(w2 * v, fmaf(kU, wi[1], c * nU[1]), gny);
-        gnz = fmaf(w2 * v, fmaf(kU, wi[2], c * nU[2]), gnz);
       }
-      dV[i * S + s] = dv;
+      dV[i * S + s] = w2 * c * kU;
+      gr = fmaf(w2 * c * v, rU, gr);
+      gm = fmaf(w2 * c * v, mU, gm);
+      gnx = fmaf(w2 * v, fmaf(kU, wi[0], c * nU[0]), gnx);
+      gny = fmaf(w2 * v, fmaf(kU, wi[1], c * nU[1]), gny);
+      gnz = fmaf(w2 * v, fmaf(kU, wi[2], c * nU[2]), gnz);
     }
     gr = warp_sum(gr);
     gm = warp_sum(gm);
@@ -1250,7 +1262,9 @@ size_t glossy_backward_workspace(int64_t n, const prtgs_transfer_params* p) {
          align_up(sizeof(uint32_t)) + (C > kMaxC ? align_up(sizeof(float) * (size_t)p->n_dirs * C) : 0);
 }
 
-static size_t glossy_bwd_smem(int S, int C) { return sizeof(float) * (3 * S + 2 * (size_t)S * C + (size_t)C * C); }
+static size_t glossy_bwd_smem(int S, int C) {
+  return sizeof(float) * (3 * S + 2 * (size_t)S * C + (size_t)C * C) + sizeof(int) * (2 * (size_t)S + kGlossyThreads / 32);
+}
 
 bool glossy_backward_fits(int S, int order) {
   return glossy_bwd_smem(S, sh_count(order)) <= (size_t)227 * 1024;
